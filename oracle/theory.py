@@ -1,0 +1,59 @@
+"""Closed forms of the paper used to pin the oracle -- TEST INFRASTRUCTURE ONLY.
+
+Each function restates one equation of the paper in binary64:
+
+* ``p0``           noise peak probability, threshold + local maximum (Eq. p0, Sec. V)
+* ``binomial``     mean and standard deviation of a noise-only number count
+                   (Eqs. phmsig, houghmean, Sec. VI)
+* ``critical_ratio``   CR = (n - N p0) / sqrt(N p0 (1 - p0))   (Eq. cr, Sec. XII)
+* ``n_thr_gauss``  count threshold for a false-alarm probability (Eq. nthr_gauss)
+* ``cr_thr``       CR threshold for N_cand of N_tot points (Eq. crthr)
+* ``n_tot``        number of coarse parameter-space points (Eq. Ntot, Sec. VIII)
+"""
+from __future__ import annotations
+
+import math
+
+from scipy.special import erfcinv
+
+
+def p0(theta: float) -> float:
+    """Eq. p0: integral over x > theta of e^-x (1 - e^-x)^2."""
+    return math.exp(-theta) - math.exp(-2.0 * theta) + math.exp(-3.0 * theta) / 3.0
+
+
+def binomial(n: int, eta: float) -> tuple:
+    """Eq. houghmean: (mu, sigma) = (N eta, sqrt(N eta (1 - eta)))."""
+    mu = n * eta
+    return mu, math.sqrt(mu * (1.0 - eta))
+
+
+def critical_ratio(count: float, n: int, p: float) -> float:
+    """Eq. cr."""
+    return (count - n * p) / math.sqrt(n * p * (1.0 - p))
+
+
+def n_thr_gauss(n: int, p: float, pfa: float) -> float:
+    """Eq. nthr_gauss: N p0 + sqrt(2 N p0 (1 - p0)) erfc^-1(2 P_fa)."""
+    return n * p + math.sqrt(2.0 * n * p * (1.0 - p)) * float(erfcinv(2.0 * pfa))
+
+
+def cr_thr(n_cand: float, n_tot: float) -> float:
+    """Eq. crthr: sqrt(2) erfc^-1(2 N_cand / N_tot)."""
+    return math.sqrt(2.0) * float(erfcinv(2.0 * n_cand / n_tot))
+
+
+def n_tot(k_f: float, k_sky: float, t_fft: float, dt: float, t_obs: float,
+          tau_min: float) -> tuple:
+    """Eq. Ntot with the product over orders j <= j_max whose N_sd^(j) >= 1 (Eq. Nsd).
+
+    Returns (N_tot, j_max)."""
+    base = t_fft / dt
+    j_max = 0
+    prod = 1.0
+    j = 1
+    while base * (t_obs / tau_min) ** j >= 1.0:
+        j_max = j
+        prod *= (t_obs / tau_min) ** j
+        j += 1
+    return 5.6 * math.pi * 1e-9 * k_f * k_sky * base ** (3 + j_max) * prod, j_max
