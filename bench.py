@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 frequency-Hough path.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+Doppler correction + fixed-point positions + shift tables (fh_correct_doppler),
+transform + profile (fh_transform), candidate selection (fh_select_candidates).
+
+Default workload: one sky point at the paper's low-frequency scale --
+T_FFT = 8192 s, half-interlaced over 150 days (3164 FFTs), 50-51 Hz with
+K = 10 (81920 cells), spin-down -1e-8 .. +1e-9 Hz/s (1169 rows), peak
+probability 0.04 (~1.18M peaks), top-5 per 0.1 Hz sub-band.
+
+Printed: one JSON line (rank 0) with throughput in peak x spin-down updates/s
+(device-resident inputs), the end-to-end figure through the C ABI with host
+buffers, the roofline of the transform kernel, the oracle's CPU baseline,
+SM clocks sampled during the timed region, the plain vs batched comparison
+on a 256-direction sky patch and the served-stream latency figures.
+
+``--impl reference`` times the CPU oracle (the reference arm of this build)
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FH peak×spindown updates/s, 1 GB300; served-job p50/p99 latency vs plain"
+UNIT = "updates/s"
+WORKLOAD = "single_sky_T8192_150d_50Hz"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu legs")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config_of(w, extra=None):
+    pp = w.plan_params()
+    cfg = {"workload": w.name,
+           "description": ("T_FFT=%g s, %d FFTs (start spacing %g s), band %.2f-%.2f Hz, K=%d "
+                           "(%d cells), %d spin-down rows (%.3g..%.3g Hz/s), p=%.3g, %d sky "
+                           "direction(s), top-%d per %.2g Hz" %
+                           (w.t_fft, w.n_fft, w.t_step, w.f_lo, w.f_hi, w.k_over, pp["n_f0"],
+                            pp["n_fdot"], pp["fdot_min"],
+                            pp["fdot_min"] + (pp["n_fdot"] - 1) * pp["fdot_step"], w.p_peak,
+                            w.n_dir, w.top_k, w.subband_hz)),
+           "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(open(self.path)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks_path():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline_leg(inp, pp, budget_s=12.0):
+    """The oracle as it stands, whole path a1-a6 on the same workload."""
+    import oracle
+    oracle.build()
+    upd = inp.n_peaks * pp["n_fdot"] * inp.sky.shape[0]
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.search(inp, pp)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 5:
+            break
+    best = min(times)
+    return {"value": upd / best, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "whole path a1-a6 (maps, profile, selection) on the full workload, "
+                      "1 direction, best of %d runs (%.2f s each)" % (len(times), best)}
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1407_8333_gb300 import build, fh, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    fh.load()
+
+    w = synth.WORKLOADS[args.workload]
+    inp = synth.make_inputs(w)
+    pp = w.plan_params()
+    n_dir = inp.sky.shape[0]
+    dev = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+    plan = fh.fh_create_plan(fh.make_desc(pp, w.n_fft, n_dir, inp.n_peaks))
+    fh.fh_correct_doppler(plan, *dev)
+    tile, warps = fh.fh_autotune(plan, 0, n_dir)
+    n_sb = -(-pp["n_f0"] // pp["subband_cells"])
+    cand = torch.empty(n_dir * n_sb * pp["top_k"] * 48, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    upd_step = inp.n_peaks * pp["n_fdot"] * n_dir
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        fh.fh_correct_doppler(plan, *dev, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        fh.fh_transform(plan, 0, n_dir, None, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        fh.fh_select_candidates(plan, 0, n_dir, cand, stream=stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    l0 = fh.fh_plan_launches(plan)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = fh.fh_plan_launches(plan) - l0
+    clocks = sampler.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    tr_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    dop_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    sel_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = upd_step * args.steps * world / (total_ms * 1e-3)
+
+    # roofline of the transform kernel (dominant): shared-memory atomics, one per update
+    atomic_peak, _ = fh.fh_bench_smem_atomics(0, 4096)
+    tr_avg = statistics.mean(tr_ms)
+    achieved_atom = upd_step / (tr_avg * 1e-3)
+    peaks, peak_src = peaks_path()
+    hbm_bytes = 8 * inp.n_peaks * n_dir + 8 * pp["n_f0"] * n_dir + 16 * w.n_fft
+    roof = {"bound": "smem_atomic", "achieved": achieved_atom / 1e9, "peak": atomic_peak / 1e9,
+            "unit": "Gatomic/s", "frac": achieved_atom / atomic_peak, "traffic": None,
+            "kernel": "transform_kernel<FH_MODE_START>",
+            "algorithmic": "1 shared-memory atomic per peak x spin-down update; %d updates per launch"
+                           % upd_step,
+            "peak_source": "own microbenchmark fh_bench_smem_atomics(0): conflict-free int32 "
+                           "atomicAdd, all SMs, measured in this run",
+            "tile_cells": tile, "block_warps": warps}
+    roof_hbm = {"bound": "hbm", "achieved": hbm_bytes / (tr_avg * 1e-3) / 1e9,
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": hbm_bytes / (tr_avg * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
+                "algorithmic": "8 B/peak (positions) + 8 B/cell (profile) + 16 B/FFT per launch"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "i64/i32 (f64 Doppler)",
+           "data": "synthetic (seeded SplitMix64 peakmap, paper-shaped)",
+           "config": config_of(w, {"parallelism": "replicas" if world > 1 else "single GPU",
+                                   "inputs": "device-resident"}),
+           "breakdown_ms": {"correct_doppler": statistics.mean(dop_ms),
+                            "transform": tr_avg, "select": statistics.mean(sel_ms)},
+           "roofline": roof, "roofline_hbm": roof_hbm, "clocks": clocks,
+           "gpu_launches": launches}
+
+    # end to end through the C ABI with host buffers (pinned), H2D/D2H inside
+    pinned = [torch.from_numpy(x).pin_memory().numpy() for x in
+              (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+    h2d = sum(x.nbytes for x in pinned)
+    e2e_ms = []
+    host_out = np.zeros(n_dir * n_sb * pp["top_k"], dtype=fh.CANDIDATE_DTYPE)
+    for k in range(max(3, args.warmup) + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fh.fh_correct_doppler(plan, *pinned, stream=stream)
+        fh.fh_transform(plan, 0, n_dir, None, stream=stream)
+        fh.fh_select_candidates(plan, 0, n_dir, host_out, stream=stream)
+        t1 = time.perf_counter()
+        if k >= max(3, args.warmup):
+            e2e_ms.append((t1 - t0) * 1e3)
+    out["e2e"] = {"value": upd_step * len(e2e_ms) / (sum(e2e_ms) * 1e-3) * world, "unit": UNIT,
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": host_out.nbytes,
+                  "ms_per_step": statistics.mean(e2e_ms)}
+    fh.fh_destroy_plan(plan)
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        out["batched_vs_plain"] = batched_vs_plain(fh, synth, torch)
+        try:
+            out["serving"] = serving_leg(fh, synth, torch, args.serve_seconds)
+        except Exception as e:  # report, do not hide
+            out["serving"] = {"error": str(e)[:300]}
+        out["cpu_baseline"] = cpu_baseline_leg(inp, pp)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def batched_vs_plain(fh, synth, torch):
+    """256-direction sky patch (T_FFT 1024 s, 200 FFTs, 100-101 Hz): one launch
+    per direction vs one persistent launch over all directions."""
+    import numpy as np
+    w = synth.WORKLOADS["sky_patch256_T1024_N200_100Hz"]
+    inp = synth.make_inputs(w)
+    pp = w.plan_params()
+    n_dir = inp.sky.shape[0]
+    dev = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+    upd = inp.n_peaks * pp["n_fdot"] * n_dir
+    n_sb = -(-pp["n_f0"] // pp["subband_cells"])
+    cand = torch.empty(n_dir * n_sb * pp["top_k"] * 48, dtype=torch.uint8, device="cuda")
+    res = {"workload": w.name, "updates_per_step": upd}
+    for name, sched in (("plain", fh.FH_SCHED_PLAIN), ("batched", fh.FH_SCHED_BATCHED)):
+        plan = fh.fh_create_plan(fh.make_desc(pp, w.n_fft, n_dir, inp.n_peaks, schedule=sched))
+        if sched == fh.FH_SCHED_BATCHED:
+            fh.fh_correct_doppler(plan, *dev)
+            fh.fh_autotune(plan, 0, n_dir)
+        ts = []
+        for k in range(13):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fh.fh_correct_doppler(plan, *dev)
+            fh.fh_transform(plan, 0, n_dir, None)
+            fh.fh_select_candidates(plan, 0, n_dir, cand)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        res[name] = {"ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3)}
+        fh.fh_destroy_plan(plan)
+    res["speedup"] = res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"]
+    return res
+
+
+def serving_leg(fh, synth, torch, seconds):
+    from paper_1407_8333_gb300 import serve
+    return serve.run_stream(seconds=seconds, seed=4)
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1407_8333_gb300 import synth
+    oracle.build()
+    w = synth.WORKLOADS[args.workload]
+    inp = synth.make_inputs(w)
+    pp = w.plan_params()
+    upd = inp.n_peaks * pp["n_fdot"] * inp.sky.shape[0]
+    for _ in range(args.warmup):
+        oracle.search(inp, pp)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.search(inp, pp)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = upd * args.steps / total
+    sample = ("whole path a1-a6 of the workload per step (1 direction, all %d rows), "
+              "%d steps" % (pp["n_fdot"], args.steps))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "i64/i32 (f64 Doppler)", "data": "synthetic (seeded SplitMix64 peakmap)",
+           "config": config_of(w, {"inputs": "host memory"}), "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

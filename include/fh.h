@@ -1,0 +1,291 @@
+/*
+ * fh.h -- C ABI of the GB300 frequency-Hough (FH) library (libfh.so).
+ *
+ * The FH transform (Astone et al., arXiv:1407.8333, Sec. VI) maps a
+ * time-frequency peakmap, Doppler-corrected for one sky direction, into the
+ * source frequency / spin-down plane: each peak (t_i, f) becomes a stripe of
+ * the line f0 = f - fdot (t_i - t0) (Eq. uno), one input bin wide (Eq. due),
+ * on a frequency axis over-resolved by K (Eq. freqres), and every cell the
+ * stripe touches gains one count (Eq. ncount).  Candidates are then taken per
+ * frequency sub-band over all spin-down rows (Sec. VIII).
+ *
+ * Numerical definition (bit-exact contract; all floating point is IEEE-754
+ * binary64, round-to-nearest-even, one rounding per operation, no fused
+ * multiply-add):
+ *   a1  r[d][i] = 1 / (1 + ((v_x n_x + v_y n_y) + v_z n_z))          (Eq. fdopp)
+ *   a2  A[d][p] = floor(((f_p r[d][i] - f0_min) * KT + (0.5 - 0.5 K)) * 2^32)
+ *       with KT = K * T_FFT; a stripe covers the K cells whose centres lie in
+ *       (x - K/2, x + K/2], x = the corrected frequency in cell units.
+ *   a3  c_i = (t_i - t_ref) * KT;  S0[i] = floor((fdot_min c_i) 2^32);
+ *       D[i] = floor((fdot_step c_i) 2^32)                    (Eqs. uno, sdstep)
+ *   a4  s = floor((A[d][p] - (S0[i] + j D[i])) / 2^32): first cell of the
+ *       stripe of peak p on spin-down row j; cells [s, s + K) clipped to
+ *       [0, n_f0) each get +1
+ *   a5  count[d][j][b] = number of (peak) stripes covering cell b on row j
+ *   a6  profile[b] = max_j count[j][b] (smallest such j); per sub-band of
+ *       subband_cells cells, up to top_k greedy picks by (count desc, row asc,
+ *       cell asc), each outside +-excl_cells of earlier picks, stopping at a
+ *       count < n_thr or a pick closer than sep_cells to an earlier one.
+ * Cell b covers [f0_min + b/KT, f0_min + (b + 1)/KT); row j has
+ * fdot_j = fdot_min + j * fdot_step.
+ *
+ * Conventions.  Every function returns an int status (FH_OK or a negative
+ * FH_ERR_*) and never aborts; fh_last_error() gives a thread-local message.
+ * Streams are cudaStream_t values passed as void* (NULL = the legacy default
+ * stream).  Pointers marked "device" must be device (or managed) memory of
+ * the current device; "host" pointers are ordinary host memory.  Calls are
+ * stream-ordered: unless a function says it synchronises, it only enqueues
+ * work, and device buffers the caller passed must stay valid until that work
+ * completes.  The caller owns every buffer it passes; the library owns the
+ * plan's internal buffers.  A plan is used by one host thread at a time; a
+ * server is thread-safe.
+ */
+#ifndef FH_H
+#define FH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    FH_OK = 0,
+    FH_ERR_INVALID_ARG = -1, /* null handle/pointer, bad size, non-finite value  */
+    FH_ERR_UNSORTED = -2,    /* t_fft not increasing, freq not ascending in an FFT,
+                                offsets not a valid CSR                          */
+    FH_ERR_RANGE = -3,       /* a fixed-point quantity would leave +-2^60        */
+    FH_ERR_NOMEM = -4,       /* device allocation failed                         */
+    FH_ERR_TOO_LARGE = -5,   /* job can never fit the server's memory budget     */
+    FH_ERR_CUDA = -6,        /* a CUDA runtime call failed                       */
+    FH_ERR_TIMEOUT = -7,     /* a bounded wait ran out                           */
+    FH_ERR_NOT_READY = -8,   /* fh_poll: the job has not finished                */
+    FH_ERR_CANCELLED = -9,   /* the job was cancelled                            */
+    FH_ERR_BAD_HANDLE = -10, /* unknown job id / destroyed server                */
+    FH_ERR_CAPACITY = -11    /* output buffer smaller than *n_out                */
+};
+
+/* where the arrays of an input live */
+enum { FH_MEM_HOST = 0, FH_MEM_DEVICE = 1 };
+
+/* counting kernels (fh_plan_desc.mode) -- both give the same integers */
+enum {
+    FH_MODE_AUTO = 0,  /* library default (FH_MODE_START)                       */
+    FH_MODE_DIFF = 1,  /* +1 at the stripe start, -1 after its end, prefix sum  */
+    FH_MODE_START = 2  /* +1 at the stripe start only, sum over a K-cell window */
+};
+
+/* how fh_transform schedules a set of directions (fh_plan_desc.schedule) */
+enum {
+    FH_SCHED_BATCHED = 0, /* one persistent launch over all directions' tiles    */
+    FH_SCHED_PLAIN = 1    /* one launch per sky direction                         */
+};
+
+typedef struct fh_plan_s *fh_plan;     /* opaque, owned by the library */
+typedef struct fh_server_s *fh_server; /* opaque, owned by the library */
+typedef int64_t fh_job_id;
+
+/* Peakmap (Sec. V): the peaks of every FFT, CSR by FFT, FFTs in time order. */
+typedef struct {
+    int32_t n_fft;          /* number of FFTs (>= 0)                              */
+    int64_t n_peaks;        /* total number of peaks = offsets[n_fft]             */
+    const double *t_fft;    /* n_fft FFT start times [s], strictly increasing     */
+    const int64_t *offsets; /* n_fft + 1; peaks of FFT i are [offsets[i], offsets[i+1]);
+                               offsets[0] = 0, non-decreasing                     */
+    const double *freq;     /* n_peaks frequencies [Hz] > 0, strictly ascending
+                               within each FFT                                    */
+    int32_t mem_kind;       /* FH_MEM_HOST or FH_MEM_DEVICE, for all three arrays
+                               and for the velocity and sky arrays of
+                               fh_correct_doppler                                 */
+} fh_peakmap;
+
+/* Plan: grids of Sec. VII and the selection rule of Sec. VIII. */
+typedef struct {
+    double t_fft;            /* T_FFT [s] > 0                                     */
+    int32_t k_over;          /* frequency over-resolution K >= 1 (Eq. freqres)     */
+    double f0_min;           /* lower edge of map cell 0 [Hz]                     */
+    int32_t n_f0;            /* number of over-resolved frequency cells >= 1      */
+    double fdot_min;         /* spin-down of row 0 [Hz/s]                         */
+    double fdot_step;        /* spin-down step [Hz/s] (Eq. sdstep)                */
+    int32_t n_fdot;          /* number of spin-down rows >= 1                     */
+    double t_ref;            /* reference time t0 [s] (middle of the run, Sec. VI) */
+    int32_t subband_cells;   /* sub-band width in cells >= 1                      */
+    int32_t top_k;           /* picks per sub-band, 1 .. 64                        */
+    int32_t excl_cells;      /* exclusion half-width around a pick, cells >= 0    */
+    int32_t sep_cells;       /* minimum distance to earlier picks, cells >= 0     */
+    int32_t n_thr;           /* minimum count of a pick                           */
+    double p0;               /* peak probability for the critical ratio (Eq. cr), in (0,1) */
+    int32_t max_fft;         /* capacity: FFTs per peakmap                        */
+    int32_t max_dir;         /* capacity: directions per fh_correct_doppler call,
+                                1 .. 65535                                        */
+    int64_t max_peaks;       /* capacity: peaks per peakmap (< 2^31)              */
+    int32_t mode;            /* FH_MODE_*                                          */
+    int32_t schedule;        /* FH_SCHED_*                                         */
+    int32_t tile_cells;      /* f0 tile width in cells; 0 = library default        */
+    int32_t block_warps;     /* warps per transform block (4..32); 0 = default     */
+} fh_plan_desc;
+
+/* One candidate slot.  Empty slots have row = cell = count = -1 and zero
+ * f0/fdot/cr; dir, subband and rank are always set. */
+typedef struct {
+    int32_t dir;      /* absolute direction index of the fh_correct_doppler call */
+    int32_t subband;  /* sub-band index q: cells [q W, q W + W)                  */
+    int32_t rank;     /* 0 .. top_k - 1 within the sub-band                       */
+    int32_t row;      /* spin-down row j                                          */
+    int32_t cell;     /* frequency cell b                                         */
+    int32_t count;    /* number count n (Eq. ncount)                              */
+    double f0;        /* f0_min + (b + 0.5) / KT [Hz], cell centre                */
+    double fdot;      /* fdot_min + j * fdot_step [Hz/s]                          */
+    double cr;        /* (n - N p0) / sqrt(N p0 (1 - p0)), N = n_fft (Eq. cr)    */
+} fh_candidate;
+
+/* ---- plan -------------------------------------------------------------- */
+
+/* Validate desc, allocate the plan's device buffers (sized by the max_*
+ * capacities) on the current device.  Errors: FH_ERR_INVALID_ARG,
+ * FH_ERR_RANGE (grid does not fit 32.32 fixed point), FH_ERR_NOMEM. */
+int fh_create_plan(const fh_plan_desc *desc, fh_plan *out);
+
+/* Synchronise the device and free the plan.  NULL is accepted. */
+int fh_destroy_plan(fh_plan plan);
+
+/* Bytes of device memory a plan with this desc allocates (0 if invalid). */
+int64_t fh_plan_device_bytes(const fh_plan_desc *desc);
+
+/* Steps a1-a3 (Sec. VI, Eq. fdopp): Doppler factor of every (direction,
+ * FFT), fixed-point corrected position of every (direction, peak) and the
+ * spin-down shift tables, into the plan's buffers.  These directions are the
+ * ones fh_transform and fh_select_candidates refer to by index.
+ *   pm        peakmap; host arrays are validated on the host and copied;
+ *             device arrays are read in place by the enqueued kernels and
+ *             validated on the device (a failure is reported by the next
+ *             fh_sync / host-output fh_select_candidates as FH_ERR_UNSORTED or
+ *             FH_ERR_INVALID_ARG; the offsets the kernels use are clamped to a
+ *             valid CSR first, so bad device input never reads out of bounds)
+ *   v_over_c  n_fft x 3 detector velocities in units of c (same memory kind)
+ *   sky_n     n_dir x 3 sky unit vectors, same frame (same memory kind)
+ *   n_dir     1 .. max_dir
+ *   out_r     nullable device n_dir x n_fft: copy of the Doppler factors
+ *   out_A     nullable device n_dir x n_peaks: copy of the positions A
+ * Host-input errors: FH_ERR_INVALID_ARG, FH_ERR_UNSORTED, FH_ERR_RANGE. */
+int fh_correct_doppler(fh_plan plan, const fh_peakmap *pm, const double *v_over_c,
+                       const double *sky_n, int32_t n_dir, double *out_r,
+                       int64_t *out_A, void *stream);
+
+/* Steps a4-a5 and the profile half of a6 (Eqs. due, ncount) for directions
+ * [dir_begin, dir_begin + n_dir) of the last fh_correct_doppler call.
+ *   out_maps  nullable device int32 n_dir x n_fdot x n_f0 (row-major): the
+ *             number counts; NULL = candidates only (the map stays on chip)
+ * The per-cell profile is kept in the plan for fh_select_candidates. */
+int fh_transform(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
+                 void *stream);
+
+/* Copy the profile of directions [dir_begin, dir_begin + n_dir) into
+ * out (device, n_dir x n_f0 uint64): key = (count << 32) | (0xFFFFFFFF - row). */
+int fh_copy_profile(fh_plan plan, int32_t dir_begin, int32_t n_dir, uint64_t *out,
+                    void *stream);
+
+/* Step a6 (Sec. VIII; Eq. cr): candidate slots of directions
+ * [dir_begin, dir_begin + n_dir), n_dir x n_sb x top_k records, n_sb =
+ * ceil(n_f0 / subband_cells), direction-major.  *n_out receives that count;
+ * if capacity < *n_out nothing is written and FH_ERR_CAPACITY is returned.
+ * out_mem_kind FH_MEM_HOST: copies to host memory and synchronises the stream
+ * (and reports device-side input validation failures); FH_MEM_DEVICE:
+ * enqueues a device copy. */
+int fh_select_candidates(fh_plan plan, int32_t dir_begin, int32_t n_dir, fh_candidate *out,
+                         int64_t capacity, int64_t *n_out, int32_t out_mem_kind,
+                         void *stream);
+
+/* Synchronise the stream and report device-side input validation (FH_OK,
+ * FH_ERR_UNSORTED, FH_ERR_INVALID_ARG) since the last fh_correct_doppler. */
+int fh_sync(fh_plan plan, void *stream);
+
+/* Time fh_transform over tile widths (and block sizes) on the current
+ * directions and keep the fastest in the plan; returns it in *tile_cells.
+ * Synchronises.  Results are cached per process by grid shape. */
+int fh_autotune(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells,
+                int32_t *block_warps, void *stream);
+
+/* Number of transform/select kernel launches the last fh_transform /
+ * fh_select_candidates / fh_correct_doppler calls enqueued (cumulative since
+ * plan creation). */
+int64_t fh_plan_launches(fh_plan plan);
+
+/* ---- serving (continuous batching) --------------------------------------- */
+
+enum { FH_JOB_QUEUED = 0, FH_JOB_RUNNING = 1, FH_JOB_DONE = 2, FH_JOB_FAILED = 3,
+       FH_JOB_CANCELLED = 4 };
+
+/* One Hough job: a band x T_FFT x sky patch (configuration 4 of the paper's
+ * workload mix).  All arrays are host memory; fh_submit copies them before it
+ * returns, so the caller may free them at once. */
+typedef struct {
+    fh_plan_desc plan;      /* grids and selection; max_* are ignored          */
+    fh_peakmap peaks;       /* mem_kind must be FH_MEM_HOST                    */
+    const double *v_over_c; /* peaks.n_fft x 3                                 */
+    const double *sky_n;    /* n_dir x 3                                       */
+    int32_t n_dir;          /* >= 1                                            */
+} fh_job_desc;
+
+typedef struct {
+    double submit_s;        /* host clock (seconds since server start)          */
+    double start_s;         /* admitted to the device                          */
+    double done_s;          /* results in host memory                          */
+    int64_t updates;        /* n_dir * n_fdot * n_peaks                        */
+    int64_t device_bytes;   /* device memory the job held                      */
+    int32_t batch;          /* index of the launch batch that ran it           */
+    int32_t batch_jobs;     /* jobs in that batch                              */
+} fh_job_stats;
+
+/* Start a server on the current device: a scheduler thread admits queued jobs
+ * while their device memory fits device_mem_budget, batches all jobs admitted
+ * together into one launch sequence on one of max_inflight streams, and lets
+ * batches overlap on the device. */
+int fh_server_create(int64_t device_mem_budget, int32_t max_inflight, fh_server *out);
+
+/* Cancel queued jobs, wait (bounded, 60 s) for running ones, free everything. */
+int fh_server_destroy(fh_server server);
+
+/* Validate and enqueue a job.  FH_ERR_TOO_LARGE if it can never fit the budget. */
+int fh_submit(fh_server server, const fh_job_desc *job, fh_job_id *out);
+
+/* Non-blocking.  *state = FH_JOB_*.  When DONE, copies the job's
+ * n_dir x n_sb x top_k candidate slots to out (host) -- FH_ERR_CAPACITY and
+ * *n_out as in fh_select_candidates; otherwise returns FH_ERR_NOT_READY
+ * (queued/running), the job's error (failed) or FH_ERR_CANCELLED. */
+int fh_poll(fh_server server, fh_job_id id, int32_t *state, fh_candidate *out,
+            int64_t capacity, int64_t *n_out);
+
+/* Timing record of a finished job. */
+int fh_job_get_stats(fh_server server, fh_job_id id, fh_job_stats *out);
+
+/* Cancel a queued job (running jobs complete). */
+int fh_cancel(fh_server server, fh_job_id id);
+
+/* Block until every submitted job is done/failed/cancelled or timeout_s
+ * passes (FH_ERR_TIMEOUT; nothing is cancelled). */
+int fh_server_drain(fh_server server, double timeout_s);
+
+/* paused != 0: stop admitting queued jobs (running batches complete);
+ * paused = 0: resume.  For maintenance and for tests of stuck queues. */
+int fh_server_pause(fh_server server, int32_t paused);
+
+/* ---- measurement ------------------------------------------------------- */
+
+/* Shared-memory atomic throughput of this GPU: every SM runs blocks of 1024
+ * threads doing int32 atomicAdd into shared memory, conflict-free (variant 0,
+ * lane l -> bank l) or to random addresses (variant 1).  Synchronises.
+ * *atomics_per_s = lane-atomics per second over the whole GPU. */
+int fh_bench_smem_atomics(int32_t variant, int32_t iters, double *atomics_per_s,
+                          double *ms, void *stream);
+
+/* ---- misc -------------------------------------------------------------- */
+const char *fh_last_error(void);
+const char *fh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FH_H */

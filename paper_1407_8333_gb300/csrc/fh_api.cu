@@ -1,0 +1,676 @@
+// C ABI of libfh: plans, host-side validation, and the stream-ordered entry
+// points fh_correct_doppler / fh_transform / fh_select_candidates.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "fh_internal.h"
+
+namespace fh {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(FH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace fh
+
+using namespace fh;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1, want = -1;
+    explicit DeviceGuard(int dev) : want(dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int device_error_code(int32_t bits)
+{
+    if (bits & (kErrCsr | kErrUnsorted))
+        return set_error(FH_ERR_UNSORTED, "device inputs: offsets not a valid CSR, t_fft not "
+                                          "increasing or freq not ascending within an FFT");
+    if (bits & kErrInvalid)
+        return set_error(FH_ERR_INVALID_ARG, "device inputs: non-finite or out-of-range value");
+    if (bits & kErrRange)
+        return set_error(FH_ERR_RANGE, "a fixed-point position or shift exceeds 2^28 cells");
+    return FH_OK;
+}
+
+}  // namespace
+
+namespace fh {
+
+int max_optin_smem(int device)
+{
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    return v > 0 ? v : 48 * 1024;
+}
+
+// largest multiple-of-32 tile width whose counters fit the per-block limit
+int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nwarps)
+{
+    const size_t lim = (size_t)max_optin_smem(device);
+    int32_t w = (int32_t)(lim / (kRows * sizeof(int32_t))) - d.k_over + 1;
+    if (mode == FH_MODE_DIFF) w -= nwarps;
+    w = (w / 32) * 32;
+    if (w < 32) w = 32;
+    if (w > d.n_f0) w = d.n_f0;
+    return w;
+}
+
+int validate_desc(const fh_plan_desc &d)
+{
+    auto bad = [](const char *m) { return set_error(FH_ERR_INVALID_ARG, "plan: %s", m); };
+    if (!(std::isfinite(d.t_fft) && d.t_fft > 0.0)) return bad("t_fft must be finite and > 0");
+    if (d.k_over < 1 || d.k_over > (1 << 16)) return bad("k_over must be in [1, 65536]");
+    const double kt = (double)d.k_over * d.t_fft;
+    if (std::fma((double)d.k_over, d.t_fft, -kt) != 0.0)
+        return bad("k_over * t_fft must be exactly representable in binary64");
+    if (!std::isfinite(d.f0_min)) return bad("f0_min must be finite");
+    if (d.n_f0 < 1) return bad("n_f0 must be >= 1");
+    if ((int64_t)d.n_f0 + d.k_over >= kFixedLimit)
+        return set_error(FH_ERR_RANGE, "plan: n_f0 + k_over must stay below 2^28");
+    if (!std::isfinite(d.fdot_min) || !std::isfinite(d.fdot_step))
+        return bad("fdot_min and fdot_step must be finite");
+    if (d.n_fdot < 1 || d.n_fdot > (1 << 20)) return bad("n_fdot must be in [1, 2^20]");
+    if (!std::isfinite(d.t_ref)) return bad("t_ref must be finite");
+    if (d.subband_cells < 1) return bad("subband_cells must be >= 1");
+    if (d.top_k < 1 || d.top_k > 64) return bad("top_k must be in [1, 64]");
+    if (d.excl_cells < 0 || d.sep_cells < 0) return bad("excl_cells and sep_cells must be >= 0");
+    if (!(d.p0 > 0.0 && d.p0 < 1.0)) return bad("p0 must be in (0, 1)");
+    if (d.max_fft < 1 || d.max_fft > (1 << 26)) return bad("max_fft must be in [1, 2^26]");
+    if (d.max_dir < 1 || d.max_dir > 65535) return bad("max_dir must be in [1, 65535]");
+    if (d.max_peaks < 1 || d.max_peaks >= ((int64_t)1 << 31))
+        return bad("max_peaks must be in [1, 2^31)");
+    if (d.mode < FH_MODE_AUTO || d.mode > FH_MODE_START) return bad("unknown mode");
+    if (d.schedule < FH_SCHED_BATCHED || d.schedule > FH_SCHED_PLAIN)
+        return bad("unknown schedule");
+    if (d.tile_cells != 0 && d.tile_cells < 32) return bad("tile_cells must be 0 or >= 32");
+    if (d.block_warps != 0 && (d.block_warps < 4 || d.block_warps > 32))
+        return bad("block_warps must be 0 or in [4, 32]");
+    return FH_OK;
+}
+
+}  // namespace fh
+
+namespace {
+
+struct Sizes {
+    int64_t t, offsets, tables, freq, v, sky, A, profile, cand;
+    int64_t total() const
+    {
+        return t + offsets + 2 * tables + freq + v + sky + A + profile + cand + 256;
+    }
+};
+
+Sizes plan_sizes(const fh_plan_desc &d)
+{
+    const int64_t n_sb = (d.n_f0 + d.subband_cells - 1) / d.subband_cells;
+    Sizes s;
+    s.t = 8 * (int64_t)d.max_fft;
+    s.offsets = 8 * ((int64_t)d.max_fft + 1);
+    s.tables = 8 * (int64_t)d.max_fft;
+    s.freq = 8 * d.max_peaks;
+    s.v = 24 * (int64_t)d.max_fft;
+    s.sky = 24 * (int64_t)d.max_dir;
+    s.A = 8 * (int64_t)d.max_dir * d.max_peaks;
+    s.profile = 8 * (int64_t)d.max_dir * d.n_f0;
+    s.cand = (int64_t)sizeof(fh_candidate) * d.max_dir * n_sb * d.top_k;
+    return s;
+}
+
+}  // namespace
+
+struct fh_plan_s {
+    fh_plan_desc d{};
+    int device = 0;
+    int n_sm = 0;
+    double kt = 0.0;
+    int32_t n_sb = 0;
+    int32_t mode = FH_MODE_START;
+    int32_t tile_cells = 0;
+    int32_t block_warps = 32;
+    double *t = nullptr, *freq = nullptr, *v = nullptr, *sky = nullptr;
+    int64_t *offsets = nullptr, *S0 = nullptr, *D = nullptr, *A = nullptr;
+    uint64_t *profile = nullptr;
+    fh_candidate *cand = nullptr;
+    int32_t *err = nullptr;
+    int32_t *h_err = nullptr;  // pinned
+    int32_t n_fft = -1;
+    int64_t n_peaks = 0;
+    int32_t n_dir = 0;
+    int64_t launches = 0;
+    size_t prepared_smem[3] = {0, 0, 0};
+
+    void release()
+    {
+        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        if (h_err) cudaFreeHost(h_err);
+        t = freq = v = sky = nullptr;
+        offsets = S0 = D = A = nullptr;
+        profile = nullptr;
+        cand = nullptr;
+        err = h_err = nullptr;
+    }
+};
+
+namespace {
+
+int prepare_transform(fh_plan p, int32_t mode, size_t smem)
+{
+    if (p->prepared_smem[mode] >= smem) return FH_OK;
+    cudaError_t e = transform_prepare(mode, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(transform)");
+    p->prepared_smem[mode] = smem;
+    return FH_OK;
+}
+
+int check_dirs(fh_plan p, int32_t dir_begin, int32_t n_dir)
+{
+    if (p->n_fft < 0)
+        return set_error(FH_ERR_INVALID_ARG, "fh_correct_doppler has not been called on this plan");
+    if (dir_begin < 0 || n_dir < 1 || (int64_t)dir_begin + n_dir > p->n_dir)
+        return set_error(FH_ERR_INVALID_ARG, "directions [%d, %d) outside [0, %d)", dir_begin,
+                         dir_begin + n_dir, p->n_dir);
+    return FH_OK;
+}
+
+}  // namespace
+
+namespace fh {
+
+int validate_host_inputs(const fh_plan_desc &d, double kt, const fh_peakmap *pm, const double *v,
+                         const double *sky, int32_t n_dir)
+{
+    const int32_t n = pm->n_fft;
+    if (n > 0 && (!pm->t_fft || !v)) return set_error(FH_ERR_INVALID_ARG, "null t_fft or v");
+    if (!pm->offsets) return set_error(FH_ERR_INVALID_ARG, "null offsets");
+    if (pm->n_peaks > 0 && !pm->freq) return set_error(FH_ERR_INVALID_ARG, "null freq");
+    if (pm->offsets[0] != 0) return set_error(FH_ERR_UNSORTED, "offsets[0] must be 0");
+    for (int32_t i = 0; i < n; ++i) {
+        if (pm->offsets[i + 1] < pm->offsets[i])
+            return set_error(FH_ERR_UNSORTED, "offsets decrease at FFT %d", i);
+        if (!std::isfinite(pm->t_fft[i]))
+            return set_error(FH_ERR_INVALID_ARG, "t_fft[%d] not finite", i);
+        if (i > 0 && !(pm->t_fft[i] > pm->t_fft[i - 1]))
+            return set_error(FH_ERR_UNSORTED, "t_fft not strictly increasing at %d", i);
+    }
+    if (pm->offsets[n] != pm->n_peaks)
+        return set_error(FH_ERR_UNSORTED, "offsets[n_fft] = %lld != n_peaks = %lld",
+                         (long long)pm->offsets[n], (long long)pm->n_peaks);
+    double fmin = INFINITY, fmax = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t q = pm->offsets[i]; q < pm->offsets[i + 1]; ++q) {
+            const double f = pm->freq[q];
+            if (!(std::isfinite(f) && f > 0.0))
+                return set_error(FH_ERR_INVALID_ARG, "freq[%lld] must be finite and > 0",
+                                 (long long)q);
+            if (q > pm->offsets[i] && !(f > pm->freq[q - 1]))
+                return set_error(FH_ERR_UNSORTED, "freq not ascending within FFT %d", i);
+            fmin = std::min(fmin, f);
+            fmax = std::max(fmax, f);
+        }
+    }
+    double vmax = 0.0, nmax = 0.0, tmax = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        const double *x = v + 3 * (int64_t)i;
+        if (!(std::isfinite(x[0]) && std::isfinite(x[1]) && std::isfinite(x[2])))
+            return set_error(FH_ERR_INVALID_ARG, "v_over_c[%d] not finite", i);
+        vmax = std::max(vmax, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+        tmax = std::max(tmax, std::fabs(pm->t_fft[i] - d.t_ref));
+    }
+    for (int32_t k = 0; k < n_dir; ++k) {
+        const double *x = sky + 3 * (int64_t)k;
+        if (!(std::isfinite(x[0]) && std::isfinite(x[1]) && std::isfinite(x[2])))
+            return set_error(FH_ERR_INVALID_ARG, "sky_n[%d] not finite", k);
+        const double nn = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (nn > 1.000001) return set_error(FH_ERR_INVALID_ARG, "sky_n[%d] longer than 1", k);
+        nmax = std::max(nmax, nn);
+    }
+    const double vn = vmax * nmax;
+    if (!(vn < 0.1)) return set_error(FH_ERR_INVALID_ARG, "|v.n| must stay below 0.1 (units of c)");
+    const double lim = (double)kFixedLimit * 0.999;
+    if (pm->n_peaks > 0) {
+        const double ulo = fmin / (1.0 + vn), uhi = fmax / (1.0 - vn);
+        const double x = std::max(std::fabs((ulo - d.f0_min) * kt), std::fabs((uhi - d.f0_min) * kt));
+        if (!(x + d.k_over + 2.0 < lim))
+            return set_error(FH_ERR_RANGE, "peak positions exceed 2^28 cells from f0_min");
+    }
+    const double flast = d.fdot_min + (double)(d.n_fdot - 1) * d.fdot_step;
+    const double fabsmax = std::max(std::fabs(d.fdot_min), std::fabs(flast));
+    if (!(fabsmax * tmax * kt < lim))
+        return set_error(FH_ERR_RANGE, "spin-down shifts exceed 2^28 cells");
+    return FH_OK;
+}
+
+}  // namespace fh
+
+extern "C" {
+
+const char *fh_last_error(void) { return g_err; }
+
+const char *fh_version(void) { return "fh-gb300 0.1 (sm_103a)"; }
+
+int64_t fh_plan_device_bytes(const fh_plan_desc *desc)
+{
+    if (!desc || validate_desc(*desc) != FH_OK) return 0;
+    return plan_sizes(*desc).total();
+}
+
+int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
+{
+    if (!desc || !out) return set_error(FH_ERR_INVALID_ARG, "null desc or out");
+    *out = nullptr;
+    int rc = validate_desc(*desc);
+    if (rc) return rc;
+    fh_plan p = new (std::nothrow) fh_plan_s;
+    if (!p) return set_error(FH_ERR_NOMEM, "host allocation failed");
+    p->d = *desc;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
+    p->kt = (double)desc->k_over * desc->t_fft;
+    p->n_sb = (desc->n_f0 + desc->subband_cells - 1) / desc->subband_cells;
+    p->mode = desc->mode == FH_MODE_AUTO ? FH_MODE_START : desc->mode;
+    p->block_warps = desc->block_warps ? desc->block_warps : 32;
+    p->tile_cells = desc->tile_cells ? std::min(desc->tile_cells, desc->n_f0)
+                                     : default_tile(*desc, p->device, p->mode, p->block_warps);
+    if (transform_smem_bytes(p->tile_cells, desc->k_over, p->mode, p->block_warps) >
+        (size_t)max_optin_smem(p->device)) {
+        delete p;
+        return set_error(FH_ERR_INVALID_ARG, "tile_cells too wide for shared memory");
+    }
+    const Sizes s = plan_sizes(*desc);
+    struct {
+        void **ptr;
+        int64_t bytes;
+    } allocs[] = {{(void **)&p->t, s.t},           {(void **)&p->offsets, s.offsets},
+                  {(void **)&p->S0, s.tables},     {(void **)&p->D, s.tables},
+                  {(void **)&p->freq, s.freq},     {(void **)&p->v, s.v},
+                  {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
+                  {(void **)&p->profile, s.profile}, {(void **)&p->cand, s.cand},
+                  {(void **)&p->err, 16}};
+    for (auto &a : allocs) {
+        e = cudaMalloc(a.ptr, (size_t)std::max<int64_t>(a.bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->release();
+            delete p;
+            return set_error(FH_ERR_NOMEM, "cudaMalloc of %lld bytes failed: %s",
+                             (long long)a.bytes, cudaGetErrorString(e));
+        }
+    }
+    e = cudaMallocHost(&p->h_err, 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p->release();
+        delete p;
+        return set_error(FH_ERR_NOMEM, "cudaMallocHost failed");
+    }
+    cudaMemset(p->err, 0, 16);
+    *out = p;
+    return FH_OK;
+}
+
+int fh_destroy_plan(fh_plan p)
+{
+    if (!p) return FH_OK;
+    {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        p->release();
+    }
+    delete p;
+    return FH_OK;
+}
+
+int64_t fh_plan_launches(fh_plan p) { return p ? p->launches : -1; }
+
+int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
+                       const double *sky_n, int32_t n_dir, double *out_r, int64_t *out_A,
+                       void *stream)
+{
+    if (!p || !pm || !sky_n) return set_error(FH_ERR_INVALID_ARG, "null plan, peakmap or sky_n");
+    if (pm->mem_kind != FH_MEM_HOST && pm->mem_kind != FH_MEM_DEVICE)
+        return set_error(FH_ERR_INVALID_ARG, "unknown mem_kind");
+    if (pm->n_fft < 0 || pm->n_fft > p->d.max_fft)
+        return set_error(FH_ERR_INVALID_ARG, "n_fft %d outside [0, max_fft=%d]", pm->n_fft,
+                         p->d.max_fft);
+    if (pm->n_peaks < 0 || pm->n_peaks > p->d.max_peaks)
+        return set_error(FH_ERR_INVALID_ARG, "n_peaks outside [0, max_peaks]");
+    if (n_dir < 1 || n_dir > p->d.max_dir)
+        return set_error(FH_ERR_INVALID_ARG, "n_dir %d outside [1, max_dir=%d]", n_dir,
+                         p->d.max_dir);
+    if (pm->n_fft > 0 && !v_over_c) return set_error(FH_ERR_INVALID_ARG, "null v_over_c");
+    DeviceGuard g(p->device);
+    cudaStream_t s = as_stream(stream);
+    const int32_t n = pm->n_fft;
+    const int64_t np = pm->n_peaks;
+    const double *t_src, *f_src, *v_src, *sky_src;
+    cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    if (pm->mem_kind == FH_MEM_HOST) {
+        int rc = validate_host_inputs(p->d, p->kt, pm, v_over_c, sky_n, n_dir);
+        if (rc) return rc;
+        struct {
+            void *dst;
+            const void *src;
+            size_t bytes;
+        } cp[] = {{p->offsets, pm->offsets, 8 * ((size_t)n + 1)},
+                  {p->t, pm->t_fft, 8 * (size_t)n},
+                  {p->freq, pm->freq, 8 * (size_t)np},
+                  {p->v, v_over_c, 24 * (size_t)n},
+                  {p->sky, sky_n, 24 * (size_t)n_dir}};
+        for (auto &c : cp) {
+            if (c.bytes == 0) continue;
+            e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(H2D inputs)");
+        }
+        t_src = p->t;
+        f_src = p->freq;
+        v_src = p->v;
+        sky_src = p->sky;
+    } else {
+        if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
+            return set_error(FH_ERR_INVALID_ARG, "null device peakmap array");
+        e = launch_sanitize_offsets(pm->offsets, n, np, p->offsets, p->err, s);
+        if (e != cudaSuccess) return cuda_error(e, "sanitize_offsets launch");
+        e = launch_validate_device_inputs(pm->t_fft, pm->freq, p->offsets, v_over_c, sky_n, n,
+                                          n_dir, p->err, s);
+        if (e != cudaSuccess) return cuda_error(e, "validate launch");
+        p->launches += 2;
+        t_src = pm->t_fft;
+        f_src = pm->freq;
+        v_src = v_over_c;
+        sky_src = sky_n;
+    }
+    const fh_plan_desc &d = p->d;
+    e = launch_shift_tables(t_src, n, d.t_ref, p->kt, d.fdot_min, d.fdot_step, d.n_fdot, p->S0,
+                            p->D, p->err, s);
+    if (e != cudaSuccess) return cuda_error(e, "shift_tables launch");
+    e = launch_positions(f_src, p->offsets, v_src, sky_src, n, np, n_dir, d.f0_min, p->kt,
+                         d.k_over, p->A, out_r, p->err, s);
+    if (e != cudaSuccess) return cuda_error(e, "positions launch");
+    p->launches += (n > 0) ? 2 : 0;
+    if (out_A && np > 0) {
+        e = cudaMemcpyAsync(out_A, p->A, 8 * (size_t)np * n_dir, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(out_A)");
+    }
+    p->n_fft = n;
+    p->n_peaks = np;
+    p->n_dir = n_dir;
+    return FH_OK;
+}
+
+static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
+                         int32_t tile, int32_t nwarps, int32_t schedule, cudaStream_t s)
+{
+    const fh_plan_desc &d = p->d;
+    const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps);
+    int rc = prepare_transform(p, p->mode, smem);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(p->profile + (int64_t)dir_begin * d.n_f0, 0,
+                                    sizeof(uint64_t) * (size_t)n_dir * d.n_f0, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(profile)");
+    TransformJob job{};
+    job.A = p->A;
+    job.offsets = p->offsets;
+    job.S0 = p->S0;
+    job.D = p->D;
+    job.profile = p->profile;
+    job.n_peaks = p->n_peaks;
+    job.n_fft = p->n_fft;
+    job.n_f0 = d.n_f0;
+    job.n_fdot = d.n_fdot;
+    job.k_over = d.k_over;
+    job.tile_cells = tile;
+    job.n_slabs = (d.n_fdot + kRows - 1) / kRows;
+    job.n_tiles = (d.n_f0 + tile - 1) / tile;
+    const int64_t per_dir = (int64_t)job.n_slabs * job.n_tiles;
+    int bps = transform_blocks_per_sm(p->mode, nwarps, smem);
+    if (bps < 1) return set_error(FH_ERR_CUDA, "transform kernel cannot be resident");
+    JobTable tbl{};
+    tbl.n_jobs = 1;
+    if (schedule == FH_SCHED_PLAIN) {
+        for (int32_t k = 0; k < n_dir; ++k) {
+            job.dir_begin = dir_begin + k;
+            job.n_dir = 1;
+            job.maps = out_maps ? out_maps + (int64_t)k * d.n_fdot * d.n_f0 : nullptr;
+            job.item_begin = 0;
+            job.n_items = per_dir;
+            tbl.job[0] = job;
+            e = launch_transform(p->mode, tbl, per_dir, (int32_t)per_dir, nwarps, smem, s);
+            if (e != cudaSuccess) return cuda_error(e, "transform launch");
+            ++p->launches;
+        }
+    } else {
+        job.dir_begin = dir_begin;
+        job.n_dir = n_dir;
+        job.maps = out_maps;
+        job.item_begin = 0;
+        job.n_items = per_dir * n_dir;
+        tbl.job[0] = job;
+        const int64_t cap = (int64_t)p->n_sm * bps;
+        const int32_t grid = (int32_t)std::min<int64_t>(job.n_items, cap);
+        e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, s);
+        if (e != cudaSuccess) return cuda_error(e, "transform launch");
+        ++p->launches;
+    }
+    return FH_OK;
+}
+
+int fh_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps, void *stream)
+{
+    if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
+    int rc = check_dirs(p, dir_begin, n_dir);
+    if (rc) return rc;
+    DeviceGuard g(p->device);
+    return run_transform(p, dir_begin, n_dir, out_maps, p->tile_cells, p->block_warps,
+                         p->d.schedule, as_stream(stream));
+}
+
+int fh_copy_profile(fh_plan p, int32_t dir_begin, int32_t n_dir, uint64_t *out, void *stream)
+{
+    if (!p || !out) return set_error(FH_ERR_INVALID_ARG, "null plan or out");
+    int rc = check_dirs(p, dir_begin, n_dir);
+    if (rc) return rc;
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaMemcpyAsync(out, p->profile + (int64_t)dir_begin * p->d.n_f0,
+                                    sizeof(uint64_t) * (size_t)n_dir * p->d.n_f0,
+                                    cudaMemcpyDeviceToDevice, as_stream(stream));
+    return e == cudaSuccess ? FH_OK : cuda_error(e, "cudaMemcpyAsync(profile)");
+}
+
+int fh_sync(fh_plan p, void *stream)
+{
+    if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
+    DeviceGuard g(p->device);
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(p->h_err, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "fh_sync");
+    return device_error_code(*p->h_err);
+}
+
+int fh_select_candidates(fh_plan p, int32_t dir_begin, int32_t n_dir, fh_candidate *out,
+                         int64_t capacity, int64_t *n_out, int32_t out_mem_kind, void *stream)
+{
+    if (!p || !n_out) return set_error(FH_ERR_INVALID_ARG, "null plan or n_out");
+    int rc = check_dirs(p, dir_begin, n_dir);
+    if (rc) return rc;
+    if (out_mem_kind != FH_MEM_HOST && out_mem_kind != FH_MEM_DEVICE)
+        return set_error(FH_ERR_INVALID_ARG, "unknown out_mem_kind");
+    const fh_plan_desc &d = p->d;
+    const int64_t need = (int64_t)n_dir * p->n_sb * d.top_k;
+    *n_out = need;
+    if (capacity < need || !out)
+        return set_error(FH_ERR_CAPACITY, "need %lld candidate slots, capacity %lld",
+                         (long long)need, (long long)capacity);
+    DeviceGuard g(p->device);
+    cudaStream_t s = as_stream(stream);
+    SelectArgs a{};
+    a.profile = p->profile;
+    a.out = out_mem_kind == FH_MEM_DEVICE ? out : p->cand;
+    a.n_f0 = d.n_f0;
+    a.subband_cells = d.subband_cells;
+    a.top_k = d.top_k;
+    a.excl = d.excl_cells;
+    a.sep = d.sep_cells;
+    a.n_thr = d.n_thr;
+    a.n_sb = p->n_sb;
+    a.dir_begin = dir_begin;
+    a.n_dir = n_dir;
+    a.n_fft = p->n_fft;
+    a.f0_min = d.f0_min;
+    a.kt = p->kt;
+    a.fdot_min = d.fdot_min;
+    a.fdot_step = d.fdot_step;
+    a.p0 = d.p0;
+    cudaError_t e = launch_select(a, s);
+    if (e != cudaSuccess) return cuda_error(e, "select launch");
+    ++p->launches;
+    if (out_mem_kind == FH_MEM_DEVICE) return FH_OK;
+    e = cudaMemcpyAsync(out, p->cand, sizeof(fh_candidate) * (size_t)need,
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(candidates)");
+    return fh_sync(p, stream);
+}
+
+int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells,
+                int32_t *block_warps, void *stream)
+{
+    if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
+    int rc = check_dirs(p, dir_begin, n_dir);
+    if (rc) return rc;
+    DeviceGuard g(p->device);
+    cudaStream_t s = as_stream(stream);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int64_t, int, int, int>, std::pair<int, int>> cache;
+    const fh_plan_desc &d = p->d;
+    const auto key = std::make_tuple(d.n_f0, d.n_fdot, d.k_over, p->n_fft, p->n_peaks / 4096,
+                                     n_dir, p->mode, p->device);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            p->tile_cells = it->second.first;
+            p->block_warps = it->second.second;
+            if (tile_cells) *tile_cells = p->tile_cells;
+            if (block_warps) *block_warps = p->block_warps;
+            return FH_OK;
+        }
+    }
+    const int lim = max_optin_smem(p->device);
+    std::vector<std::pair<int, int>> cands;
+    for (int nw : {32, 16}) {
+        const int32_t wmax = default_tile(d, p->device, p->mode, nw);
+        for (int32_t w : {wmax, 1536, 1280, 1024, 768, 512}) {
+            if (w > wmax || w > d.n_f0) continue;
+            if (transform_smem_bytes(w, d.k_over, p->mode, nw) > (size_t)lim) continue;
+            if (std::find(cands.begin(), cands.end(), std::make_pair((int)w, nw)) == cands.end())
+                cands.push_back({w, nw});
+        }
+    }
+    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> pick = cands[0];
+    for (auto &c : cands) {
+        rc = run_transform(p, dir_begin, n_dir, nullptr, c.first, c.second, FH_SCHED_BATCHED, s);
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2 && rc == FH_OK; ++r)
+            rc = run_transform(p, dir_begin, n_dir, nullptr, c.first, c.second, FH_SCHED_BATCHED, s);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    p->tile_cells = pick.first;
+    p->block_warps = pick.second;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = pick;
+    }
+    if (tile_cells) *tile_cells = p->tile_cells;
+    if (block_warps) *block_warps = p->block_warps;
+    return FH_OK;
+}
+
+int fh_bench_smem_atomics(int32_t variant, int32_t iters, double *atomics_per_s, double *ms,
+                          void *stream)
+{
+    if (!atomics_per_s || iters < 1 || variant < 0 || variant > 1)
+        return set_error(FH_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = as_stream(stream);
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    unsigned long long *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(unsigned long long));
+    if (e != cudaSuccess) return set_error(FH_ERR_NOMEM, "cudaMalloc(sink)");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int grid = n_sm * 2;
+    e = launch_smem_atomic_bench(variant, std::max(1, iters / 8), grid, sink, s);  // warm-up
+    cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_smem_atomic_bench(variant, iters, grid, sink, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_error(e, "smem atomic bench");
+    *atomics_per_s = (double)grid * 1024.0 * 8.0 * (double)iters / ((double)t * 1e-3);
+    if (ms) *ms = t;
+    return FH_OK;
+}
+
+}  // extern "C"

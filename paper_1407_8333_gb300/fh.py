@@ -1,0 +1,341 @@
+"""Thin ctypes binding of libfh (``include/fh.h``), same entry-point names.
+
+Argument marshalling only: every step of the frequency-Hough path runs in the
+library's CUDA kernels.  Arrays are passed as raw pointers: numpy arrays (host
+memory, ``FH_MEM_HOST``) or CUDA tensors (device memory, ``FH_MEM_DEVICE``,
+via ``data_ptr()``); streams are ``torch.cuda.Stream`` objects, raw handles or
+None (legacy default stream).  The library must have been built
+(``paper_1407_8333_gb300.build.build()``); loading fails loudly otherwise --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FH_OK = 0
+FH_ERR_INVALID_ARG = -1
+FH_ERR_UNSORTED = -2
+FH_ERR_RANGE = -3
+FH_ERR_NOMEM = -4
+FH_ERR_TOO_LARGE = -5
+FH_ERR_CUDA = -6
+FH_ERR_TIMEOUT = -7
+FH_ERR_NOT_READY = -8
+FH_ERR_CANCELLED = -9
+FH_ERR_BAD_HANDLE = -10
+FH_ERR_CAPACITY = -11
+FH_MEM_HOST, FH_MEM_DEVICE = 0, 1
+FH_MODE_AUTO, FH_MODE_DIFF, FH_MODE_START = 0, 1, 2
+FH_SCHED_BATCHED, FH_SCHED_PLAIN = 0, 1
+FH_JOB_QUEUED, FH_JOB_RUNNING, FH_JOB_DONE, FH_JOB_FAILED, FH_JOB_CANCELLED = 0, 1, 2, 3, 4
+
+_i32, _i64, _f64, _P = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class fh_peakmap(ctypes.Structure):
+    _fields_ = [("n_fft", _i32), ("n_peaks", _i64), ("t_fft", _P), ("offsets", _P),
+                ("freq", _P), ("mem_kind", _i32)]
+
+
+class fh_plan_desc(ctypes.Structure):
+    _fields_ = [("t_fft", _f64), ("k_over", _i32), ("f0_min", _f64), ("n_f0", _i32),
+                ("fdot_min", _f64), ("fdot_step", _f64), ("n_fdot", _i32), ("t_ref", _f64),
+                ("subband_cells", _i32), ("top_k", _i32), ("excl_cells", _i32),
+                ("sep_cells", _i32), ("n_thr", _i32), ("p0", _f64), ("max_fft", _i32),
+                ("max_dir", _i32), ("max_peaks", _i64), ("mode", _i32), ("schedule", _i32),
+                ("tile_cells", _i32), ("block_warps", _i32)]
+
+
+class fh_candidate(ctypes.Structure):
+    _fields_ = [("dir", _i32), ("subband", _i32), ("rank", _i32), ("row", _i32),
+                ("cell", _i32), ("count", _i32), ("f0", _f64), ("fdot", _f64), ("cr", _f64)]
+
+
+CANDIDATE_DTYPE = np.dtype([("dir", "<i4"), ("subband", "<i4"), ("rank", "<i4"),
+                            ("row", "<i4"), ("cell", "<i4"), ("count", "<i4"),
+                            ("f0", "<f8"), ("fdot", "<f8"), ("cr", "<f8")])
+assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(fh_candidate) == 48
+
+
+class fh_job_desc(ctypes.Structure):
+    _fields_ = [("plan", fh_plan_desc), ("peaks", fh_peakmap), ("v_over_c", _P),
+                ("sky_n", _P), ("n_dir", _i32)]
+
+
+class fh_job_stats(ctypes.Structure):
+    _fields_ = [("submit_s", _f64), ("start_s", _f64), ("done_s", _f64), ("updates", _i64),
+                ("device_bytes", _i64), ("batch", _i32), ("batch_jobs", _i32)]
+
+
+class FHError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__("%s failed (%d): %s" % (func, code, msg))
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "fh_create_plan": ([ctypes.POINTER(fh_plan_desc), ctypes.POINTER(_P)], ctypes.c_int),
+    "fh_destroy_plan": ([_P], ctypes.c_int),
+    "fh_plan_device_bytes": ([ctypes.POINTER(fh_plan_desc)], _i64),
+    "fh_correct_doppler": ([_P, ctypes.POINTER(fh_peakmap), _P, _P, _i32, _P, _P, _P], ctypes.c_int),
+    "fh_transform": ([_P, _i32, _i32, _P, _P], ctypes.c_int),
+    "fh_copy_profile": ([_P, _i32, _i32, _P, _P], ctypes.c_int),
+    "fh_select_candidates": ([_P, _i32, _i32, _P, _i64, ctypes.POINTER(_i64), _i32, _P], ctypes.c_int),
+    "fh_sync": ([_P, _P], ctypes.c_int),
+    "fh_autotune": ([_P, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P], ctypes.c_int),
+    "fh_plan_launches": ([_P], _i64),
+    "fh_server_create": ([_i64, _i32, ctypes.POINTER(_P)], ctypes.c_int),
+    "fh_server_destroy": ([_P], ctypes.c_int),
+    "fh_submit": ([_P, ctypes.POINTER(fh_job_desc), ctypes.POINTER(_i64)], ctypes.c_int),
+    "fh_poll": ([_P, _i64, ctypes.POINTER(_i32), _P, _i64, ctypes.POINTER(_i64)], ctypes.c_int),
+    "fh_job_get_stats": ([_P, _i64, ctypes.POINTER(fh_job_stats)], ctypes.c_int),
+    "fh_cancel": ([_P, _i64], ctypes.c_int),
+    "fh_server_drain": ([_P, _f64], ctypes.c_int),
+    "fh_server_pause": ([_P, _i32], ctypes.c_int),
+    "fh_bench_smem_atomics": ([_i32, _i32, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _P], ctypes.c_int),
+    "fh_last_error": ([], ctypes.c_char_p),
+    "fh_version": ([], ctypes.c_char_p),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str = None):
+    """Load libfh.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _build.LIB
+            if not os.path.exists(p):
+                raise RuntimeError("libfh.so not found at %s: build it with "
+                                   "paper_1407_8333_gb300.build.build()" % p)
+            lib = ctypes.CDLL(p)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list:
+    return list(_SIGS.keys())
+
+
+def _check(rc: int, func: str, ok=(FH_OK,)):
+    if rc not in ok:
+        raise FHError(rc, func, load().fh_last_error().decode(errors="replace"))
+    return rc
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(x) -> bool:
+    return hasattr(x, "data_ptr") and hasattr(x, "is_cuda")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _mem_kind(x) -> int:
+    if _is_torch(x):
+        if not x.is_cuda:
+            raise ValueError("CPU tensors are not accepted; pass numpy arrays for host memory")
+        return FH_MEM_DEVICE
+    return FH_MEM_HOST
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def make_desc(params: dict, max_fft: int, max_dir: int, max_peaks: int, mode: int = FH_MODE_AUTO,
+              schedule: int = FH_SCHED_BATCHED, tile_cells: int = 0, block_warps: int = 0) -> fh_plan_desc:
+    d = fh_plan_desc()
+    for k in ("t_fft", "f0_min", "fdot_min", "fdot_step", "t_ref", "p0"):
+        setattr(d, k, float(params[k]))
+    for k in ("k_over", "n_f0", "n_fdot", "subband_cells", "top_k", "excl_cells", "sep_cells",
+              "n_thr"):
+        setattr(d, k, int(params[k]))
+    d.max_fft, d.max_dir, d.max_peaks = int(max_fft), int(max_dir), int(max(1, max_peaks))
+    d.mode, d.schedule = int(mode), int(schedule)
+    d.tile_cells, d.block_warps = int(tile_cells), int(block_warps)
+    return d
+
+
+def make_peakmap(t, offsets, freq, n_peaks: int = None) -> fh_peakmap:
+    kind = _mem_kind(offsets)
+    pm = fh_peakmap()
+    pm.n_fft = int(offsets.shape[0] - 1)
+    pm.n_peaks = int(n_peaks if n_peaks is not None else
+                     (offsets[-1] if kind == FH_MEM_HOST else freq.shape[0]))
+    pm.t_fft = _ptr(t)
+    pm.offsets = _ptr(offsets)
+    pm.freq = _ptr(freq)
+    pm.mem_kind = kind
+    return pm
+
+
+# ---------------------------------------------------------------- entry points
+def fh_version() -> str:
+    return load().fh_version().decode()
+
+
+def fh_last_error() -> str:
+    return load().fh_last_error().decode(errors="replace")
+
+
+def fh_plan_device_bytes(desc: fh_plan_desc) -> int:
+    return int(load().fh_plan_device_bytes(ctypes.byref(desc)))
+
+
+def fh_create_plan(desc: fh_plan_desc) -> ctypes.c_void_p:
+    h = _P()
+    _check(load().fh_create_plan(ctypes.byref(desc), ctypes.byref(h)), "fh_create_plan")
+    return h
+
+
+def fh_destroy_plan(plan) -> None:
+    _check(load().fh_destroy_plan(plan), "fh_destroy_plan")
+
+
+def fh_correct_doppler(plan, t, offsets, freq, v_over_c, sky_n, out_r=None, out_A=None,
+                       stream=None, n_peaks: int = None) -> None:
+    pm = make_peakmap(t, offsets, freq, n_peaks)
+    n_dir = int(sky_n.shape[0])
+    _check(load().fh_correct_doppler(plan, ctypes.byref(pm), _ptr(v_over_c), _ptr(sky_n), n_dir,
+                                     _ptr(out_r), _ptr(out_A), _stream(stream)),
+           "fh_correct_doppler")
+
+
+def fh_transform(plan, dir_begin: int, n_dir: int, out_maps=None, stream=None) -> None:
+    _check(load().fh_transform(plan, int(dir_begin), int(n_dir), _ptr(out_maps), _stream(stream)),
+           "fh_transform")
+
+
+def fh_copy_profile(plan, dir_begin: int, n_dir: int, out, stream=None) -> None:
+    _check(load().fh_copy_profile(plan, int(dir_begin), int(n_dir), _ptr(out), _stream(stream)),
+           "fh_copy_profile")
+
+
+def fh_select_candidates(plan, dir_begin: int, n_dir: int, out=None, stream=None):
+    """Candidate slots; ``out`` = None -> a new numpy structured array (host)."""
+    n = _i64(0)
+    if out is None:
+        load().fh_select_candidates(plan, int(dir_begin), int(n_dir), None, 0, ctypes.byref(n), 0,
+                                    _stream(stream))
+        out = np.zeros(int(n.value), dtype=CANDIDATE_DTYPE)
+    kind = _mem_kind(out)
+    cap = (out.numel() * out.element_size() // 48) if kind == FH_MEM_DEVICE else out.shape[0]
+    _check(load().fh_select_candidates(plan, int(dir_begin), int(n_dir), _ptr(out), int(cap),
+                                       ctypes.byref(n), kind, _stream(stream)),
+           "fh_select_candidates")
+    return out
+
+
+def fh_sync(plan, stream=None) -> None:
+    _check(load().fh_sync(plan, _stream(stream)), "fh_sync")
+
+
+def fh_autotune(plan, dir_begin: int, n_dir: int, stream=None) -> tuple:
+    w, nw = _i32(0), _i32(0)
+    _check(load().fh_autotune(plan, int(dir_begin), int(n_dir), ctypes.byref(w), ctypes.byref(nw),
+                              _stream(stream)), "fh_autotune")
+    return int(w.value), int(nw.value)
+
+
+def fh_plan_launches(plan) -> int:
+    return int(load().fh_plan_launches(plan))
+
+
+def fh_bench_smem_atomics(variant: int = 0, iters: int = 4096, stream=None) -> tuple:
+    r, ms = _f64(0), _f64(0)
+    _check(load().fh_bench_smem_atomics(int(variant), int(iters), ctypes.byref(r), ctypes.byref(ms),
+                                        _stream(stream)), "fh_bench_smem_atomics")
+    return float(r.value), float(ms.value)
+
+
+# ---- serving
+def fh_server_create(device_mem_budget: int, max_inflight: int = 4):
+    h = _P()
+    _check(load().fh_server_create(int(device_mem_budget), int(max_inflight), ctypes.byref(h)),
+           "fh_server_create")
+    return h
+
+
+def fh_server_destroy(server) -> None:
+    _check(load().fh_server_destroy(server), "fh_server_destroy")
+
+
+def fh_submit(server, params: dict, t, offsets, freq, v_over_c, sky_n, mode: int = FH_MODE_AUTO,
+              tile_cells: int = 0) -> int:
+    jd = fh_job_desc()
+    jd.plan = make_desc(params, 1, 1, 1, mode=mode, tile_cells=tile_cells)
+    jd.peaks = make_peakmap(t, offsets, freq)
+    jd.v_over_c = _ptr(v_over_c)
+    jd.sky_n = _ptr(sky_n)
+    jd.n_dir = int(sky_n.shape[0])
+    jid = _i64(0)
+    _check(load().fh_submit(server, ctypes.byref(jd), ctypes.byref(jid)), "fh_submit")
+    return int(jid.value)
+
+
+def fh_poll(server, job_id: int, out: np.ndarray = None):
+    """(state, candidates or None).  Raises on a failed job."""
+    st = _i32(0)
+    n = _i64(0)
+    cap = 0 if out is None else out.shape[0]
+    rc = load().fh_poll(server, int(job_id), ctypes.byref(st), _ptr(out), cap, ctypes.byref(n))
+    if rc == FH_ERR_NOT_READY:
+        return int(st.value), None
+    if rc == FH_ERR_CAPACITY and out is None:
+        out = np.zeros(int(n.value), dtype=CANDIDATE_DTYPE)
+        rc = load().fh_poll(server, int(job_id), ctypes.byref(st), _ptr(out), out.shape[0],
+                            ctypes.byref(n))
+    _check(rc, "fh_poll")
+    return int(st.value), out
+
+
+def fh_job_get_stats(server, job_id: int) -> dict:
+    s = fh_job_stats()
+    _check(load().fh_job_get_stats(server, int(job_id), ctypes.byref(s)), "fh_job_get_stats")
+    return {k: getattr(s, k) for k, _ in fh_job_stats._fields_}
+
+
+def fh_cancel(server, job_id: int) -> None:
+    _check(load().fh_cancel(server, int(job_id)), "fh_cancel")
+
+
+def fh_server_drain(server, timeout_s: float) -> None:
+    _check(load().fh_server_drain(server, float(timeout_s)), "fh_server_drain")
+
+
+def fh_server_pause(server, paused: bool) -> None:
+    _check(load().fh_server_pause(server, int(bool(paused))), "fh_server_pause")
