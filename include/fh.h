@@ -213,6 +213,34 @@ int fh_autotune(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *tile_ce
  * plan creation). */
 int64_t fh_plan_launches(fh_plan plan);
 
+/* ---- allocation-free search (one direction) ------------------------------ */
+
+/* fh_search_static: steps a1-a6 for ONE sky direction, like fh_correct_doppler
+ * + fh_transform + fh_select_candidates on a plan, but without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate while they run -- an application that has
+ * reserved the GPU's memory for its own pool, or a loop that must not take the
+ * device-wide synchronisation a cudaMalloc/cudaFree can cause.  Its working
+ * memory (CSR copy, shift tables, positions, profile, error word; 20,447,744
+ * bytes, 19.5 MiB) is one fixed-size __device__ array in the library, held by every
+ * GPU that loads this part of the library until the process exits.
+ *   desc          grids and selection as for fh_create_plan (max_* ignored)
+ *   pm            peakmap in DEVICE memory; at most 65,536 FFTs and 2,097,152
+ *                 peaks; desc->n_f0 at most 262,144 cells -- larger inputs are
+ *                 rejected with FH_ERR_TOO_LARGE before anything is enqueued
+ *   v_over_c      device, pm->n_fft x 3; sky_n device, 1 x 3
+ *   out           device, n_sb x top_k candidate slots (capacity >= *n_out)
+ *   device_status nullable device int32: receives the device-side input
+ *                 checks (0 = inputs valid) when the enqueued work completes
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * reuses the same array, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race: serialise them, e.g. on one
+ * stream.  Calls only enqueue work; nothing is allocated, nothing is freed. */
+int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const double *v_over_c,
+                     const double *sky_n, fh_candidate *out, int64_t capacity, int64_t *n_out,
+                     int32_t *device_status, void *stream);
+
 /* ---- serving (continuous batching) --------------------------------------- */
 
 enum { FH_JOB_QUEUED = 0, FH_JOB_RUNNING = 1, FH_JOB_DONE = 2, FH_JOB_FAILED = 3,

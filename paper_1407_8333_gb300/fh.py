@@ -101,6 +101,8 @@ _SIGS = {
     "fh_cancel": ([_P, _i64], ctypes.c_int),
     "fh_server_drain": ([_P, _f64], ctypes.c_int),
     "fh_server_pause": ([_P, _i32], ctypes.c_int),
+    "fh_search_static": ([ctypes.POINTER(fh_plan_desc), ctypes.POINTER(fh_peakmap), _P, _P, _P, _i64,
+                          ctypes.POINTER(_i64), _P, _P], ctypes.c_int),
     "fh_bench_smem_atomics": ([_i32, _i32, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _P], ctypes.c_int),
     "fh_last_error": ([], ctypes.c_char_p),
     "fh_version": ([], ctypes.c_char_p),
@@ -280,6 +282,20 @@ def fh_bench_smem_atomics(variant: int = 0, iters: int = 4096, stream=None) -> t
     _check(load().fh_bench_smem_atomics(int(variant), int(iters), ctypes.byref(r), ctypes.byref(ms),
                                         _stream(stream)), "fh_bench_smem_atomics")
     return float(r.value), float(ms.value)
+
+
+def fh_search_static(params: dict, t, offsets, freq, v_over_c, sky_n, out, device_status=None,
+                     stream=None, mode: int = FH_MODE_AUTO, tile_cells: int = 0,
+                     block_warps: int = 0) -> int:
+    """One direction, no device allocation; all arrays are CUDA tensors.  Returns n_out."""
+    desc = make_desc(params, 1, 1, 1, mode=mode, tile_cells=tile_cells, block_warps=block_warps)
+    pm = make_peakmap(t, offsets, freq, n_peaks=int(freq.shape[0]))
+    n = _i64(0)
+    cap = out.numel() * out.element_size() // 48
+    _check(load().fh_search_static(ctypes.byref(desc), ctypes.byref(pm), _ptr(v_over_c), _ptr(sky_n),
+                                   _ptr(out), int(cap), ctypes.byref(n), _ptr(device_status),
+                                   _stream(stream)), "fh_search_static")
+    return int(n.value)
 
 
 # ---- serving
