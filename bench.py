@@ -195,10 +195,13 @@ def run_ours(args):
         if ev:
             ev[3].record(stream)
 
+    nvtx = torch.cuda.nvtx
+    nvtx.range_push("warmup")
     for _ in range(max(3, args.warmup)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    nvtx.range_pop()
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -208,10 +211,12 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
+    nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     launches = fh.fh_plan_launches(plan) - l0

@@ -221,9 +221,10 @@ int64_t fh_plan_launches(fh_plan plan);
  * callers that cannot allocate while they run -- an application that has
  * reserved the GPU's memory for its own pool, or a loop that must not take the
  * device-wide synchronisation a cudaMalloc/cudaFree can cause.  Its working
- * memory (CSR copy, shift tables, positions, profile, error word; 20,447,744
- * bytes, 19.5 MiB) is one fixed-size __device__ array in the library, held by every
- * GPU that loads this part of the library until the process exits.
+ * memory (CSR copy, shift tables, positions, profile, error and drift words;
+ * 20,448,000 bytes, 19.5 MiB) is one fixed-size __device__ array in the
+ * library, held by every GPU that loads this part of the library until the
+ * process exits.
  *   desc          grids and selection as for fh_create_plan (max_* ignored)
  *   pm            peakmap in DEVICE memory; at most 65,536 FFTs and 2,097,152
  *                 peaks; desc->n_f0 at most 262,144 cells -- larger inputs are

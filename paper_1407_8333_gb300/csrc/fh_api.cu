@@ -76,15 +76,31 @@ int max_optin_smem(int device)
 }
 
 // largest multiple-of-32 tile width whose counters fit the per-block limit
-int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nwarps)
+int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nwarps, int32_t guard)
 {
     const size_t lim = (size_t)max_optin_smem(device);
-    int32_t w = (int32_t)(lim / (kRows * sizeof(int32_t))) - d.k_over + 1;
-    if (mode == FH_MODE_DIFF) w -= nwarps;
-    w = (w / 32) * 32;
-    if (w < 32) w = 32;
+    int32_t w = 32;
+    for (int32_t t = 32; t <= 8192; t += 32) {
+        if (transform_smem_bytes(t, d.k_over, mode, nwarps, guard) > lim) break;
+        w = t;
+    }
     if (w > d.n_f0) w = d.n_f0;
     return w;
+}
+
+int32_t default_guard(const fh_plan_desc &d)
+{
+    const double cells = 0.5 * d.k_over + 0.25;
+    return guard_for((unsigned long long)(cells * 4294967296.0));
+}
+
+// guard for host-memory FFT times: the largest |D_i| in 32.32 cells per row
+int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft)
+{
+    double m = 0.0;
+    for (int32_t i = 0; i < n_fft; ++i)
+        m = std::max(m, std::fabs(d.fdot_step * ((t[i] - d.t_ref) * kt)));
+    return guard_for((unsigned long long)(m * 4294967296.0) + 4);
 }
 
 int validate_desc(const fh_plan_desc &d)
@@ -125,12 +141,18 @@ int validate_desc(const fh_plan_desc &d)
 namespace {
 
 struct Sizes {
-    int64_t t, offsets, tables, freq, v, sky, A, profile, cand;
+    int64_t t, offsets, tables, freq, v, sky, A, profile, cand, bidx;
     int64_t total() const
     {
-        return t + offsets + 2 * tables + freq + v + sky + A + profile + cand + 256;
+        return t + offsets + 2 * tables + freq + v + sky + A + profile + cand + bidx + 256;
     }
 };
+
+BucketIndex plan_buckets(const fh_plan_desc &d)
+{
+    const double cpp = ((double)d.n_f0 + 2.0 * d.k_over) * (double)d.max_fft / (double)d.max_peaks;
+    return bucket_geometry(d.n_f0, d.k_over, cpp);
+}
 
 Sizes plan_sizes(const fh_plan_desc &d)
 {
@@ -145,6 +167,7 @@ Sizes plan_sizes(const fh_plan_desc &d)
     s.A = 8 * (int64_t)d.max_dir * d.max_peaks;
     s.profile = 8 * (int64_t)d.max_dir * d.n_f0;
     s.cand = (int64_t)sizeof(fh_candidate) * d.max_dir * n_sb * d.top_k;
+    s.bidx = 4 * (int64_t)d.max_dir * d.max_fft * plan_buckets(d).nb;
     return s;
 }
 
@@ -165,6 +188,9 @@ struct fh_plan_s {
     fh_candidate *cand = nullptr;
     int32_t *err = nullptr;
     int32_t *h_err = nullptr;  // pinned
+    unsigned long long *dmax = nullptr;  // largest |D_i| of the current peakmap
+    int32_t guard = 0;                   // guard cells for the transform's fast path
+    BucketIndex bix;                     // bix.idx: [max_dir][max_fft][nb]
     int32_t n_fft = -1;
     int64_t n_peaks = 0;
     int32_t n_dir = 0;
@@ -173,7 +199,7 @@ struct fh_plan_s {
 
     void release()
     {
-        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err};
+        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, bix.idx, dmax};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -182,6 +208,8 @@ struct fh_plan_s {
         profile = nullptr;
         cand = nullptr;
         err = h_err = nullptr;
+        bix.idx = nullptr;
+        dmax = nullptr;
     }
 };
 
@@ -307,14 +335,22 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
     p->n_sb = (desc->n_f0 + desc->subband_cells - 1) / desc->subband_cells;
     p->mode = desc->mode == FH_MODE_AUTO ? FH_MODE_START : desc->mode;
     p->block_warps = desc->block_warps ? desc->block_warps : 32;
+    p->guard = default_guard(*desc);
     p->tile_cells = desc->tile_cells ? std::min(desc->tile_cells, desc->n_f0)
-                                     : default_tile(*desc, p->device, p->mode, p->block_warps);
-    if (transform_smem_bytes(p->tile_cells, desc->k_over, p->mode, p->block_warps) >
+                                     : default_tile(*desc, p->device, p->mode, p->block_warps,
+                                                    p->guard);
+    if (transform_smem_bytes(p->tile_cells, desc->k_over, p->mode, p->block_warps, p->guard) >
         (size_t)max_optin_smem(p->device)) {
         delete p;
         return set_error(FH_ERR_INVALID_ARG, "tile_cells too wide for shared memory");
     }
     const Sizes s = plan_sizes(*desc);
+    {
+        const BucketIndex g = plan_buckets(*desc);
+        p->bix.base = g.base;
+        p->bix.gsh = g.gsh;
+        p->bix.nb = g.nb;
+    }
     struct {
         void **ptr;
         int64_t bytes;
@@ -323,7 +359,8 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                   {(void **)&p->freq, s.freq},     {(void **)&p->v, s.v},
                   {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
                   {(void **)&p->profile, s.profile}, {(void **)&p->cand, s.cand},
-                  {(void **)&p->err, 16}};
+                  {(void **)&p->err, 16},          {(void **)&p->bix.idx, s.bidx},
+                  {(void **)&p->dmax, 16}};
     for (auto &a : allocs) {
         e = cudaMalloc(a.ptr, (size_t)std::max<int64_t>(a.bytes, 16));
         if (e != cudaSuccess) {
@@ -382,10 +419,12 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     const int64_t np = pm->n_peaks;
     const double *t_src, *f_src, *v_src, *sky_src;
     cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->dmax, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
     if (pm->mem_kind == FH_MEM_HOST) {
         int rc = validate_host_inputs(p->d, p->kt, pm, v_over_c, sky_n, n_dir);
         if (rc) return rc;
+        p->guard = std::max(default_guard(p->d), host_guard(p->d, p->kt, pm->t_fft, n));
         struct {
             void *dst;
             const void *src;
@@ -420,10 +459,10 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     }
     const fh_plan_desc &d = p->d;
     e = launch_shift_tables(t_src, n, d.t_ref, p->kt, d.fdot_min, d.fdot_step, d.n_fdot, p->S0,
-                            p->D, p->err, s);
+                            p->D, p->dmax, p->err, s);
     if (e != cudaSuccess) return cuda_error(e, "shift_tables launch");
     e = launch_positions(f_src, p->offsets, v_src, sky_src, n, np, n_dir, d.f0_min, p->kt,
-                         d.k_over, p->A, out_r, p->err, s);
+                         d.k_over, p->A, out_r, p->err, p->bix, s);
     if (e != cudaSuccess) return cuda_error(e, "positions launch");
     p->launches += (n > 0) ? 2 : 0;
     if (out_A && np > 0) {
@@ -440,7 +479,11 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
                          int32_t tile, int32_t nwarps, int32_t schedule, cudaStream_t s)
 {
     const fh_plan_desc &d = p->d;
-    const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps);
+    // keep the tile's counters within shared memory with this plan's guard cells
+    const int32_t guard = p->guard;
+    const int32_t wmax = default_tile(d, p->device, p->mode, nwarps, guard);
+    if (tile > wmax) tile = wmax;
+    const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps, guard);
     int rc = prepare_transform(p, p->mode, smem);
     if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(p->profile + (int64_t)dir_begin * d.n_f0, 0,
@@ -452,6 +495,11 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.S0 = p->S0;
     job.D = p->D;
     job.profile = p->profile;
+    job.bidx = p->bix.idx;
+    job.dmax = p->dmax;
+    job.bbase = p->bix.base;
+    job.bgsh = p->bix.gsh;
+    job.bnb = p->bix.nb;
     job.n_peaks = p->n_peaks;
     job.n_fft = p->n_fft;
     job.n_f0 = d.n_f0;
@@ -473,7 +521,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
             job.item_begin = 0;
             job.n_items = per_dir;
             tbl.job[0] = job;
-            e = launch_transform(p->mode, tbl, per_dir, (int32_t)per_dir, nwarps, smem, s);
+            e = launch_transform(p->mode, tbl, per_dir, (int32_t)per_dir, nwarps, smem, guard, s);
             if (e != cudaSuccess) return cuda_error(e, "transform launch");
             ++p->launches;
         }
@@ -486,7 +534,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
         tbl.job[0] = job;
         const int64_t cap = (int64_t)p->n_sm * bps;
         const int32_t grid = (int32_t)std::min<int64_t>(job.n_items, cap);
-        e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, s);
+        e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, guard, s);
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
         ++p->launches;
     }
@@ -597,10 +645,10 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     const int lim = max_optin_smem(p->device);
     std::vector<std::pair<int, int>> cands;
     for (int nw : {32, 16}) {
-        const int32_t wmax = default_tile(d, p->device, p->mode, nw);
+        const int32_t wmax = default_tile(d, p->device, p->mode, nw, p->guard);
         for (int32_t w : {wmax, 1536, 1280, 1024, 768, 512}) {
             if (w > wmax || w > d.n_f0) continue;
-            if (transform_smem_bytes(w, d.k_over, p->mode, nw) > (size_t)lim) continue;
+            if (transform_smem_bytes(w, d.k_over, p->mode, nw, p->guard) > (size_t)lim) continue;
             if (std::find(cands.begin(), cands.end(), std::make_pair((int)w, nw)) == cands.end())
                 cands.push_back({w, nw});
         }

@@ -21,6 +21,21 @@ constexpr int64_t kFixedLimit = int64_t(1) << 28;  // |cells| bound for 32.32 fi
 // error bits written by the device-side input checks
 enum : int32_t { kErrUnsorted = 1, kErrRange = 2, kErrInvalid = 4, kErrCsr = 8 };
 
+// Per-direction coarse index of each FFT's (ascending) positions: for bucket
+// g, the first peak of the FFT (counted from the FFT's first peak) whose cell
+// floor(A / 2^32) is >= base + g * 2^gsh.  It turns the transform's search
+// for the first relevant peak of an FFT into one load and a short scan.
+struct BucketIndex {
+    int32_t *idx = nullptr;  // [dir][n_fft][nb]; nullptr = no index (binary search)
+    int32_t base = 0;        // cell of bucket 0's lower edge
+    int32_t gsh = 8;         // log2 of the bucket width in cells
+    int32_t nb = 0;          // buckets per FFT
+};
+
+// bucket geometry for a map of n_f0 cells, K, and about cells_per_peak cells
+// between consecutive peaks of one FFT
+BucketIndex bucket_geometry(int32_t n_f0, int32_t k_over, double cells_per_peak);
+
 // One direction set of one plan, as the transform kernel sees it.
 struct TransformJob {
     const int64_t *A;        // positions, [dir][n_peaks] (absolute directions)
@@ -29,6 +44,9 @@ struct TransformJob {
     const int64_t *D;        // n_fft
     uint64_t *profile;       // [dir][n_f0] (absolute directions)
     int32_t *maps;           // nullable, [dir - dir_begin][n_fdot][n_f0]
+    const int32_t *bidx;     // nullable bucket index [dir][n_fft][bnb]
+    const unsigned long long *dmax;  // max_i |D_i| (32.32 cells per row), from a3
+    int32_t bbase, bgsh, bnb;
     int64_t n_peaks;
     int64_t item_begin;      // first work item of this job in the launch
     int64_t n_items;         // n_dir * n_slabs * n_tiles
@@ -54,22 +72,30 @@ struct SelectArgs {
 // ---- launchers (fh_kernels.cu); all return cudaGetLastError() ----
 cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
                                 double fdot_min, double fdot_step, int32_t n_fdot,
-                                int64_t *S0, int64_t *D, int32_t *err, cudaStream_t s);
+                                int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,
+                                cudaStream_t s);
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, cudaStream_t s);
+                             double *out_r, int32_t *err, const BucketIndex &bix, cudaStream_t s);
 cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
                                     int64_t *out, int32_t *err, cudaStream_t s);
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
                                           const int64_t *offsets, const double *v,
                                           const double *sky, int32_t n_fft, int32_t n_dir,
                                           int32_t *err, cudaStream_t s);
+// Guard cells kept below and above a tile so that, in the fast path, no
+// update of a slab needs a bounds clamp: enough for a drift of 31 rows x
+// max|D| cells.  guard_for(dmax) is what a job needs; a launch allocates one
+// guard for all its jobs and jobs needing more take the clamped path.
+__host__ __device__ int32_t guard_for(unsigned long long dmax);
 // smem bytes the transform needs for tile width W (and mode)
-size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, int32_t nwarps);
+size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, int32_t nwarps,
+                            int32_t guard);
 cudaError_t transform_prepare(int32_t mode, size_t smem);  // opt-in dynamic smem
 cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_items,
-                             int32_t grid, int32_t nwarps, size_t smem, cudaStream_t s);
+                             int32_t grid, int32_t nwarps, size_t smem, int32_t guard,
+                             cudaStream_t s);
 int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem);
 cudaError_t launch_select(const SelectArgs &a, cudaStream_t s);
 cudaError_t launch_smem_atomic_bench(int32_t variant, int32_t iters, int32_t grid,
@@ -79,7 +105,13 @@ cudaError_t launch_smem_atomic_bench(int32_t variant, int32_t iters, int32_t gri
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
 int max_optin_smem(int device);
-int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nwarps);
+int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nwarps,
+                     int32_t guard);
+// guard for a plan when the FFT times are not known on the host: the drift of
+// a grid with fdot_step = 1/(T_FFT T_obs) over +-T_obs/2 is K/2 cells per row
+int32_t default_guard(const fh_plan_desc &d);
+// guard for FFT start times held in host memory (exact drift of the grid)
+int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft);
 int validate_desc(const fh_plan_desc &d);
 // host-memory inputs: CSR, ordering, finiteness and the 32.32 fixed-point range
 int validate_host_inputs(const fh_plan_desc &d, double kt, const fh_peakmap *pm, const double *v,

@@ -12,6 +12,7 @@
 // After the fixed-point conversion the path is integer only.
 #include <climits>
 #include <cstdint>
+#include <utility>
 
 #include "fh_internal.h"
 
@@ -26,12 +27,15 @@ constexpr int kPosThreads = 256;
 // ---------------------------------------------------------------- a1 + a2
 // grid (ceil(n_fft / 64), n_dir): the block computes r = 1 / (1 + v.n) for 64
 // FFTs of one direction, then the fixed-point position of each of their peaks
-// (a contiguous CSR range, so loads and stores are coalesced).
+// (a contiguous CSR range, so loads and stores are coalesced), then -- if an
+// index is wanted -- the bucket index of those 64 FFTs from the positions it
+// has just written (still in L1/L2).
 __global__ void __launch_bounds__(kPosThreads)
 positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
                  int64_t n_peaks, double f0_min, double kt, double cshift,
-                 int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err)
+                 int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
+                 BucketIndex bix)
 {
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
@@ -68,23 +72,60 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
         Ad[p] = (int64_t)floor(__dmul_rn(a, kTwo32));
     }
     if (bad) atomicOr(err, kErrRange);
+    if (bix.idx == nullptr) return;
+    __syncthreads();
+    // bucket index: peak k of an FFT is the first of buckets (g_{k-1}, g_k]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = bix.nb;
+    for (int f = warp; f < nf; f += nw) {
+        const int64_t o0 = off_s[f];
+        const int n = (int)(off_s[f + 1] - o0);
+        int32_t *row = bix.idx + ((int64_t)d * n_fft + (i0 + f)) * nb;
+        int glast = -1;  // bucket of the last peak seen so far (warp-uniform)
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            int gk = -1;
+            if (k < n) {
+                const int c = (int)(Ad[o0 + k] >> 32);
+                gk = (c - bix.base) >> bix.gsh;
+                gk = gk < -1 ? -1 : (gk > nb - 1 ? nb - 1 : gk);
+            }
+            int gp = __shfl_up_sync(kFull, gk, 1);
+            if (lane == 0) gp = glast;
+            if (k < n)
+                for (int g = (gp + 1 > 0 ? gp + 1 : 0); g <= gk; ++g) row[g] = k;
+            const int last = min(31, n - 1 - k0);
+            glast = __shfl_sync(kFull, gk, last);
+        }
+        for (int g = (glast + 1 > 0 ? glast + 1 : 0) + lane; g < nb; g += 32) row[g] = n;
+    }
 }
 
 // ---------------------------------------------------------------- a3
 __global__ void shift_tables_kernel(const double *__restrict__ t, int32_t n_fft, double t_ref,
                                     double kt, double fdot_min, double fdot_step,
                                     double fdot_absmax, int64_t *__restrict__ S0,
-                                    int64_t *__restrict__ D, int32_t *err)
+                                    int64_t *__restrict__ D, unsigned long long *dmax, int32_t *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_fft) return;
-    const double dt = __dsub_rn(t[i], t_ref);
-    const double c = __dmul_rn(dt, kt);
-    const double s0 = __dmul_rn(fdot_min, c);
-    const double dd = __dmul_rn(fdot_step, c);
-    if (!(fabs(c) * fdot_absmax < (double)kFixedLimit)) atomicOr(err, kErrRange);
-    S0[i] = (int64_t)floor(__dmul_rn(s0, kTwo32));
-    D[i] = (int64_t)floor(__dmul_rn(dd, kTwo32));
+    unsigned long long amax = 0;
+    if (i < n_fft) {
+        const double dt = __dsub_rn(t[i], t_ref);
+        const double c = __dmul_rn(dt, kt);
+        const double s0 = __dmul_rn(fdot_min, c);
+        const double dd = __dmul_rn(fdot_step, c);
+        if (!(fabs(c) * fdot_absmax < (double)kFixedLimit)) atomicOr(err, kErrRange);
+        S0[i] = (int64_t)floor(__dmul_rn(s0, kTwo32));
+        const int64_t Di = (int64_t)floor(__dmul_rn(dd, kTwo32));
+        D[i] = Di;
+        amax = (unsigned long long)(Di < 0 ? -Di : Di);
+    }
+    // largest per-row drift, for the transform's guard cells
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(kFull, amax, o);
+        amax = y > amax ? y : amax;
+    }
+    if ((threadIdx.x & 31) == 0 && amax) atomicMax(dmax, amax);
 }
 
 // ---------------------------------------------------------------- device inputs
@@ -163,33 +204,171 @@ __global__ void validate_device_inputs_kernel(const double *__restrict__ t,
 }
 
 // ---------------------------------------------------------------- a4 + a5 + profile
+// First position >= X among the peaks [q_from, o1) of an FFT whose peaks are
+// [o0, o1) (ascending): one bucket-index load (entries count from o0) and a
+// forward scan four positions at a time, or a binary search when the plan keeps
+// no index.  For any input the result stays inside [q_from, o1].
+__device__ __forceinline__ int64_t first_at_least(const int64_t *__restrict__ Ad,
+                                                  const int32_t *__restrict__ brow, int32_t bbase,
+                                                  int32_t bgsh, int32_t bnb, int64_t o0,
+                                                  int64_t q_from, int64_t o1, int64_t X)
+{
+    int64_t q = q_from;
+    if (brow != nullptr) {
+        const int c = (int)(X >> 32);
+        int g = (c - bbase) >> bgsh;
+        if (g >= 0) {
+            if (g > bnb - 1) g = bnb - 1;
+            int32_t r = brow[g];
+            const int32_t n = (int32_t)(o1 - o0);
+            r = r < 0 ? 0 : (r > n ? n : r);
+            if (o0 + r > q) q = o0 + r;
+        }
+        for (;;) {
+            const int64_t a0 = q < o1 ? __ldg(Ad + q) : LLONG_MAX;
+            const int64_t a1 = q + 1 < o1 ? __ldg(Ad + q + 1) : LLONG_MAX;
+            const int64_t a2 = q + 2 < o1 ? __ldg(Ad + q + 2) : LLONG_MAX;
+            const int64_t a3 = q + 3 < o1 ? __ldg(Ad + q + 3) : LLONG_MAX;
+            const int k = (a0 < X) + (a1 < X) + (a2 < X) + (a3 < X);
+            q += k;
+            if (k < 4) break;
+        }
+        return q;
+    }
+    int64_t b = o1;
+    while (q < b) {
+        const int64_t m = (q + b) >> 1;
+        if (__ldg(Ad + m) < X) q = m + 1; else b = m;
+    }
+    return q;
+}
+
+// Adds the 32 row updates of one peak.  The lane visits rows lane ^ g(t),
+// g(t) = t ^ (t >> 1) (Gray code): for every step t the 32 lanes of the warp
+// visit 32 different rows, i.e. 32 different banks, and consecutive rows of
+// one lane differ in one bit b, so X moves by +-2^b D, with the sign fixed by
+// the lane's bit b and by g(t) (a compile-time constant).
+//   X    = A - shift of row `lane` - tile origin, 32.32 fixed point
+//   e[b] = +-(D << b), sign + when the lane's bit b is set
+// An update whose cell falls outside the tile goes to the dump cell E (never
+// read), so every step issues its atomic unconditionally -- no branch.
+__host__ __device__ constexpr int ctz5(int x)
+{
+    return (x & 1) ? 0 : (x & 2) ? 1 : (x & 4) ? 2 : (x & 8) ? 3 : 4;
+}
+
+// Step T of one peak's 32 row updates.  The lane visits row lane ^ g(T),
+// g(T) = T ^ (T >> 1) (a Gray code; T, g(T), the bit b that flips next and its
+// sign are compile-time constants): for every step the 32 lanes of a warp
+// visit 32 different rows, i.e. 32 different banks of the [cell][row]
+// counters, and from one step to the next the lane's row changes in bit b
+// only, so X moves by e[b] = +-(D << b) (sign + when the lane's bit b is set,
+// applied with the compile-time sign of the flip).
+//   X      A - shift of the lane's current row - tile origin, 32.32 fixed point
+//   rbase  shared address of (cell 0, row `lane`); cell 0 is 128-byte aligned
+//   stride bytes per cell (128), a run-time value
+// CLAMP = false: the caller guarantees every cell of the 32 rows lies inside
+// the guard cells around the tile, so the atomic needs no bounds clamp.
+// CLAMP = true: cells outside [0, E) go to the dump cell E (never read).
+template <bool CLAMP, int T>
+__device__ __forceinline__ void start_step(uint32_t rbase, int64_t &X, const int64_t (&e)[5],
+                                           uint32_t stride, uint32_t E)
+{
+    constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
+    const uint32_t rb = rbase ^ (gt << 2);
+    uint32_t cell = (uint32_t)(int32_t)(X >> 32);
+    if (CLAMP) cell = min(cell, E);
+    const uint32_t addr = cell * stride + rb;
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+    if constexpr (T < 31) {
+        constexpr int b = ctz5(T + 1);
+        if constexpr ((gt >> b) & 1) X -= e[b]; else X += e[b];
+    }
+}
+
+// DIFF mode (+1 at the first covered cell of the tile, -1 after the stripe)
+// always clamps: the differential form itself cuts stripes at the tile edges.
+template <int T>
+__device__ __forceinline__ void diff_step(int32_t *H0, int lane, int64_t &X, const int64_t (&e)[5],
+                                          int E, int Wt, int K)
+{
+    constexpr int gt = T ^ (T >> 1);
+    const int row = lane ^ gt;
+    const int L = (int)(X >> 32);
+    const bool in = (unsigned)L < (unsigned)E;
+    const int st = in ? max(L - K + 1, 0) : E;
+    const int en = (in && L + 1 < Wt) ? L + 1 : E;
+    atomicAdd(&H0[st * kRows + row], 1);
+    atomicAdd(&H0[en * kRows + row], -1);
+    if constexpr (T < 31) {
+        constexpr int b = ctz5(T + 1);
+        if constexpr ((gt >> b) & 1) X -= e[b]; else X += e[b];
+    }
+}
+
+template <bool CLAMP, int... Ts>
+__device__ __forceinline__ void start_steps(std::integer_sequence<int, Ts...>, uint32_t rbase,
+                                            int64_t X, const int64_t (&e)[5], uint32_t stride,
+                                            uint32_t E)
+{
+    (start_step<CLAMP, Ts>(rbase, X, e, stride, E), ...);
+}
+
+template <int... Ts>
+__device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, int32_t *H0, int lane,
+                                           int64_t X, const int64_t (&e)[5], int E, int Wt, int K)
+{
+    (diff_step<Ts>(H0, lane, X, e, E, Wt, K), ...);
+}
+
 // One block per work item (direction, slab of 32 spin-down rows, tile of W
 // frequency cells); a persistent grid strides over the items of all jobs.
 //
 // Shared memory holds the tile's counters H[L][row], L = s - (b0 - K + 1) for
 // a stripe starting at cell s (so L in [0, W + K - 1) covers every stripe that
-// touches the tile), row stride 32 words: lane l <-> row j0 + l <-> bank l.
+// touches the tile), row stride 32 words: row r lives in bank r.
 //
-// Accumulate: each warp takes 32 FFTs at a time.  Lane i binary-searches FFT
-// i's (ascending) positions for the first peak that can reach the tile on any
-// row of the slab; then, FFT by FFT, the warp loads 32 positions at once and,
-// for each peak, every lane adds its own row's +1 (START: one atomic at the
-// stripe start; DIFF: +1 at the first covered cell and -1 after the last).
-// All 32 atomics of one instruction go to 32 different banks.
+// Accumulate: each warp takes 32 FFTs at a time (lane <-> FFT) and finds, per
+// FFT, the peaks that can reach the tile on some row of the slab (bucket index
+// + short scan).  The peaks of the 32 FFTs are then dealt out to the lanes in
+// rounds of 32 (a warp scan of the per-FFT counts; each lane finds the FFT
+// owning its peak from the round's start bits), the next round's positions
+// are loaded while the current round is added, and every lane adds its own
+// peak's 32 row updates along the Gray-code row order (add_peak_rows), so the
+// 32 atomics of one warp instruction always go to 32 different banks.
 //
-// Emit: lane l walks its row along f0 over a segment of the tile (one segment
+// Emit: lane l walks row l along f0 over a segment of the tile (one segment
 // per warp): START sums a K-cell window of starts, DIFF takes a running sum
 // with the other segments' totals as carry-in.  The count goes to the map
 // (optional) and the warp's max over rows (smallest row on ties) to the
 // direction's profile by a 64-bit atomicMax, which is order-independent.
-template <int MODE>
-__global__ void __launch_bounds__(1024, 1)
-transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words)
+template <int MODE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words,
+                 int32_t guard, uint32_t cell_stride)
 {
-    extern __shared__ __align__(16) int32_t smem[];
+    extern __shared__ __align__(16) int32_t smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    // counters: `guard` cells below the tile, the tile's W + K - 1 cells (plus
+    // the dump cell), `guard` cells above; cell 0 sits at a 128-byte aligned
+    // shared address (the allocation has 128 spare bytes), so a lane's row
+    // offset is a single XOR
+    const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t hbase = (sraw + 127u) & ~127u;
+    int32_t *const Hlo = smem_raw + ((hbase - sraw) >> 2);  // lowest guard cell
+    int32_t *const H = Hlo + guard * kRows;                  // cell 0
+    const uint32_t rbase = hbase + (uint32_t)guard * (kRows * 4u) + 4u * (uint32_t)lane;
+    int32_t *const tab = Hlo + hist_words + warp * 32;  // per-warp owner table
+    int32_t *const next_chunk = Hlo + hist_words + nwarps * 32 +
+                                (MODE == FH_MODE_DIFF ? nwarps * 32 : 0);
+    const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    // step table factors: e[b] = mult[b] * D, mult[b] = +-2^b, + when lane bit b is set
+    int32_t mult[5];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) mult[b] = ((lane >> b) & 1) ? (1 << b) : -(1 << b);
 
     for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
         int jb = 0;
@@ -213,13 +392,20 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int64_t *__restrict__ offs = J->offsets;
         const int64_t *__restrict__ S0 = J->S0;
         const int64_t *__restrict__ Dt = J->D;
+        const int32_t *__restrict__ bidx =
+            J->bidx ? J->bidx + (int64_t)d_abs * n_fft * J->bnb : nullptr;
+        const int32_t bbase = J->bbase, bgsh = J->bgsh, bnb = J->bnb;
         const bool row_ok = lane < R;
+        // fast path when the job's largest drift over 32 rows stays inside the guards
+        const bool fast = MODE == FH_MODE_START && J->dmax != nullptr &&
+                          guard_for(*J->dmax) <= guard;
 
-        // zero the counters
+        // zero the counters (with the guard cells in the fast path); reset the chunk counter
         {
-            int4 *h4 = reinterpret_cast<int4 *>(smem);
-            const int n4 = (E * kRows) >> 2;
+            int4 *h4 = reinterpret_cast<int4 *>(fast ? Hlo : H);
+            const int n4 = ((fast ? E + 2 * guard : E) * kRows) >> 2;
             for (int w = threadIdx.x; w < n4; w += blockDim.x) h4[w] = make_int4(0, 0, 0, 0);
+            if (threadIdx.x == 0) *next_chunk = nwarps;
         }
         __syncthreads();
 
@@ -227,53 +413,87 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int64_t base_shift = (int64_t)(b0 - K + 1) * 4294967296LL;
         const int64_t e_fixed = (int64_t)E * 4294967296LL;
         const int nchunks = (n_fft + 31) >> 5;
-        for (int c = warp; c < nchunks; c += nwarps) {
+        // chunks of 32 FFTs: the first round one per warp, then whoever is free
+        for (int c = warp; c < nchunks;) {
             const int i = (c << 5) + lane;
-            int64_t q0 = 0, q1 = 0, hi = 0, cb = 0, dv = 0;
+            int64_t cb = 0, dv = 0, q0 = 0;
+            int n = 0;
             if (i < n_fft) {
                 const int64_t o0 = offs[i], o1 = offs[i + 1];
                 dv = Dt[i];
                 cb = S0[i] + (int64_t)j0 * dv + base_shift;
                 const int64_t span = (int64_t)(R - 1) * dv;
                 const int64_t lo = cb + (span < 0 ? span : 0);
-                hi = cb + (span > 0 ? span : 0) + e_fixed;
-                int64_t a = o0, b = o1;
-                while (a < b) {
-                    const int64_t m = (a + b) >> 1;
-                    if (__ldg(Ad + m) < lo) a = m + 1; else b = m;
-                }
-                q0 = a;
-                q1 = o1;
+                const int64_t hi = cb + (span > 0 ? span : 0) + e_fixed;
+                const int32_t *brow = bidx ? bidx + (int64_t)i * bnb : nullptr;
+                q0 = first_at_least(Ad, brow, bbase, bgsh, bnb, o0, o0, o1, lo);
+                const int64_t q1 = first_at_least(Ad, brow, bbase, bgsh, bnb, o0, q0, o1, hi);
+                n = (int)(q1 - q0);
             }
-            unsigned todo = __ballot_sync(kFull, q0 < q1);
-            while (todo) {
-                const int k = __ffs(todo) - 1;
-                todo &= todo - 1;
-                int64_t q = __shfl_sync(kFull, q0, k);
-                const int64_t qe = __shfl_sync(kFull, q1, k);
-                const int64_t h = __shfl_sync(kFull, hi, k);
-                const int64_t off = __shfl_sync(kFull, cb, k) + (int64_t)lane * __shfl_sync(kFull, dv, k);
-                for (;;) {
-                    const int64_t idx = q + lane;
-                    const int64_t av = (idx < qe) ? __ldg(Ad + idx) : LLONG_MAX;
-                    const int n = __popc(__ballot_sync(kFull, av < h));
-                    for (int t = 0; t < n; ++t) {
-                        const int64_t a = __shfl_sync(kFull, av, t);
-                        const int L = (int)((a - off) >> 32);
-                        if (row_ok && (unsigned)L < (unsigned)E) {
-                            if (MODE == FH_MODE_START) {
-                                atomicAdd(&smem[L * kRows + lane], 1);
-                            } else {
-                                const int st = L - K + 1;
-                                atomicAdd(&smem[(st > 0 ? st : 0) * kRows + lane], 1);
-                                if (L + 1 < Wt) atomicAdd(&smem[(L + 1) * kRows + lane], -1);
-                            }
-                        }
+            // exclusive scan of the per-FFT counts, owner table of non-empty FFTs
+            int P = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, P, o);
+                if (lane >= o) P += y;
+            }
+            const int T = __shfl_sync(kFull, P, 31);
+            P -= n;
+            const unsigned nonempty = __ballot_sync(kFull, n > 0);
+            if (n > 0) tab[__popc(nonempty & lanemask_lt)] = lane;
+            __syncwarp();
+
+            // deal the T peaks out in rounds of 32; the next round's positions are
+            // loaded while the current round is added
+            auto fetch = [&](int base, int64_t &a, int &owner) {
+                const bool starts = n > 0 && P >= base && P < base + 32;
+                const unsigned bits = __reduce_or_sync(kFull, starts ? (1u << (P - base)) : 0u);
+                const int before = (int)__reduce_add_sync(kFull, (n > 0 && P < base) ? 1u : 0u);
+                int oc = before + __popc(bits & lanemask_le) - 1;
+                oc = oc < 0 ? 0 : oc;
+                owner = tab[oc];
+                const int64_t oq0 = __shfl_sync(kFull, q0, owner);
+                const int oP = __shfl_sync(kFull, P, owner);
+                const int g = base + lane;
+                a = g < T ? __ldg(Ad + oq0 + (g - oP)) : 0;
+            };
+            int64_t a_nx = 0;
+            int own_nx = 0;
+            if (T > 0) fetch(0, a_nx, own_nx);
+            for (int base = 0; base < T; base += 32) {
+                const int64_t a = a_nx;
+                const int owner = own_nx;
+                if (base + 32 < T) fetch(base + 32, a_nx, own_nx);
+                const int64_t ocb = __shfl_sync(kFull, cb, owner);
+                const int64_t odv = __shfl_sync(kFull, dv, owner);
+                if (base + lane < T) {
+                    const int64_t e[5] = {(int64_t)mult[0] * odv, (int64_t)mult[1] * odv,
+                                          (int64_t)mult[2] * odv, (int64_t)mult[3] * odv,
+                                          (int64_t)mult[4] * odv};
+                    const int64_t X = a - ocb - (int64_t)lane * odv;
+                    if (MODE == FH_MODE_START) {
+                        // rows 0 and 31 bound the 32 rows' cells (X is linear in the row)
+                        const int64_t Xr0 = a - ocb;
+                        const int64_t Xr31 = Xr0 - 31 * odv;
+                        const uint32_t span_ok = (uint32_t)(E + 2 * guard);
+                        const bool inside =
+                            (uint32_t)((int32_t)(Xr0 >> 32) + guard) < span_ok &&
+                            (uint32_t)((int32_t)(Xr31 >> 32) + guard) < span_ok;
+                        if (fast && inside)
+                            start_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
+                                               cell_stride, (uint32_t)E);
+                        else
+                            start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
+                                              cell_stride, (uint32_t)E);
+                    } else {
+                        diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X, e, E, Wt, K);
                     }
-                    if (n < 32) break;
-                    q += 32;
                 }
             }
+            __syncwarp();
+            int nc = 0;
+            if (lane == 0) nc = atomicAdd(next_chunk, 1);
+            c = __shfl_sync(kFull, nc, 0);
         }
         __syncthreads();
 
@@ -297,22 +517,22 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         if (MODE == FH_MODE_START) {
             int win = 0;
             if (c0 < c1)
-                for (int L = c0; L < c0 + K - 1; ++L) win += smem[L * kRows + lane];
+                for (int L = c0; L < c0 + K - 1; ++L) win += H[L * kRows + lane];
             for (int c = c0; c < c1; ++c) {
-                win += smem[(c + K - 1) * kRows + lane];
+                win += H[(c + K - 1) * kRows + lane];
                 emit(c, win);
-                win -= smem[c * kRows + lane];
+                win -= H[c * kRows + lane];
             }
         } else {
-            int32_t *segtot = smem + hist_words;
+            int32_t *segtot = Hlo + hist_words + nwarps * 32;
             int tot = 0;
-            for (int c = c0; c < c1; ++c) tot += smem[c * kRows + lane];
+            for (int c = c0; c < c1; ++c) tot += H[c * kRows + lane];
             segtot[warp * 32 + lane] = tot;
             __syncthreads();
             int acc = 0;
             for (int w = 0; w < warp; ++w) acc += segtot[w * 32 + lane];
             for (int c = c0; c < c1; ++c) {
-                acc += smem[c * kRows + lane];
+                acc += H[c * kRows + lane];
                 emit(c, acc);
             }
         }
@@ -448,26 +668,27 @@ smem_atomic_bench_kernel(int32_t variant, int32_t iters, unsigned long long *sin
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
                                 double fdot_min, double fdot_step, int32_t n_fdot,
-                                int64_t *S0, int64_t *D, int32_t *err, cudaStream_t s)
+                                int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,
+                                cudaStream_t s)
 {
     if (n_fft <= 0) return cudaSuccess;
     const double f_last = fdot_min + (double)(n_fdot - 1) * fdot_step;
     const double absmax = fabs(fdot_min) > fabs(f_last) ? fabs(fdot_min) : fabs(f_last);
     shift_tables_kernel<<<(n_fft + 255) / 256, 256, 0, s>>>(t, n_fft, t_ref, kt, fdot_min,
-                                                             fdot_step, absmax, S0, D, err);
+                                                             fdot_step, absmax, S0, D, dmax, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, cudaStream_t s)
+                             double *out_r, int32_t *err, const BucketIndex &bix, cudaStream_t s)
 {
     if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
     dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
     positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
-                                                  kt, cshift, A, out_r, err);
+                                                  kt, cshift, A, out_r, err, bix);
     return cudaGetLastError();
 }
 
@@ -490,48 +711,84 @@ cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
     return cudaGetLastError();
 }
 
-size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, int32_t nwarps)
+__host__ __device__ int32_t guard_for(unsigned long long dmax)
 {
-    size_t words = (size_t)(tile_cells + k_over - 1) * kRows;
+    // 31 rows of drift, rounded up to whole cells, plus 2 cells of margin
+    const unsigned long long drift = 31ull * dmax;
+    return (int32_t)((drift + 0xFFFFFFFFull) >> 32) + 2;
+}
+
+size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, int32_t nwarps,
+                            int32_t guard)
+{
+    // counters of W + K - 1 cells, one dump cell and 2 x guard cells, per-warp
+    // owner tables, (DIFF) per-warp segment totals, the chunk counter, and 128
+    // bytes of alignment slack
+    size_t words = (size_t)(tile_cells + k_over + 2 * guard) * kRows + (size_t)nwarps * 32;
     if (mode == FH_MODE_DIFF) words += (size_t)nwarps * 32;
-    return words * sizeof(int32_t);
+    return (words + 4) * sizeof(int32_t) + 128;
+}
+
+BucketIndex bucket_geometry(int32_t n_f0, int32_t k_over, double cells_per_peak)
+{
+    BucketIndex b;
+    int gsh = 4;
+    while (gsh < 12 && (double)(1 << (gsh + 1)) <= cells_per_peak) ++gsh;
+    const int32_t margin = n_f0 / 2 > 1024 ? n_f0 / 2 : 1024;
+    b.gsh = gsh;
+    b.base = -k_over - margin;
+    b.nb = (int32_t)(((int64_t)n_f0 + k_over + 2 * (int64_t)margin) >> gsh) + 2;
+    return b;
+}
+
+// Kernel instantiation for a counting mode and block size: blocks of up to 512
+// threads get up to 128 registers per thread, blocks of 1024 threads 64.
+template <typename F>
+static auto with_transform_kernel(int32_t mode, int32_t nwarps, F &&f)
+{
+    if (mode == FH_MODE_DIFF)
+        return nwarps > 16 ? f(transform_kernel<FH_MODE_DIFF, 1024>)
+                           : f(transform_kernel<FH_MODE_DIFF, 512>);
+    return nwarps > 16 ? f(transform_kernel<FH_MODE_START, 1024>)
+                       : f(transform_kernel<FH_MODE_START, 512>);
 }
 
 cudaError_t transform_prepare(int32_t mode, size_t smem)
 {
-    if (mode == FH_MODE_DIFF)
-        return cudaFuncSetAttribute(transform_kernel<FH_MODE_DIFF>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(transform_kernel<FH_MODE_START>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    for (int nw : {16, 32}) {
+        const cudaError_t r = with_transform_kernel(mode, nw, [&](auto k) {
+            return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (r != cudaSuccess) e = r;
+    }
+    return e;
 }
 
 int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem)
 {
     int n = 0;
-    cudaError_t e;
-    if (mode == FH_MODE_DIFF)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transform_kernel<FH_MODE_DIFF>,
-                                                          nwarps * 32, smem);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transform_kernel<FH_MODE_START>,
-                                                          nwarps * 32, smem);
+    const cudaError_t e = with_transform_kernel(mode, nwarps, [&](auto k) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, nwarps * 32, smem);
+    });
     return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_items,
-                             int32_t grid, int32_t nwarps, size_t smem, cudaStream_t s)
+                             int32_t grid, int32_t nwarps, size_t smem, int32_t guard,
+                             cudaStream_t s)
 {
     if (total_items <= 0) return cudaSuccess;
+    // counters (+ dump cell) of the widest tile with its guard cells; owner tables follow
     int32_t hist_words = 0;
     for (int j = 0; j < tbl.n_jobs; ++j) {
-        const int32_t w = (tbl.job[j].tile_cells + tbl.job[j].k_over - 1) * kRows;
+        const int32_t w = (tbl.job[j].tile_cells + tbl.job[j].k_over + 2 * guard) * kRows;
         hist_words = w > hist_words ? w : hist_words;
     }
-    if (mode == FH_MODE_DIFF)
-        transform_kernel<FH_MODE_DIFF><<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words);
-    else
-        transform_kernel<FH_MODE_START><<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words);
+    with_transform_kernel(mode, nwarps, [&](auto k) {
+        k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u);
+        return cudaSuccess;
+    });
     return cudaGetLastError();
 }
 

@@ -61,6 +61,9 @@ struct Job {
     uint64_t *d_prof = nullptr;
     fh_candidate *d_cand = nullptr;
     int32_t *d_err = nullptr;
+    unsigned long long *d_dmax = nullptr;
+    int32_t guard = 0;
+    BucketIndex bix;
     size_t pin_off = 0;  // offset of its candidates in the batch's pinned buffer
     size_t err_off = 0;
 
@@ -86,7 +89,11 @@ struct Job {
         const size_t a_prof = take(8 * (size_t)n_dir * (size_t)d.n_f0);
         const size_t a_cand = take(sizeof(fh_candidate) * (size_t)cand_count());
         const size_t a_err = take(16);
+        const size_t a_bidx = take(4 * (size_t)n_dir * (size_t)n_fft * (size_t)bix.nb);
+        const size_t a_dmax = take(16);
         if (carve) {
+            d_dmax = (unsigned long long *)(dbuf + a_dmax);
+            bix.idx = (int32_t *)(dbuf + a_bidx);
             d_off = (int64_t *)(dbuf + a_off);
             d_t = (double *)(dbuf + a_t);
             d_freq = (double *)(dbuf + a_freq);
@@ -188,24 +195,33 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             if (c.bytes && e == cudaSuccess)
                 e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(j->d_err, 0, 16, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(j->d_dmax, 0, 16, s);
         if (e == cudaSuccess)
             e = launch_shift_tables(j->d_t, j->n_fft, d.t_ref, j->kt, d.fdot_min, d.fdot_step,
-                                    d.n_fdot, j->d_S0, j->d_D, j->d_err, s);
+                                    d.n_fdot, j->d_S0, j->d_D, j->d_dmax, j->d_err, s);
         if (e == cudaSuccess)
             e = launch_positions(j->d_freq, j->d_off, j->d_v, j->d_sky, j->n_fft, j->n_peaks,
-                                 j->n_dir, d.f0_min, j->kt, d.k_over, j->d_A, nullptr, j->d_err, s);
+                                 j->n_dir, d.f0_min, j->kt, d.k_over, j->d_A, nullptr, j->d_err,
+                                 j->bix, s);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(j->d_prof, 0, 8 * (size_t)j->n_dir * d.n_f0, s);
         if (e != cudaSuccess) return cuda_error(e, "job set-up");
     }
-    // one persistent transform launch per group of kMaxBatchJobs jobs
+    // one persistent transform launch per group of kMaxBatchJobs jobs; the group
+    // shares the largest guard its jobs need, and each job's tile is kept
+    // within shared memory with that guard
     const int nwarps = 32;
     for (size_t g = 0; g < batch.size(); g += kMaxBatchJobs) {
+        const size_t g_end = std::min(batch.size(), g + (size_t)kMaxBatchJobs);
+        int32_t guard = 2;
+        for (size_t k = g; k < g_end; ++k) guard = std::max(guard, batch[k]->guard);
         JobTable tbl{};
         int64_t items = 0;
         size_t smem = 0;
-        for (size_t k = g; k < batch.size() && k < g + kMaxBatchJobs; ++k) {
+        for (size_t k = g; k < g_end; ++k) {
             Job *j = batch[k];
+            const int32_t tile =
+                std::min(j->tile, default_tile(j->d, device, FH_MODE_START, nwarps, guard));
             TransformJob &t = tbl.job[tbl.n_jobs++];
             t.A = j->d_A;
             t.offsets = j->d_off;
@@ -213,20 +229,26 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.D = j->d_D;
             t.profile = j->d_prof;
             t.maps = nullptr;
+            t.bidx = j->bix.idx;
+            t.dmax = j->d_dmax;
+            t.bbase = j->bix.base;
+            t.bgsh = j->bix.gsh;
+            t.bnb = j->bix.nb;
             t.n_peaks = j->n_peaks;
             t.n_fft = j->n_fft;
             t.n_f0 = j->d.n_f0;
             t.n_fdot = j->d.n_fdot;
             t.k_over = j->d.k_over;
-            t.tile_cells = j->tile;
+            t.tile_cells = tile;
             t.n_slabs = (j->d.n_fdot + kRows - 1) / kRows;
-            t.n_tiles = (j->d.n_f0 + j->tile - 1) / j->tile;
+            t.n_tiles = (j->d.n_f0 + tile - 1) / tile;
             t.dir_begin = 0;
             t.n_dir = j->n_dir;
             t.item_begin = items;
             t.n_items = (int64_t)t.n_slabs * t.n_tiles * j->n_dir;
             items += t.n_items;
-            smem = std::max(smem, transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps));
+            smem = std::max(smem, transform_smem_bytes(tile, j->d.k_over, FH_MODE_START, nwarps,
+                                                       guard));
         }
         if (smem > prepared_smem) {
             e = transform_prepare(FH_MODE_START, smem);
@@ -235,7 +257,7 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
         }
         const int bps = std::max(1, transform_blocks_per_sm(FH_MODE_START, nwarps, smem));
         const int32_t grid = (int32_t)std::min<int64_t>(items, (int64_t)n_sm * bps);
-        e = launch_transform(FH_MODE_START, tbl, items, grid, nwarps, smem, s);
+        e = launch_transform(FH_MODE_START, tbl, items, grid, nwarps, smem, guard, s);
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
     }
     for (Job *j : batch) {
@@ -428,6 +450,14 @@ int copy_job(const fh_job_desc *jd, Job &j)
     j.freq.assign(pm.freq, pm.freq + pm.n_peaks);
     j.v.assign(jd->v_over_c, jd->v_over_c + 3 * (size_t)pm.n_fft);
     j.sky.assign(jd->sky_n, jd->sky_n + 3 * (size_t)jd->n_dir);
+    {
+        const double cpp = ((double)j.d.n_f0 + 2.0 * j.d.k_over) * (double)std::max(1, j.n_fft) /
+                           (double)std::max<int64_t>(1, j.n_peaks);
+        const BucketIndex g = bucket_geometry(j.d.n_f0, j.d.k_over, cpp);
+        j.bix.base = g.base;
+        j.bix.gsh = g.gsh;
+        j.bix.nb = g.nb;
+    }
     j.bytes = j.layout(false);
     return FH_OK;
 }
@@ -535,8 +565,9 @@ int fh_submit(fh_server sv, const fh_job_desc *jd, fh_job_id *out)
     if (job->bytes > sv->budget)
         return set_error(FH_ERR_TOO_LARGE, "job needs %lld device bytes, budget is %lld",
                          (long long)job->bytes, (long long)sv->budget);
-    // a job of this shape runs with the library's default tile
-    job->tile = default_tile(job->d, sv->device, FH_MODE_START, 32);
+    // a job of this shape runs with the library's default tile for its guard
+    job->guard = std::max(default_guard(job->d), host_guard(job->d, job->kt, job->t.data(), job->n_fft));
+    job->tile = default_tile(job->d, sv->device, FH_MODE_START, 32, job->guard);
     job->id = sv->next_id++;
     job->submit_s = sv->now();
     *out = job->id;

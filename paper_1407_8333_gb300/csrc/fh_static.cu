@@ -36,7 +36,8 @@ constexpr size_t kOffD = kOffS0 + round256(8 * (size_t)kStaticMaxFft);
 constexpr size_t kOffA = kOffD + round256(8 * (size_t)kStaticMaxFft);
 constexpr size_t kOffProfile = kOffA + round256(8 * (size_t)kStaticMaxPeaks);
 constexpr size_t kOffErr = kOffProfile + round256(8 * (size_t)kStaticMaxCells);
-constexpr size_t kScratchBytes = kOffErr + 256;
+constexpr size_t kOffDmax = kOffErr + 256;
+constexpr size_t kScratchBytes = kOffDmax + 256;
 
 static __device__ __align__(256) unsigned char g_fh_static_scratch[kScratchBytes];
 
@@ -107,6 +108,7 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     int64_t *A = reinterpret_cast<int64_t *>(base + kOffA);
     uint64_t *profile = reinterpret_cast<uint64_t *>(base + kOffProfile);
     int32_t *err = reinterpret_cast<int32_t *>(base + kOffErr);
+    unsigned long long *dmax = reinterpret_cast<unsigned long long *>(base + kOffDmax);
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int32_t n = pm->n_fft;
@@ -118,23 +120,25 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
 
     // the array keeps the previous call's contents: clear what must start at zero
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(profile, 0, sizeof(uint64_t) * (size_t)d.n_f0, s);
     if (e == cudaSuccess) e = launch_sanitize_offsets(pm->offsets, n, np, offsets, err, s);
     if (e == cudaSuccess)
         e = launch_validate_device_inputs(pm->t_fft, pm->freq, offsets, v_over_c, sky_n, n, 1, err, s);
     if (e == cudaSuccess)
         e = launch_shift_tables(pm->t_fft, n, d.t_ref, kt, d.fdot_min, d.fdot_step, d.n_fdot, S0, D,
-                                err, s);
+                                dmax, err, s);
     if (e == cudaSuccess)
         e = launch_positions(pm->freq, offsets, v_over_c, sky_n, n, np, 1, d.f0_min, kt, d.k_over, A,
-                             nullptr, err, s);
+                             nullptr, err, BucketIndex{}, s);
     if (e != cudaSuccess) return cuda_error(e, "fh_search_static set-up");
 
     const int32_t mode = d.mode == FH_MODE_DIFF ? FH_MODE_DIFF : FH_MODE_START;
     const int32_t nwarps = d.block_warps ? d.block_warps : 32;
+    const int32_t guard = default_guard(d);
     int32_t tile = d.tile_cells ? (d.tile_cells < d.n_f0 ? d.tile_cells : d.n_f0)
-                                : default_tile(d, dev, mode, nwarps);
-    const size_t smem = transform_smem_bytes(tile, d.k_over, mode, nwarps);
+                                : default_tile(d, dev, mode, nwarps, guard);
+    const size_t smem = transform_smem_bytes(tile, d.k_over, mode, nwarps, guard);
     if (smem > (size_t)max_optin_smem(dev))
         return set_error(FH_ERR_INVALID_ARG, "tile_cells too wide for shared memory");
     e = transform_prepare(mode, smem);
@@ -148,6 +152,8 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     job.D = D;
     job.profile = profile;
     job.maps = nullptr;
+    job.bidx = nullptr;  // no bucket index in the fixed scratch: binary search
+    job.dmax = dmax;
     job.n_peaks = np;
     job.item_begin = 0;
     job.n_fft = n;
@@ -164,7 +170,7 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     if (bps < 1) return set_error(FH_ERR_CUDA, "transform kernel cannot be resident");
     const int64_t cap = (int64_t)n_sm * bps;
     const int32_t grid = (int32_t)(job.n_items < cap ? job.n_items : cap);
-    e = launch_transform(mode, tbl, job.n_items, grid, nwarps, smem, s);
+    e = launch_transform(mode, tbl, job.n_items, grid, nwarps, smem, guard, s);
     if (e != cudaSuccess) return cuda_error(e, "transform launch");
 
     SelectArgs a{};
