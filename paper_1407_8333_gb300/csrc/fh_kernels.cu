@@ -21,15 +21,15 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kTwo32 = 4294967296.0;
-constexpr int kPosFfts = 64;
+constexpr int kPosFfts = 8;
 constexpr int kPosThreads = 256;
 
 // ---------------------------------------------------------------- a1 + a2
-// grid (ceil(n_fft / 64), n_dir): the block computes r = 1 / (1 + v.n) for 64
+// grid (ceil(n_fft / 8), n_dir): the block computes r = 1 / (1 + v.n) for 8
 // FFTs of one direction, then the fixed-point position of each of their peaks
 // (a contiguous CSR range, so loads and stores are coalesced), then -- if an
-// index is wanted -- the bucket index of those 64 FFTs from the positions it
-// has just written (still in L1/L2).
+// index is wanted -- one warp per FFT builds that FFT's bucket index from the
+// positions just written (still in L1/L2).
 __global__ void __launch_bounds__(kPosThreads)
 positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
@@ -172,7 +172,9 @@ sanitize_offsets_kernel(const int64_t *__restrict__ in, int32_t n_fft, int64_t n
     if (bad) atomicOr(err, kErrCsr);
 }
 
-// Flags non-finite / unordered device inputs (thread per FFT and per direction).
+// Flags non-finite / unordered device inputs: one warp per FFT (its peaks are
+// read coalesced and compared with their left neighbour) and one thread per
+// sky direction.
 __global__ void validate_device_inputs_kernel(const double *__restrict__ t,
                                               const double *__restrict__ freq,
                                               const int64_t *__restrict__ offsets,
@@ -180,27 +182,32 @@ __global__ void validate_device_inputs_kernel(const double *__restrict__ t,
                                               const double *__restrict__ sky, int32_t n_fft,
                                               int32_t n_dir, int32_t *err)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int32_t e = 0;
-    if (i < n_fft) {
-        if (!isfinite(t[i]) || (i > 0 && !(t[i] > t[i - 1]))) e |= kErrUnsorted;
-        for (int c = 0; c < 3; ++c)
-            if (!(fabs(v[3 * (int64_t)i + c]) < 0.1)) e |= kErrInvalid;
-        double prev = 0.0;
-        for (int64_t p = offsets[i]; p < offsets[i + 1]; ++p) {
+    if (gw < n_fft) {
+        const int i = gw;
+        if (lane == 0) {
+            if (!isfinite(t[i]) || (i > 0 && !(t[i] > t[i - 1]))) e |= kErrUnsorted;
+            for (int c = 0; c < 3; ++c)
+                if (!(fabs(v[3 * (int64_t)i + c]) < 0.1)) e |= kErrInvalid;
+        }
+        const int64_t o0 = offsets[i], o1 = offsets[i + 1];
+        for (int64_t p = o0 + lane; p < o1; p += 32) {
             const double f = freq[p];
             if (!isfinite(f) || !(f > 0.0)) e |= kErrInvalid;
-            if (p > offsets[i] && !(f > prev)) e |= kErrUnsorted;
-            prev = f;
+            if (p > o0 && !(f > freq[p - 1])) e |= kErrUnsorted;
         }
     }
-    if (i < n_dir) {
-        const double x = sky[3 * (int64_t)i], y = sky[3 * (int64_t)i + 1],
-                     z = sky[3 * (int64_t)i + 2];
+    const int gt = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (gt < n_dir) {
+        const double x = sky[3 * (int64_t)gt], y = sky[3 * (int64_t)gt + 1],
+                     z = sky[3 * (int64_t)gt + 2];
         if (!(fabs(x) <= 1.000001 && fabs(y) <= 1.000001 && fabs(z) <= 1.000001))
             e |= kErrInvalid;
     }
-    if (e) atomicOr(err, e);
+    e = (int32_t)__reduce_or_sync(kFull, (unsigned)e);
+    if (lane == 0 && e) atomicOr(err, e);
 }
 
 // ---------------------------------------------------------------- a4 + a5 + profile
@@ -312,6 +319,38 @@ __device__ __forceinline__ void start_steps(std::integer_sequence<int, Ts...>, u
                                             uint32_t E)
 {
     (start_step<CLAMP, Ts>(rbase, X, e, stride, E), ...);
+}
+
+// Two peaks per lane, same row walk: both share the step's row offset.
+template <int T>
+__device__ __forceinline__ void start_step2(uint32_t rbase, int64_t &X1, int64_t &X2,
+                                            const int64_t (&e1)[5], const int64_t (&e2)[5],
+                                            uint32_t stride)
+{
+    constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
+    const uint32_t rb = rbase ^ (gt << 2);
+    const uint32_t a1 = (uint32_t)(int32_t)(X1 >> 32) * stride + rb;
+    const uint32_t a2 = (uint32_t)(int32_t)(X2 >> 32) * stride + rb;
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a1) : "memory");
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a2) : "memory");
+    if constexpr (T < 31) {
+        constexpr int b = ctz5(T + 1);
+        if constexpr ((gt >> b) & 1) {
+            X1 -= e1[b];
+            X2 -= e2[b];
+        } else {
+            X1 += e1[b];
+            X2 += e2[b];
+        }
+    }
+}
+
+template <int... Ts>
+__device__ __forceinline__ void start_steps2(std::integer_sequence<int, Ts...>, uint32_t rbase,
+                                             int64_t X1, int64_t X2, const int64_t (&e1)[5],
+                                             const int64_t (&e2)[5], uint32_t stride)
+{
+    (start_step2<Ts>(rbase, X1, X2, e1, e2, stride), ...);
 }
 
 template <int... Ts>
@@ -443,8 +482,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             if (n > 0) tab[__popc(nonempty & lanemask_lt)] = lane;
             __syncwarp();
 
-            // deal the T peaks out in rounds of 32; the next round's positions are
-            // loaded while the current round is added
+            // deal the T peaks out to the lanes: position g = base + lane of a round
+            // belongs to the non-empty FFT whose range [P, P + n) holds it
             auto fetch = [&](int base, int64_t &a, int &owner) {
                 const bool starts = n > 0 && P >= base && P < base + 32;
                 const unsigned bits = __reduce_or_sync(kFull, starts ? (1u << (P - base)) : 0u);
@@ -457,37 +496,73 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 const int g = base + lane;
                 a = g < T ? __ldg(Ad + oq0 + (g - oP)) : 0;
             };
-            int64_t a_nx = 0;
-            int own_nx = 0;
-            if (T > 0) fetch(0, a_nx, own_nx);
-            for (int base = 0; base < T; base += 32) {
-                const int64_t a = a_nx;
-                const int owner = own_nx;
-                if (base + 32 < T) fetch(base + 32, a_nx, own_nx);
+            // X of the lane's row and its step table for the peak at position g;
+            // positions beyond T are parked in guard cell -1 (never read)
+            auto setup = [&](int g, int64_t a, int owner, int64_t &X, int64_t (&e)[5],
+                             bool &inside) {
                 const int64_t ocb = __shfl_sync(kFull, cb, owner);
                 const int64_t odv = __shfl_sync(kFull, dv, owner);
-                if (base + lane < T) {
-                    const int64_t e[5] = {(int64_t)mult[0] * odv, (int64_t)mult[1] * odv,
-                                          (int64_t)mult[2] * odv, (int64_t)mult[3] * odv,
-                                          (int64_t)mult[4] * odv};
-                    const int64_t X = a - ocb - (int64_t)lane * odv;
-                    if (MODE == FH_MODE_START) {
-                        // rows 0 and 31 bound the 32 rows' cells (X is linear in the row)
-                        const int64_t Xr0 = a - ocb;
-                        const int64_t Xr31 = Xr0 - 31 * odv;
-                        const uint32_t span_ok = (uint32_t)(E + 2 * guard);
-                        const bool inside =
-                            (uint32_t)((int32_t)(Xr0 >> 32) + guard) < span_ok &&
-                            (uint32_t)((int32_t)(Xr31 >> 32) + guard) < span_ok;
-                        if (fast && inside)
-                            start_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
-                                               cell_stride, (uint32_t)E);
-                        else
-                            start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
-                                              cell_stride, (uint32_t)E);
+#pragma unroll
+                for (int b = 0; b < 5; ++b) e[b] = (int64_t)mult[b] * odv;
+                X = a - ocb - (int64_t)lane * odv;
+                // rows 0 and 31 bound the 32 rows' cells (X is linear in the row)
+                const int64_t Xr0 = a - ocb;
+                const int64_t Xr31 = Xr0 - 31 * odv;
+                const uint32_t span_ok = (uint32_t)(E + 2 * guard);
+                inside = (uint32_t)((int32_t)(Xr0 >> 32) + guard) < span_ok &&
+                         (uint32_t)((int32_t)(Xr31 >> 32) + guard) < span_ok;
+                if (g >= T) {
+#pragma unroll
+                    for (int b = 0; b < 5; ++b) e[b] = 0;
+                    X = -(int64_t(1) << 32);
+                    inside = true;
+                }
+            };
+            constexpr bool kTwoPeaks = MODE == FH_MODE_START && MAXT <= 512;
+            int64_t a_nx = 0, a2_nx = 0;
+            int own_nx = 0, own2_nx = 0;
+            if (T > 0) fetch(0, a_nx, own_nx);
+            if (kTwoPeaks && T > 32) fetch(32, a2_nx, own2_nx);
+            int base = 0;
+            if (kTwoPeaks) {
+                // rounds of 64 positions (two peaks per lane) while more than 32 remain
+                for (; T - base > 32; base += 64) {
+                    const int64_t a1 = a_nx, a2 = a2_nx;
+                    const int o1 = own_nx, o2 = own2_nx;
+                    if (base + 64 < T) fetch(base + 64, a_nx, own_nx);
+                    if (base + 96 < T) fetch(base + 96, a2_nx, own2_nx);
+                    int64_t X1, X2, e1[5], e2[5];
+                    bool in1, in2;
+                    setup(base + lane, a1, o1, X1, e1, in1);
+                    setup(base + 32 + lane, a2, o2, X2, e2, in2);
+                    if (__all_sync(kFull, fast && in1 && in2)) {
+                        start_steps2(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e1, e2,
+                                     cell_stride);
                     } else {
-                        diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X, e, E, Wt, K);
+                        start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X1, e1,
+                                          cell_stride, (uint32_t)E);
+                        start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X2, e2,
+                                          cell_stride, (uint32_t)E);
                     }
+                }
+            }
+            // rounds of 32 positions
+            for (; base < T; base += 32) {
+                const int64_t a = a_nx;
+                const int owner = own_nx;
+                if (!kTwoPeaks && base + 32 < T) fetch(base + 32, a_nx, own_nx);
+                int64_t X, e[5];
+                bool inside;
+                setup(base + lane, a, owner, X, e, inside);
+                if (MODE == FH_MODE_START) {
+                    if (__all_sync(kFull, fast && inside))
+                        start_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
+                                           cell_stride, (uint32_t)E);
+                    else
+                        start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
+                                          cell_stride, (uint32_t)E);
+                } else if (base + lane < T) {
+                    diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X, e, E, Wt, K);
                 }
             }
             __syncwarp();
@@ -506,13 +581,32 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             maprow = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
         unsigned long long *prof =
             reinterpret_cast<unsigned long long *>(J->profile) + (int64_t)d_abs * n_f0 + b0;
+        // per cell: the warp's max over its rows, smallest row on ties.  Counts
+        // below 2^26 fit one packed reduction (count << 5 | 31 - lane); the
+        // cell's lane keeps the key and every lane issues one profile atomic
+        // per 32 cells
+        const bool packed = J->n_peaks < (int64_t(1) << 26);
+        unsigned long long mykey = 0;
         auto emit = [&](int c, int count) {
             if (maprow) maprow[c] = count;
-            const int cm = __reduce_max_sync(kFull, row_ok ? count : INT_MIN);
-            const unsigned rm = __reduce_min_sync(kFull, (row_ok && count == cm) ? (unsigned)lane : 32u);
-            if (lane == (c & 31))
-                atomicMax(prof + c, ((unsigned long long)(unsigned)cm << 32) |
-                                        (0xFFFFFFFFull - (unsigned long long)(unsigned)(j0 + rm)));
+            unsigned cm, rm;
+            if (packed) {
+                const unsigned v = __reduce_max_sync(
+                    kFull, row_ok ? ((unsigned)count << 5) | (unsigned)(31 - lane) : 0u);
+                cm = v >> 5;
+                rm = 31u - (v & 31u);
+            } else {
+                const int m = __reduce_max_sync(kFull, row_ok ? count : INT_MIN);
+                cm = (unsigned)m;
+                rm = __reduce_min_sync(kFull, (row_ok && count == m) ? (unsigned)lane : 32u);
+            }
+            const unsigned long long key = ((unsigned long long)cm << 32) |
+                                           (0xFFFFFFFFull - (unsigned long long)(unsigned)(j0 + rm));
+            if (lane == ((c - c0) & 31)) mykey = key;
+            if (((c - c0) & 31) == 31 || c == c1 - 1) {
+                const int first = c - ((c - c0) & 31);
+                if (first + lane <= c) atomicMax(prof + first + lane, mykey);
+            }
         };
         if (MODE == FH_MODE_START) {
             int win = 0;
@@ -704,10 +798,12 @@ cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
                                           const double *sky, int32_t n_fft, int32_t n_dir,
                                           int32_t *err, cudaStream_t s)
 {
-    const int n = n_fft > n_dir ? n_fft : n_dir;
-    if (n <= 0) return cudaSuccess;
-    validate_device_inputs_kernel<<<(n + 255) / 256, 256, 0, s>>>(t, freq, offsets, v, sky,
-                                                                  n_fft, n_dir, err);
+    // one warp per FFT; the first n_dir threads also check the sky vectors
+    const int64_t threads = (int64_t)(n_fft > 0 ? n_fft : 0) * 32 > n_dir
+                                ? (int64_t)n_fft * 32 : (int64_t)n_dir;
+    if (threads <= 0) return cudaSuccess;
+    validate_device_inputs_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        t, freq, offsets, v, sky, n_fft, n_dir, err);
     return cudaGetLastError();
 }
 
