@@ -128,6 +128,25 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+def transform_traffic():
+    """DRAM bytes per transform launch from the committed ncu summary, if the
+    transform section of the kernel source is still the one that was profiled."""
+    import hashlib
+    import re
+    try:
+        src = open(os.path.join(ROOT, "paper_1407_8333_gb300", "csrc", "fh_kernels.cu")).read()
+        a = src.index("// ---------------------------------------------------------------- a4 + a5 + profile")
+        b = src.index("// ---------------------------------------------------------------- a6")
+        sha = hashlib.sha1(src[a:b].encode()).hexdigest()
+        md = open(os.path.join(ROOT, "profiles", "transform_single_sky_T8192_150d_50Hz.md")).read()
+        m = re.search(r"traffic: dram_bytes_per_launch=(\d+) transform_source_sha1=([0-9a-f]+)", md)
+        if m and m.group(2) == sha:
+            return int(m.group(1))
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def peaks_path():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -239,7 +258,9 @@ def run_ours(args):
     peaks, peak_src = peaks_path()
     hbm_bytes = 8 * inp.n_peaks * n_dir + 8 * pp["n_f0"] * n_dir + 16 * w.n_fft
     roof = {"bound": "smem_atomic", "achieved": achieved_atom / 1e9, "peak": atomic_peak / 1e9,
-            "unit": "Gatomic/s", "frac": achieved_atom / atomic_peak, "traffic": None,
+            "unit": "Gatomic/s", "frac": achieved_atom / atomic_peak,
+            "traffic": transform_traffic() if args.workload == WORKLOAD else None,
+            "traffic_note": "dram__bytes_read+write per launch from profiles/transform_single_sky_T8192_150d_50Hz.md (null if the kernel changed since)",
             "kernel": "transform_kernel<FH_MODE_START>",
             "algorithmic": "1 shared-memory atomic per peak x spin-down update; %d updates per launch"
                            % upd_step,
