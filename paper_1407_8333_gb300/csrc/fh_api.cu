@@ -189,6 +189,8 @@ struct fh_plan_s {
     int32_t *err = nullptr;
     int32_t *h_err = nullptr;  // pinned
     unsigned long long *dmax = nullptr;  // largest |D_i| of the current peakmap
+    int2 *win = nullptr;                 // peak windows of the directions being transformed
+    size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path
     BucketIndex bix;                     // bix.idx: [max_dir][max_fft][nb]
     int32_t n_fft = -1;
@@ -199,7 +201,7 @@ struct fh_plan_s {
 
     void release()
     {
-        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, bix.idx, dmax};
+        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, bix.idx, dmax, win};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -210,6 +212,8 @@ struct fh_plan_s {
         err = h_err = nullptr;
         bix.idx = nullptr;
         dmax = nullptr;
+        win = nullptr;
+        win_bytes = 0;
     }
 };
 
@@ -511,30 +515,50 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     const int64_t per_dir = (int64_t)job.n_slabs * job.n_tiles;
     int bps = transform_blocks_per_sm(p->mode, nwarps, smem);
     if (bps < 1) return set_error(FH_ERR_CUDA, "transform kernel cannot be resident");
+    // peak windows of a group of directions (bounded table), then the transform
+    const size_t per_dir_win = sizeof(int2) * (size_t)per_dir * (size_t)std::max(1, p->n_fft);
+    const size_t win_cap = std::max(per_dir_win, (size_t)1 << 30);
+    // (the windows grid has n_dir x n_slabs blocks along y: at most 65535)
+    const size_t zcap = (size_t)std::max(1, 65535 / job.n_slabs);
+    const int32_t group = schedule == FH_SCHED_PLAIN
+                              ? 1
+                              : (int32_t)std::max<size_t>(1, std::min<size_t>(
+                                    std::min<size_t>((size_t)n_dir, zcap), win_cap / per_dir_win));
+    const size_t need = per_dir_win * (size_t)group;
+    if (need > p->win_bytes) {
+        if (p->win) cudaFree(p->win);
+        p->win = nullptr;
+        p->win_bytes = 0;
+        e = cudaMalloc(&p->win, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FH_ERR_NOMEM, "cudaMalloc of %zu bytes (peak windows) failed", need);
+        }
+        p->win_bytes = need;
+    }
     JobTable tbl{};
     tbl.n_jobs = 1;
-    if (schedule == FH_SCHED_PLAIN) {
-        for (int32_t k = 0; k < n_dir; ++k) {
-            job.dir_begin = dir_begin + k;
-            job.n_dir = 1;
-            job.maps = out_maps ? out_maps + (int64_t)k * d.n_fdot * d.n_f0 : nullptr;
-            job.item_begin = 0;
-            job.n_items = per_dir;
-            tbl.job[0] = job;
-            e = launch_transform(p->mode, tbl, per_dir, (int32_t)per_dir, nwarps, smem, guard, s);
-            if (e != cudaSuccess) return cuda_error(e, "transform launch");
-            ++p->launches;
-        }
-    } else {
-        job.dir_begin = dir_begin;
-        job.n_dir = n_dir;
-        job.maps = out_maps;
+    for (int32_t g0 = 0; g0 < n_dir; g0 += group) {
+        const int32_t gn = std::min(group, n_dir - g0);
+        job.dir_begin = dir_begin + g0;
+        job.n_dir = gn;
+        job.maps = out_maps ? out_maps + (int64_t)g0 * d.n_fdot * d.n_f0 : nullptr;
         job.item_begin = 0;
-        job.n_items = per_dir * n_dir;
+        job.n_items = per_dir * gn;
+        job.windows = p->win;
+        e = launch_windows(job, p->win, s);
+        if (e != cudaSuccess) return cuda_error(e, "windows launch");
+        ++p->launches;
         tbl.job[0] = job;
-        const int64_t cap = (int64_t)p->n_sm * bps;
-        const int32_t grid = (int32_t)std::min<int64_t>(job.n_items, cap);
-        e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, guard, s);
+        if (schedule == FH_SCHED_PLAIN) {
+            // one sky direction per launch, one block per work item
+            e = launch_transform(p->mode, tbl, job.n_items, (int32_t)job.n_items, nwarps, smem,
+                                 guard, s);
+        } else {
+            const int64_t cap = (int64_t)p->n_sm * bps;
+            const int32_t grid = (int32_t)std::min<int64_t>(job.n_items, cap);
+            e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, guard, s);
+        }
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
         ++p->launches;
     }

@@ -46,6 +46,8 @@ struct TransformJob {
     int32_t *maps;           // nullable, [dir - dir_begin][n_fdot][n_f0]
     const int32_t *bidx;     // nullable bucket index [dir][n_fft][bnb]
     const unsigned long long *dmax;  // max_i |D_i| (32.32 cells per row), from a3
+    const int2 *windows;     // nullable: precomputed peak windows (first, end) per
+                             // [dir - dir_begin][slab][tile][fft]; else looked up
     int32_t bbase, bgsh, bnb;
     int64_t n_peaks;
     int64_t item_begin;      // first work item of this job in the launch
@@ -97,6 +99,9 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
                              int32_t grid, int32_t nwarps, size_t smem, int32_t guard,
                              cudaStream_t s);
 int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem);
+// Peak windows of every (direction, slab, tile, FFT) of a job, written to
+// job.windows (the job's other fields as for the transform).
+cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, cudaStream_t s);
 cudaError_t launch_smem_atomic_bench(int32_t variant, int32_t iters, int32_t grid,
                                      unsigned long long *sink, cudaStream_t s);

@@ -259,6 +259,162 @@ __device__ __forceinline__ int64_t first_at_least(const int64_t *__restrict__ Ad
 //   e[b] = +-(D << b), sign + when the lane's bit b is set
 // An update whose cell falls outside the tile goes to the dump cell E (never
 // read), so every step issues its atomic unconditionally -- no branch.
+// Peak windows of NF FFTs per lane, with every load of the NF lookups issued
+// together (three dependent rounds: CSR/shift tables, bucket entries, positions)
+// instead of one lookup after the other.  For FFT i on rows j0 .. j0 + R - 1 of
+// a tile whose stripe starts L lie in [0, E): the peaks with lo <= A < hi,
+// lo = cb + min(0, (R-1) D), hi = cb + max(0, (R-1) D) + E 2^32, cb = S0 + j0 D
+// + tile origin.  Outputs: cb, D, first peak q0 and count n (0 for i >= n_fft).
+// Every index stays inside the FFT's CSR range for any input.
+template <int NF>
+__device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
+                                               const int64_t *__restrict__ offs,
+                                               const int64_t *__restrict__ S0,
+                                               const int64_t *__restrict__ Dt,
+                                               const int32_t *__restrict__ bidx, int32_t bbase,
+                                               int32_t bgsh, int32_t bnb, int n_fft, int j0, int R,
+                                               int64_t base_shift, int64_t e_fixed,
+                                               const int (&fi)[NF], int64_t (&cb)[NF],
+                                               int64_t (&dv)[NF], int64_t (&q0)[NF], int (&n)[NF])
+{
+    int64_t o0[NF], o1[NF], lo[NF], hi[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const bool ok = fi[f] < n_fft;
+        const int i = ok ? fi[f] : 0;
+        o0[f] = ok ? __ldg(offs + i) : 0;
+        o1[f] = ok ? __ldg(offs + i + 1) : 0;
+        dv[f] = ok ? __ldg(Dt + i) : 0;
+        const int64_t s0 = ok ? __ldg(S0 + i) : 0;
+        cb[f] = s0 + (int64_t)j0 * dv[f] + base_shift;
+        const int64_t span = (int64_t)(R - 1) * dv[f];
+        lo[f] = cb[f] + (span < 0 ? span : 0);
+        hi[f] = cb[f] + (span > 0 ? span : 0) + e_fixed;
+    }
+    if (bidx == nullptr) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            int64_t a = o0[f], b = o1[f];
+            while (a < b) {
+                const int64_t m = (a + b) >> 1;
+                if (__ldg(Ad + m) < lo[f]) a = m + 1; else b = m;
+            }
+            q0[f] = a;
+            b = o1[f];
+            while (a < b) {
+                const int64_t m = (a + b) >> 1;
+                if (__ldg(Ad + m) < hi[f]) a = m + 1; else b = m;
+            }
+            n[f] = (int)(a - q0[f]);
+        }
+        return;
+    }
+    // bucket entries: lower bounds of the first peak >= lo and >= hi
+    int64_t ql[NF], qh[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const bool ok = fi[f] < n_fft;
+        const int32_t *brow = bidx + (int64_t)(ok ? fi[f] : 0) * bnb;
+        const int32_t cnt = (int32_t)(o1[f] - o0[f]);
+        int gl = ((int)(lo[f] >> 32) - bbase) >> bgsh;
+        int gh = ((int)(hi[f] >> 32) - bbase) >> bgsh;
+        const int32_t rl = (ok && gl >= 0) ? __ldg(brow + (gl < bnb ? gl : bnb - 1)) : 0;
+        const int32_t rh = (ok && gh >= 0) ? __ldg(brow + (gh < bnb ? gh : bnb - 1)) : 0;
+        ql[f] = o0[f] + (rl < 0 ? 0 : (rl > cnt ? cnt : rl));
+        qh[f] = o0[f] + (rh < 0 ? 0 : (rh > cnt ? cnt : rh));
+    }
+    // forward scans, four positions at a time, all NF x 2 scans' loads together
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        int64_t al[4], ah[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            al[m] = ql[f] + m < o1[f] ? __ldg(Ad + ql[f] + m) : LLONG_MAX;
+            ah[m] = qh[f] + m < o1[f] ? __ldg(Ad + qh[f] + m) : LLONG_MAX;
+        }
+        int kl = 0, kh = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            kl += al[m] < lo[f];
+            kh += ah[m] < hi[f];
+        }
+        ql[f] += kl;
+        qh[f] += kh;
+        // rare: more than four peaks inside one bucket before the bound
+        while (kl == 4) {
+            kl = 0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                kl += (ql[f] + m < o1[f] ? __ldg(Ad + ql[f] + m) : LLONG_MAX) < lo[f];
+            ql[f] += kl;
+        }
+        if (qh[f] < ql[f]) {
+            qh[f] = ql[f];
+            kh = 4;
+        }
+        while (kh == 4) {
+            kh = 0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                kh += (qh[f] + m < o1[f] ? __ldg(Ad + qh[f] + m) : LLONG_MAX) < hi[f];
+            qh[f] += kh;
+        }
+        q0[f] = ql[f];
+        n[f] = (int)(qh[f] - ql[f]);
+    }
+}
+
+// The transform's peak window of every (direction, slab, tile, FFT).  A block
+// takes 32 FFTs of one (direction, slab); a warp takes one FFT at a time and
+// its lanes take consecutive tiles, so neighbouring lanes read neighbouring
+// bucket entries and position ranges (mostly L1 hits).  Results are staged in
+// shared memory as [FFT][tile] and written out as [tile][FFT], coalesced over
+// FFTs, the layout the transform reads with one 8-byte load per lane.
+// grid (ceil(n_fft / 32), n_dir * n_slabs), 256 threads.
+constexpr int kWinTiles = 64;  // tiles staged per pass
+__global__ void __launch_bounds__(256)
+windows_kernel(const TransformJob J, int2 *__restrict__ windows)
+{
+    __shared__ int2 stage[32][kWinTiles + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int f0 = blockIdx.x * 32;
+    const int d_rel = blockIdx.y / J.n_slabs;
+    const int slab = blockIdx.y - d_rel * J.n_slabs;
+    const int K = J.k_over, W = J.tile_cells;
+    const int j0 = slab * kRows;
+    const int R = min(kRows, J.n_fdot - j0);
+    const int d_abs = J.dir_begin + d_rel;
+    const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
+    const int32_t *bidx = J.bidx ? J.bidx + (int64_t)d_abs * J.n_fft * J.bnb : nullptr;
+    int2 *out = windows + ((int64_t)d_rel * J.n_slabs + slab) * J.n_tiles * (int64_t)J.n_fft;
+    for (int t0 = 0; t0 < J.n_tiles; t0 += kWinTiles) {
+        const int nt = min(kWinTiles, J.n_tiles - t0);
+        for (int f = warp; f < 32; f += 8) {
+            const int i = f0 + f;
+            if (i >= J.n_fft) break;
+            for (int tt = lane; tt < nt; tt += 32) {
+                const int tile = t0 + tt;
+                const int b0 = tile * W;
+                const int Wt = min(W, J.n_f0 - b0);
+                const int E = Wt + K - 1;
+                const int fi[1] = {i};
+                int64_t cb[1], dv[1], q0[1];
+                int n[1];
+                lookup_windows<1>(Ad, J.offsets, J.S0, J.D, bidx, J.bbase, J.bgsh, J.bnb,
+                                  J.n_fft, j0, R, (int64_t)(b0 - K + 1) * 4294967296LL,
+                                  (int64_t)E * 4294967296LL, fi, cb, dv, q0, n);
+                stage[f][tt] = make_int2((int)q0[0], (int)(q0[0] + n[0]));
+            }
+        }
+        __syncthreads();
+        for (int tt = warp; tt < nt; tt += 8) {
+            const int i = f0 + lane;
+            if (i < J.n_fft) out[(int64_t)(t0 + tt) * J.n_fft + i] = stage[lane][tt];
+        }
+        __syncthreads();
+    }
+}
+
 __host__ __device__ constexpr int ctz5(int x)
 {
     return (x & 1) ? 0 : (x & 2) ? 1 : (x & 4) ? 2 : (x & 8) ? 3 : 4;
@@ -434,6 +590,10 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int32_t *__restrict__ bidx =
             J->bidx ? J->bidx + (int64_t)d_abs * n_fft * J->bnb : nullptr;
         const int32_t bbase = J->bbase, bgsh = J->bgsh, bnb = J->bnb;
+        const int2 *__restrict__ wrow =
+            J->windows ? J->windows + (((int64_t)d_rel * J->n_slabs + slab) * J->n_tiles + tile) *
+                                          n_fft
+                       : nullptr;
         const bool row_ok = lane < R;
         // fast path when the job's largest drift over 32 rows stays inside the guards
         const bool fast = MODE == FH_MODE_START && J->dmax != nullptr &&
@@ -452,22 +612,38 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int64_t base_shift = (int64_t)(b0 - K + 1) * 4294967296LL;
         const int64_t e_fixed = (int64_t)E * 4294967296LL;
         const int nchunks = (n_fft + 31) >> 5;
-        // chunks of 32 FFTs: the first round one per warp, then whoever is free
+        // chunks of 32 FFTs (lane <-> FFT): the first round one per warp, then
+        // whoever is free
         for (int c = warp; c < nchunks;) {
-            const int i = (c << 5) + lane;
-            int64_t cb = 0, dv = 0, q0 = 0;
-            int n = 0;
-            if (i < n_fft) {
-                const int64_t o0 = offs[i], o1 = offs[i + 1];
-                dv = Dt[i];
-                cb = S0[i] + (int64_t)j0 * dv + base_shift;
-                const int64_t span = (int64_t)(R - 1) * dv;
-                const int64_t lo = cb + (span < 0 ? span : 0);
-                const int64_t hi = cb + (span > 0 ? span : 0) + e_fixed;
-                const int32_t *brow = bidx ? bidx + (int64_t)i * bnb : nullptr;
-                q0 = first_at_least(Ad, brow, bbase, bgsh, bnb, o0, o0, o1, lo);
-                const int64_t q1 = first_at_least(Ad, brow, bbase, bgsh, bnb, o0, q0, o1, hi);
-                n = (int)(q1 - q0);
+            int64_t cb, dv, q0;
+            int n;
+            if (wrow != nullptr) {
+                // precomputed window: one coalesced load, clamped into the FFT's CSR range
+                const int i = (c << 5) + lane;
+                cb = 0;
+                dv = 0;
+                q0 = 0;
+                n = 0;
+                if (i < n_fft) {
+                    const int2 wv = wrow[i];
+                    const int64_t o0 = __ldg(offs + i), o1 = __ldg(offs + i + 1);
+                    dv = __ldg(Dt + i);
+                    cb = __ldg(S0 + i) + (int64_t)j0 * dv + base_shift;
+                    const int64_t a = wv.x < o0 ? o0 : (wv.x > o1 ? o1 : wv.x);
+                    const int64_t b = wv.y < a ? a : (wv.y > o1 ? o1 : wv.y);
+                    q0 = a;
+                    n = (int)(b - a);
+                }
+            } else {
+                const int fi[1] = {(c << 5) + lane};
+                int64_t cb1[1], dv1[1], q01[1];
+                int n1[1];
+                lookup_windows<1>(Ad, offs, S0, Dt, bidx, bbase, bgsh, bnb, n_fft, j0, R,
+                                  base_shift, e_fixed, fi, cb1, dv1, q01, n1);
+                cb = cb1[0];
+                dv = dv1[0];
+                q0 = q01[0];
+                n = n1[0];
             }
             // exclusive scan of the per-FFT counts, owner table of non-empty FFTs
             int P = n;
@@ -609,13 +785,28 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             }
         };
         if (MODE == FH_MODE_START) {
+            // a K-cell window slides along the segment (count of cell c = sum of
+            // the starts in cells c .. c + K - 1); eight cells per batch so that
+            // their shared loads and their warp reductions are independent
+            constexpr int kC = 8;
             int win = 0;
             if (c0 < c1)
-                for (int L = c0; L < c0 + K - 1; ++L) win += H[L * kRows + lane];
-            for (int c = c0; c < c1; ++c) {
-                win += H[(c + K - 1) * kRows + lane];
+                for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
+            int c = c0;
+            for (; c + kC <= c1; c += kC) {
+                int cnt[kC];
+#pragma unroll
+                for (int m = 0; m < kC; ++m) {
+                    cnt[m] = win;
+                    // the last step may read cell E (the dump cell); that value is unused
+                    win += H[(c + m + K) * kRows + lane] - H[(c + m) * kRows + lane];
+                }
+#pragma unroll
+                for (int m = 0; m < kC; ++m) emit(c + m, cnt[m]);
+            }
+            for (; c < c1; ++c) {
                 emit(c, win);
-                win -= H[c * kRows + lane];
+                win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
             }
         } else {
             int32_t *segtot = Hlo + hist_words + nwarps * 32;
@@ -885,6 +1076,14 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
         k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u);
         return cudaSuccess;
     });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t s)
+{
+    if (job.n_fft <= 0 || job.n_dir <= 0) return cudaSuccess;
+    dim3 grid((job.n_fft + 31) / 32, job.n_dir * job.n_slabs);
+    windows_kernel<<<grid, 256, 0, s>>>(job, windows);
     return cudaGetLastError();
 }
 
