@@ -167,7 +167,7 @@ Sizes plan_sizes(const fh_plan_desc &d)
     s.A = 8 * (int64_t)d.max_dir * d.max_peaks;
     s.profile = 8 * (int64_t)d.max_dir * d.n_f0;
     s.cand = (int64_t)sizeof(fh_candidate) * d.max_dir * n_sb * d.top_k;
-    s.bidx = 4 * (int64_t)d.max_dir * d.max_fft * plan_buckets(d).nb;
+    s.bidx = 0;  // plans search positions directly (see fh_correct_doppler)
     return s;
 }
 
@@ -363,8 +363,7 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                   {(void **)&p->freq, s.freq},     {(void **)&p->v, s.v},
                   {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
                   {(void **)&p->profile, s.profile}, {(void **)&p->cand, s.cand},
-                  {(void **)&p->err, 16},          {(void **)&p->bix.idx, s.bidx},
-                  {(void **)&p->dmax, 16}};
+                  {(void **)&p->err, 16},          {(void **)&p->dmax, 16}};
     for (auto &a : allocs) {
         e = cudaMalloc(a.ptr, (size_t)std::max<int64_t>(a.bytes, 16));
         if (e != cudaSuccess) {
@@ -465,8 +464,10 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     e = launch_shift_tables(t_src, n, d.t_ref, p->kt, d.fdot_min, d.fdot_step, d.n_fdot, p->S0,
                             p->D, p->dmax, p->err, s);
     if (e != cudaSuccess) return cuda_error(e, "shift_tables launch");
+    // the plan's transform reads precomputed windows, whose pre-pass searches
+    // each FFT's (L1-resident) positions directly: no bucket index needed
     e = launch_positions(f_src, p->offsets, v_src, sky_src, n, np, n_dir, d.f0_min, p->kt,
-                         d.k_over, p->A, out_r, p->err, p->bix, s);
+                         d.k_over, p->A, out_r, p->err, BucketIndex{}, s);
     if (e != cudaSuccess) return cuda_error(e, "positions launch");
     p->launches += (n > 0) ? 2 : 0;
     if (out_A && np > 0) {
@@ -499,7 +500,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.S0 = p->S0;
     job.D = p->D;
     job.profile = p->profile;
-    job.bidx = p->bix.idx;
+    job.bidx = nullptr;
     job.dmax = p->dmax;
     job.bbase = p->bix.base;
     job.bgsh = p->bix.gsh;
@@ -518,8 +519,8 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     // peak windows of a group of directions (bounded table), then the transform
     const size_t per_dir_win = sizeof(int2) * (size_t)per_dir * (size_t)std::max(1, p->n_fft);
     const size_t win_cap = std::max(per_dir_win, (size_t)1 << 30);
-    // (the windows grid has n_dir x n_slabs blocks along y: at most 65535)
-    const size_t zcap = (size_t)std::max(1, 65535 / job.n_slabs);
+    // (the windows grid has one block row per direction: at most 65535)
+    const size_t zcap = 65535;
     const int32_t group = schedule == FH_SCHED_PLAIN
                               ? 1
                               : (int32_t)std::max<size_t>(1, std::min<size_t>(

@@ -365,53 +365,97 @@ __device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
 }
 
 // The transform's peak window of every (direction, slab, tile, FFT).  A block
-// takes 32 FFTs of one (direction, slab); a warp takes one FFT at a time and
-// its lanes take consecutive tiles, so neighbouring lanes read neighbouring
-// bucket entries and position ranges (mostly L1 hits).  Results are staged in
-// shared memory as [FFT][tile] and written out as [tile][FFT], coalesced over
-// FFTs, the layout the transform reads with one 8-byte load per lane.
-// grid (ceil(n_fft / 32), n_dir * n_slabs), 256 threads.
-constexpr int kWinTiles = 64;  // tiles staged per pass
+// takes 8 FFTs of one direction, one warp per FFT; the warp copies its FFT's
+// ascending positions into shared memory once (an FFT with more than
+// kWinPeaks peaks is read from global memory instead).  Lanes take tiles, 64
+// at a time, and walk the slabs in order: the first slab's bounds come from a
+// binary search, each later one from a short linear step away from the
+// previous slab's bounds (a slab moves a window by at most a few cells).
+// Each (slab, 64 tiles) result is staged as [tile][FFT] and written as 64-byte
+// runs of 8 FFTs, the layout the transform reads with one 8-byte load per lane.
+// grid (ceil(n_fft / 8), n_dir), 256 threads.
+constexpr int kWinPeaks = 640;
+constexpr int kWinTiles = 64;
+__device__ __forceinline__ int lower_bound_pos(const int64_t *a, int n, int64_t x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] < x) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+__device__ __forceinline__ int step_bound(const int64_t *a, int n, int q, int64_t x)
+{
+    while (q > 0 && a[q - 1] >= x) --q;
+    while (q < n && a[q] < x) ++q;
+    return q;
+}
+
 __global__ void __launch_bounds__(256)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
-    __shared__ int2 stage[32][kWinTiles + 1];
+    __shared__ int64_t pos_s[8][kWinPeaks];
+    __shared__ int2 stage[kWinTiles][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int f0 = blockIdx.x * 32;
-    const int d_rel = blockIdx.y / J.n_slabs;
-    const int slab = blockIdx.y - d_rel * J.n_slabs;
-    const int K = J.k_over, W = J.tile_cells;
-    const int j0 = slab * kRows;
-    const int R = min(kRows, J.n_fdot - j0);
+    const int i = blockIdx.x * 8 + warp;
+    const bool live = i < J.n_fft;
+    const int d_rel = blockIdx.y;
     const int d_abs = J.dir_begin + d_rel;
     const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
-    const int32_t *bidx = J.bidx ? J.bidx + (int64_t)d_abs * J.n_fft * J.bnb : nullptr;
-    int2 *out = windows + ((int64_t)d_rel * J.n_slabs + slab) * J.n_tiles * (int64_t)J.n_fft;
+    const int64_t o0 = live ? J.offsets[i] : 0;
+    const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
+    const int64_t *pos = Ad + o0;
+    if (n <= kWinPeaks) {
+        for (int k = lane; k < n; k += 32) pos_s[warp][k] = pos[k];
+        __syncwarp();
+        pos = pos_s[warp];
+    }
+    const int64_t dv = live ? J.D[i] : 0;
+    const int64_t s0 = live ? J.S0[i] : 0;
+    const int K = J.k_over, W = J.tile_cells;
+    const int64_t nf = J.n_fft;
+    int2 *out = windows + (int64_t)d_rel * J.n_slabs * J.n_tiles * nf;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kWinTiles) {
         const int nt = min(kWinTiles, J.n_tiles - t0);
-        for (int f = warp; f < 32; f += 8) {
-            const int i = f0 + f;
-            if (i >= J.n_fft) break;
-            for (int tt = lane; tt < nt; tt += 32) {
-                const int tile = t0 + tt;
-                const int b0 = tile * W;
-                const int Wt = min(W, J.n_f0 - b0);
-                const int E = Wt + K - 1;
-                const int fi[1] = {i};
-                int64_t cb[1], dv[1], q0[1];
-                int n[1];
-                lookup_windows<1>(Ad, J.offsets, J.S0, J.D, bidx, J.bbase, J.bgsh, J.bnb,
-                                  J.n_fft, j0, R, (int64_t)(b0 - K + 1) * 4294967296LL,
-                                  (int64_t)E * 4294967296LL, fi, cb, dv, q0, n);
-                stage[f][tt] = make_int2((int)q0[0], (int)(q0[0] + n[0]));
+        int qa[2] = {0, 0}, qb[2] = {0, 0};
+        for (int slab = 0; slab < J.n_slabs; ++slab) {
+            const int j0 = slab * kRows;
+            const int R = min(kRows, J.n_fdot - j0);
+            const int64_t span = (int64_t)(R - 1) * dv;
+            if (live) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int tt = lane + 32 * h;
+                    if (tt < nt) {
+                        const int b0 = (t0 + tt) * W;
+                        const int Wt = min(W, J.n_f0 - b0);
+                        const int64_t cb =
+                            s0 + (int64_t)j0 * dv + (int64_t)(b0 - K + 1) * 4294967296LL;
+                        const int64_t lo = cb + (span < 0 ? span : 0);
+                        const int64_t hi =
+                            cb + (span > 0 ? span : 0) + (int64_t)(Wt + K - 1) * 4294967296LL;
+                        if (slab == 0) {
+                            qa[h] = lower_bound_pos(pos, n, lo);
+                            qb[h] = lower_bound_pos(pos, n, hi);
+                        } else {
+                            qa[h] = step_bound(pos, n, qa[h], lo);
+                            qb[h] = step_bound(pos, n, qb[h], hi);
+                        }
+                        stage[tt][warp] =
+                            make_int2((int)(o0 + qa[h]), (int)(o0 + max(qa[h], qb[h])));
+                    }
+                }
             }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nt * 8; e += 256) {
+                const int tt = e >> 3, f = e & 7;
+                const int fi = blockIdx.x * 8 + f;
+                if (fi < J.n_fft)
+                    out[((int64_t)slab * J.n_tiles + t0 + tt) * nf + fi] = stage[tt][f];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int tt = warp; tt < nt; tt += 8) {
-            const int i = f0 + lane;
-            if (i < J.n_fft) out[(int64_t)(t0 + tt) * J.n_fft + i] = stage[lane][tt];
-        }
-        __syncthreads();
     }
 }
 
@@ -826,13 +870,14 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
 }
 
 // ---------------------------------------------------------------- a6
-// grid (n_sb, n_dir), 256 threads: greedy picks of one sub-band of one direction.
-__global__ void __launch_bounds__(256) select_kernel(const SelectArgs a)
+// grid (n_sb, n_dir), 1024 threads: greedy picks of one sub-band of one direction.
+constexpr int kSelThreads = 1024;
+__global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectArgs a)
 {
     __shared__ int picks[64];
     __shared__ unsigned long long pkey[64];
-    __shared__ unsigned long long wkey[8];
-    __shared__ int wcell[8];
+    __shared__ unsigned long long wkey[kSelThreads / 32];
+    __shared__ int wcell[kSelThreads / 32];
     __shared__ int npick, stop;
     const int q = blockIdx.x, d_rel = blockIdx.y;
     const int lo = q * a.subband_cells;
@@ -1082,7 +1127,7 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
 cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t s)
 {
     if (job.n_fft <= 0 || job.n_dir <= 0) return cudaSuccess;
-    dim3 grid((job.n_fft + 31) / 32, job.n_dir * job.n_slabs);
+    dim3 grid((job.n_fft + 7) / 8, job.n_dir);
     windows_kernel<<<grid, 256, 0, s>>>(job, windows);
     return cudaGetLastError();
 }
@@ -1091,7 +1136,7 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t s)
 {
     if (a.n_dir <= 0 || a.n_sb <= 0) return cudaSuccess;
     dim3 grid(a.n_sb, a.n_dir);
-    select_kernel<<<grid, 256, 0, s>>>(a);
+    select_kernel<<<grid, kSelThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
