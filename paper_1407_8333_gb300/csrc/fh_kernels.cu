@@ -698,45 +698,42 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             }
             const int T = __shfl_sync(kFull, P, 31);
             P -= n;
-            const unsigned nonempty = __ballot_sync(kFull, n > 0);
-            if (n > 0) tab[__popc(nonempty & lanemask_lt)] = lane;
+            const bool has = n > 0;
+            const unsigned nonempty = __ballot_sync(kFull, has);
+            if (has) tab[__popc(nonempty & lanemask_lt)] = lane;
+            // position index of slot g of this FFT: delta + g
+            const int64_t delta = q0 - P;
             __syncwarp();
 
-            // deal the T peaks out to the lanes: position g = base + lane of a round
-            // belongs to the non-empty FFT whose range [P, P + n) holds it
+            // deal the T peaks out to the lanes: slot g = base + lane of a round
+            // belongs to the non-empty FFT whose range [P, P + n) holds it.
+            // `before` counts the non-empty FFTs starting below the base; bases
+            // are fetched in increasing order, 32 apart.
+            int before = 0;
             auto fetch = [&](int base, int64_t &a, int &owner) {
-                const bool starts = n > 0 && P >= base && P < base + 32;
-                const unsigned bits = __reduce_or_sync(kFull, starts ? (1u << (P - base)) : 0u);
-                const int before = (int)__reduce_add_sync(kFull, (n > 0 && P < base) ? 1u : 0u);
-                int oc = before + __popc(bits & lanemask_le) - 1;
-                oc = oc < 0 ? 0 : oc;
-                owner = tab[oc];
-                const int64_t oq0 = __shfl_sync(kFull, q0, owner);
-                const int oP = __shfl_sync(kFull, P, owner);
+                const unsigned rel = (unsigned)(P - base);
+                const unsigned bits = __reduce_or_sync(kFull, (has && rel < 32u) ? (1u << rel) : 0u);
+                const int oc = before + __popc(bits & lanemask_le) - 1;
+                before += __popc(bits);
+                owner = tab[oc < 0 ? 0 : oc];
+                const int64_t od = __shfl_sync(kFull, delta, owner);
                 const int g = base + lane;
-                a = g < T ? __ldg(Ad + oq0 + (g - oP)) : 0;
+                a = g < T ? __ldg(Ad + od + g) : 0;
             };
-            // X of the lane's row and its step table for the peak at position g;
-            // positions beyond T are parked in guard cell -1 (never read)
-            auto setup = [&](int g, int64_t a, int owner, int64_t &X, int64_t (&e)[5],
-                             bool &inside) {
+            // X of the lane's row and its step table for the peak in slot g.  Slots
+            // beyond T are parked in guard cell -1 with zero steps (never read; the
+            // clamped walk sends them to the dump cell).  On the unclamped walk
+            // every windowed peak's 32 rows stay inside the guard cells: the
+            // window holds the peaks with A - cb in [min(0, (R-1) D), max(0,
+            // (R-1) D) + E 2^32), and |31 D| stays below guard - 1 cells.
+            auto setup = [&](int g, int64_t a, int owner, int64_t &X, int64_t (&e)[5]) {
                 const int64_t ocb = __shfl_sync(kFull, cb, owner);
-                const int64_t odv = __shfl_sync(kFull, dv, owner);
+                const int64_t odv0 = __shfl_sync(kFull, dv, owner);
+                const bool live = g < T;
+                const int64_t odv = live ? odv0 : 0;
 #pragma unroll
                 for (int b = 0; b < 5; ++b) e[b] = (int64_t)mult[b] * odv;
-                X = a - ocb - (int64_t)lane * odv;
-                // rows 0 and 31 bound the 32 rows' cells (X is linear in the row)
-                const int64_t Xr0 = a - ocb;
-                const int64_t Xr31 = Xr0 - 31 * odv;
-                const uint32_t span_ok = (uint32_t)(E + 2 * guard);
-                inside = (uint32_t)((int32_t)(Xr0 >> 32) + guard) < span_ok &&
-                         (uint32_t)((int32_t)(Xr31 >> 32) + guard) < span_ok;
-                if (g >= T) {
-#pragma unroll
-                    for (int b = 0; b < 5; ++b) e[b] = 0;
-                    X = -(int64_t(1) << 32);
-                    inside = true;
-                }
+                X = live ? a - ocb - (int64_t)lane * odv : -(int64_t(1) << 32);
             };
             constexpr bool kTwoPeaks = MODE == FH_MODE_START && MAXT <= 512;
             int64_t a_nx = 0, a2_nx = 0;
@@ -752,10 +749,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     if (base + 64 < T) fetch(base + 64, a_nx, own_nx);
                     if (base + 96 < T) fetch(base + 96, a2_nx, own2_nx);
                     int64_t X1, X2, e1[5], e2[5];
-                    bool in1, in2;
-                    setup(base + lane, a1, o1, X1, e1, in1);
-                    setup(base + 32 + lane, a2, o2, X2, e2, in2);
-                    if (__all_sync(kFull, fast && in1 && in2)) {
+                    setup(base + lane, a1, o1, X1, e1);
+                    setup(base + 32 + lane, a2, o2, X2, e2);
+                    if (fast) {
                         start_steps2(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e1, e2,
                                      cell_stride);
                     } else {
@@ -772,10 +768,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 const int owner = own_nx;
                 if (!kTwoPeaks && base + 32 < T) fetch(base + 32, a_nx, own_nx);
                 int64_t X, e[5];
-                bool inside;
-                setup(base + lane, a, owner, X, e, inside);
+                setup(base + lane, a, owner, X, e);
                 if (MODE == FH_MODE_START) {
-                    if (__all_sync(kFull, fast && inside))
+                    if (fast)
                         start_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
                                            cell_stride, (uint32_t)E);
                     else
@@ -793,76 +788,99 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         __syncthreads();
 
         // emit counts, map and profile
-        const int seg = (Wt + nwarps - 1) / nwarps;
-        const int c0 = min(Wt, warp * seg);
-        const int c1 = min(Wt, c0 + seg);
         int32_t *maprow = nullptr;
         if (J->maps != nullptr && row_ok)
             maprow = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
         unsigned long long *prof =
             reinterpret_cast<unsigned long long *>(J->profile) + (int64_t)d_abs * n_f0 + b0;
-        // per cell: the warp's max over its rows, smallest row on ties.  Counts
-        // below 2^26 fit one packed reduction (count << 5 | 31 - lane); the
-        // cell's lane keeps the key and every lane issues one profile atomic
-        // per 32 cells
+        // Per cell the profile takes the warp's max over its rows, smallest row
+        // on ties.  Counts below 2^26 fit one packed signed reduction
+        // 32 count + (31 - lane); rows beyond the slab start their window at
+        // -2^26, so they stay negative and never win.
         const bool packed = J->n_peaks < (int64_t(1) << 26);
-        unsigned long long mykey = 0;
-        auto emit = [&](int c, int count) {
-            if (maprow) maprow[c] = count;
-            unsigned cm, rm;
-            if (packed) {
-                const unsigned v = __reduce_max_sync(
-                    kFull, row_ok ? ((unsigned)count << 5) | (unsigned)(31 - lane) : 0u);
-                cm = v >> 5;
-                rm = 31u - (v & 31u);
-            } else {
-                const int m = __reduce_max_sync(kFull, row_ok ? count : INT_MIN);
-                cm = (unsigned)m;
-                rm = __reduce_min_sync(kFull, (row_ok && count == m) ? (unsigned)lane : 32u);
-            }
-            const unsigned long long key = ((unsigned long long)cm << 32) |
-                                           (0xFFFFFFFFull - (unsigned long long)(unsigned)(j0 + rm));
-            if (lane == ((c - c0) & 31)) mykey = key;
-            if (((c - c0) & 31) == 31 || c == c1 - 1) {
-                const int first = c - ((c - c0) & 31);
-                if (first + lane <= c) atomicMax(prof + first + lane, mykey);
-            }
+        const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 31u;
+        auto key_of = [&](int v) {
+            return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
+                   (unsigned long long)(key_lo + (uint32_t)(v & 31));
         };
-        if (MODE == FH_MODE_START) {
-            // a K-cell window slides along the segment (count of cell c = sum of
-            // the starts in cells c .. c + K - 1); eight cells per batch so that
-            // their shared loads and their warp reductions are independent
-            constexpr int kC = 8;
-            int win = 0;
+        if (MODE == FH_MODE_START && packed) {
+            // a K-cell window slides along the warp's segment (count of cell c =
+            // sum of the starts in cells c .. c + K - 1), 16 cells per group:
+            // lane m keeps cell m's reduction and the group's 16 profile atomics
+            // go out together
+            const int seg = (((Wt + nwarps - 1) / nwarps) + 15) & ~15;
+            const int c0 = min(Wt, warp * seg);
+            const int c1 = min(Wt, c0 + seg);
+            const int c31 = 31 - lane;
+            int win = row_ok ? 0 : -(1 << 26);
             if (c0 < c1)
                 for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
-            int c = c0;
-            for (; c + kC <= c1; c += kC) {
-                int cnt[kC];
+            auto run = [&](auto map_tag) {
+                constexpr bool kMap = decltype(map_tag)::value;
+                int c = c0;
+                for (; c + 16 <= c1; c += 16) {
+                    const int32_t *h0 = H + c * kRows + lane;
+                    const int32_t *h1 = h0 + K * kRows;
+                    int myv = 0;
 #pragma unroll
-                for (int m = 0; m < kC; ++m) {
-                    cnt[m] = win;
-                    // the last step may read cell E (the dump cell); that value is unused
-                    win += H[(c + m + K) * kRows + lane] - H[(c + m) * kRows + lane];
+                    for (int m = 0; m < 16; ++m) {
+                        const int cnt = win;
+                        win += h1[m * kRows] - h0[m * kRows];
+                        if (kMap && row_ok) maprow[c + m] = cnt;
+                        const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
+                        if (lane == m) myv = v;
+                    }
+                    if (lane < 16) atomicMax(prof + c + lane, key_of(myv));
                 }
-#pragma unroll
-                for (int m = 0; m < kC; ++m) emit(c + m, cnt[m]);
-            }
-            for (; c < c1; ++c) {
-                emit(c, win);
-                win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
-            }
+                for (; c < c1; ++c) {
+                    const int cnt = win;
+                    // the segment's last step may read cell E (the dump cell); that value is unused
+                    win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
+                    if (kMap && row_ok) maprow[c] = cnt;
+                    const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
+                    if (lane == 0) atomicMax(prof + c, key_of(v));
+                }
+            };
+            if (J->maps != nullptr)
+                run(std::true_type{});
+            else
+                run(std::false_type{});
         } else {
-            int32_t *segtot = Hlo + hist_words + nwarps * 32;
-            int tot = 0;
-            for (int c = c0; c < c1; ++c) tot += H[c * kRows + lane];
-            segtot[warp * 32 + lane] = tot;
-            __syncthreads();
-            int acc = 0;
-            for (int w = 0; w < warp; ++w) acc += segtot[w * 32 + lane];
-            for (int c = c0; c < c1; ++c) {
-                acc += H[c * kRows + lane];
-                emit(c, acc);
+            // generic path (DIFF mode, or counts too large to pack): one cell at a
+            // time, lane 0 takes the profile atomic
+            const int seg = (Wt + nwarps - 1) / nwarps;
+            const int c0 = min(Wt, warp * seg);
+            const int c1 = min(Wt, c0 + seg);
+            auto emit = [&](int c, int count) {
+                if (maprow) maprow[c] = count;
+                const int m = __reduce_max_sync(kFull, row_ok ? count : INT_MIN);
+                const unsigned rm =
+                    __reduce_min_sync(kFull, (row_ok && count == m) ? (unsigned)lane : 32u);
+                const unsigned long long key =
+                    ((unsigned long long)(unsigned)m << 32) |
+                    (0xFFFFFFFFull - (unsigned long long)(unsigned)(j0 + rm));
+                if (lane == 0) atomicMax(prof + c, key);
+            };
+            if (MODE == FH_MODE_START) {
+                int win = 0;
+                if (c0 < c1)
+                    for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
+                for (int c = c0; c < c1; ++c) {
+                    emit(c, win);
+                    win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
+                }
+            } else {
+                int32_t *segtot = Hlo + hist_words + nwarps * 32;
+                int tot = 0;
+                for (int c = c0; c < c1; ++c) tot += H[c * kRows + lane];
+                segtot[warp * 32 + lane] = tot;
+                __syncthreads();
+                int acc = 0;
+                for (int w = 0; w < warp; ++w) acc += segtot[w * 32 + lane];
+                for (int c = c0; c < c1; ++c) {
+                    acc += H[c * kRows + lane];
+                    emit(c, acc);
+                }
             }
         }
         __syncthreads();
