@@ -366,13 +366,14 @@ __device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
 
 // The transform's peak window of every (direction, slab, tile, FFT).  A block
 // takes 8 FFTs of one direction, one warp per FFT; the warp copies its FFT's
-// ascending positions into shared memory once (an FFT with more than
-// kWinPeaks peaks is read from global memory instead).  Lanes take tiles, 64
-// at a time, and walk the slabs in order: the first slab's bounds come from a
-// binary search, each later one from a short linear step away from the
-// previous slab's bounds (a slab moves a window by at most a few cells).
-// Each (slab, 64 tiles) result is staged as [tile][FFT] and written as 64-byte
-// runs of 8 FFTs, the layout the transform reads with one 8-byte load per lane.
+// ascending positions into shared memory once, between two sentinels (an FFT
+// with more than kWinPeaks - 2 peaks is read from global memory instead, with
+// bounds checks).  Lanes take tiles, 64 at a time, and walk the slabs in
+// order: the first slab's bounds come from a binary search, each later one
+// from a short linear step away from the previous slab's bounds (a slab moves
+// a window by 32 D, a few cells).  Each (slab, 64 tiles) result is staged as
+// [tile][FFT] and written as 64-byte runs of 8 FFTs, the layout the transform
+// reads with one 8-byte load per lane.
 // grid (ceil(n_fft / 8), n_dir), 256 threads.
 constexpr int kWinPeaks = 640;
 constexpr int kWinTiles = 64;
@@ -385,10 +386,18 @@ __device__ __forceinline__ int lower_bound_pos(const int64_t *a, int n, int64_t 
     }
     return lo;
 }
+// first index q with a[q] >= x, starting from a nearby q; unchecked: a[-1] and
+// a[n] are sentinels (smallest and largest int64)
+template <bool CHECKED>
 __device__ __forceinline__ int step_bound(const int64_t *a, int n, int q, int64_t x)
 {
-    while (q > 0 && a[q - 1] >= x) --q;
-    while (q < n && a[q] < x) ++q;
+    if (CHECKED) {
+        while (q < n && a[q] < x) ++q;
+        while (q > 0 && a[q - 1] >= x) --q;
+    } else {
+        while (a[q] < x) ++q;
+        while (a[q - 1] >= x) --q;
+    }
     return q;
 }
 
@@ -405,11 +414,14 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
     const int64_t o0 = live ? J.offsets[i] : 0;
     const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
-    const int64_t *pos = Ad + o0;
-    if (n <= kWinPeaks) {
-        for (int k = lane; k < n; k += 32) pos_s[warp][k] = pos[k];
+    const bool staged = n + 2 <= kWinPeaks;
+    if (staged) {
+        for (int k = lane; k < n; k += 32) pos_s[warp][k + 1] = Ad[o0 + k];
+        if (lane == 0) {
+            pos_s[warp][0] = LLONG_MIN;
+            pos_s[warp][n + 1] = LLONG_MAX;
+        }
         __syncwarp();
-        pos = pos_s[warp];
     }
     const int64_t dv = live ? J.D[i] : 0;
     const int64_t s0 = live ? J.S0[i] : 0;
@@ -418,35 +430,47 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     int2 *out = windows + (int64_t)d_rel * J.n_slabs * J.n_tiles * nf;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kWinTiles) {
         const int nt = min(kWinTiles, J.n_tiles - t0);
+        // per tile: c = S0 + (b0 - K + 1) 2^32 and the stripe extent E 2^32
+        int64_t c[2], ext[2];
         int qa[2] = {0, 0}, qb[2] = {0, 0};
-        for (int slab = 0; slab < J.n_slabs; ++slab) {
-            const int j0 = slab * kRows;
-            const int R = min(kRows, J.n_fdot - j0);
-            const int64_t span = (int64_t)(R - 1) * dv;
-            if (live) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int tt = lane + 32 * h;
-                    if (tt < nt) {
-                        const int b0 = (t0 + tt) * W;
-                        const int Wt = min(W, J.n_f0 - b0);
-                        const int64_t cb =
-                            s0 + (int64_t)j0 * dv + (int64_t)(b0 - K + 1) * 4294967296LL;
-                        const int64_t lo = cb + (span < 0 ? span : 0);
-                        const int64_t hi =
-                            cb + (span > 0 ? span : 0) + (int64_t)(Wt + K - 1) * 4294967296LL;
-                        if (slab == 0) {
-                            qa[h] = lower_bound_pos(pos, n, lo);
-                            qb[h] = lower_bound_pos(pos, n, hi);
-                        } else {
-                            qa[h] = step_bound(pos, n, qa[h], lo);
-                            qb[h] = step_bound(pos, n, qb[h], hi);
-                        }
-                        stage[tt][warp] =
-                            make_int2((int)(o0 + qa[h]), (int)(o0 + max(qa[h], qb[h])));
+        for (int h = 0; h < 2; ++h) {
+            const int b0 = (t0 + lane + 32 * h) * W;
+            c[h] = s0 + (int64_t)(b0 - K + 1) * 4294967296LL;
+            ext[h] = (int64_t)(min(W, J.n_f0 - b0) + K - 1) * 4294967296LL;
+        }
+        int64_t jd = 0;  // j0 D
+        auto body = [&](auto checked_tag, int slab, int64_t smin, int64_t smax) {
+            constexpr bool CHK = decltype(checked_tag)::value;
+            const int64_t *pos = CHK ? Ad + o0 : &pos_s[warp][1];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int tt = lane + 32 * h;
+                if (tt < nt) {
+                    const int64_t cb = c[h] + jd;
+                    const int64_t lo = cb + smin;
+                    const int64_t hi = cb + smax + ext[h];
+                    if (slab == 0) {
+                        qa[h] = lower_bound_pos(pos, n, lo);
+                        qb[h] = lower_bound_pos(pos, n, hi);
+                    } else {
+                        qa[h] = step_bound<CHK>(pos, n, qa[h], lo);
+                        qb[h] = step_bound<CHK>(pos, n, qb[h], hi);
                     }
+                    stage[tt][warp] = make_int2((int)(o0 + qa[h]), (int)(o0 + max(qa[h], qb[h])));
                 }
             }
+        };
+        for (int slab = 0; slab < J.n_slabs; ++slab) {
+            const int R = min(kRows, J.n_fdot - slab * kRows);
+            const int64_t span = (int64_t)(R - 1) * dv;
+            if (live) {
+                if (staged)
+                    body(std::false_type{}, slab, span < 0 ? span : 0, span > 0 ? span : 0);
+                else
+                    body(std::true_type{}, slab, span < 0 ? span : 0, span > 0 ? span : 0);
+            }
+            jd += 32 * dv;
             __syncthreads();
             for (int e = threadIdx.x; e < nt * 8; e += 256) {
                 const int tt = e >> 3, f = e & 7;
