@@ -449,27 +449,40 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     } else {
         if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
             return set_error(FH_ERR_INVALID_ARG, "null device peakmap array");
-        e = launch_sanitize_offsets(pm->offsets, n, np, p->offsets, p->err, s);
-        if (e != cudaSuccess) return cuda_error(e, "sanitize_offsets launch");
-        e = launch_validate_device_inputs(pm->t_fft, pm->freq, p->offsets, v_over_c, sky_n, n,
-                                          n_dir, p->err, s);
-        if (e != cudaSuccess) return cuda_error(e, "validate launch");
-        p->launches += 2;
         t_src = pm->t_fft;
         f_src = pm->freq;
         v_src = v_over_c;
         sky_src = sky_n;
     }
     const fh_plan_desc &d = p->d;
-    e = launch_shift_tables(t_src, n, d.t_ref, p->kt, d.fdot_min, d.fdot_step, d.n_fdot, p->S0,
-                            p->D, p->dmax, p->err, s);
-    if (e != cudaSuccess) return cuda_error(e, "shift_tables launch");
+    const bool on_device = pm->mem_kind == FH_MEM_DEVICE;
+    PrepArgs pa{};
+    pa.offsets_in = on_device ? pm->offsets : nullptr;  // host inputs were checked on the host
+    pa.offsets_out = p->offsets;
+    pa.t = t_src;
+    pa.v = v_src;
+    pa.sky = sky_src;
+    pa.n_fft = n;
+    pa.n_dir = n_dir;
+    pa.n_fdot = d.n_fdot;
+    pa.validate = on_device ? 1 : 0;
+    pa.n_peaks = np;
+    pa.t_ref = d.t_ref;
+    pa.kt = p->kt;
+    pa.fdot_min = d.fdot_min;
+    pa.fdot_step = d.fdot_step;
+    pa.S0 = p->S0;
+    pa.D = p->D;
+    pa.dmax = p->dmax;
+    pa.err = p->err;
+    e = launch_prep(pa, s);
+    if (e != cudaSuccess) return cuda_error(e, "prep launch");
     // the plan's transform reads precomputed windows, whose pre-pass searches
-    // each FFT's (L1-resident) positions directly: no bucket index needed
+    // each FFT's positions directly: no bucket index needed
     e = launch_positions(f_src, p->offsets, v_src, sky_src, n, np, n_dir, d.f0_min, p->kt,
-                         d.k_over, p->A, out_r, p->err, BucketIndex{}, s);
+                         d.k_over, p->A, out_r, p->err, BucketIndex{}, on_device, s);
     if (e != cudaSuccess) return cuda_error(e, "positions launch");
-    p->launches += (n > 0) ? 2 : 0;
+    p->launches += ((n > 0 || on_device) ? 1 : 0) + ((n > 0) ? 1 : 0);
     if (out_A && np > 0) {
         e = cudaMemcpyAsync(out_A, p->A, 8 * (size_t)np * n_dir, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(out_A)");

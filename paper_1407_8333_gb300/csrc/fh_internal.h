@@ -72,6 +72,24 @@ struct SelectArgs {
 };
 
 // ---- launchers (fh_kernels.cu); all return cudaGetLastError() ----
+// Per-call set-up in one block: (a) if offsets_in is given, the sanitised
+// CSR copy of it (clamped to [0, n_peaks], non-decreasing, first 0, last
+// n_peaks; kErrCsr if anything changed); (b) the spin-down shift tables S0, D
+// of every FFT and the largest |D| (atomicMax into *dmax, which starts at 0);
+// (c) if validate: t finite and strictly increasing, |v| < 0.1 componentwise,
+// sky components within 1.000001.
+struct PrepArgs {
+    const int64_t *offsets_in;  // device CSR to sanitise, or null (offsets_out already valid)
+    int64_t *offsets_out;
+    const double *t, *v, *sky;
+    int32_t n_fft, n_dir, n_fdot, validate;
+    int64_t n_peaks;
+    double t_ref, kt, fdot_min, fdot_step;
+    int64_t *S0, *D;
+    unsigned long long *dmax;
+    int32_t *err;
+};
+cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
 cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
                                 double fdot_min, double fdot_step, int32_t n_fdot,
                                 int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,
@@ -79,7 +97,8 @@ cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, do
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, const BucketIndex &bix, cudaStream_t s);
+                             double *out_r, int32_t *err, const BucketIndex &bix, bool validate,
+                             cudaStream_t s);
 cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
                                     int64_t *out, int32_t *err, cudaStream_t s);
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,

@@ -1,15 +1,18 @@
 // Kernels of the frequency-Hough hot path (sm_103a).
 //
+//   prep_kernel          a3       per-FFT spin-down shift (Eqs. uno, sdstep), CSR
+//                                 sanitising and per-FFT input checks
 //   positions_kernel     a1 + a2  Doppler factor and 32.32 fixed-point stripe start
 //                                 (Eq. fdopp; Sec. VI; Eq. freqres)
-//   shift_tables_kernel  a3       per-FFT spin-down shift (Eqs. uno, sdstep)
+//   shift_tables_kernel  a3       the shift tables alone (server path)
 //   transform_kernel     a4 + a5 + profile half of a6 (Eqs. due, ncount; Sec. VIII)
 //   select_kernel        a6       per-sub-band greedy picks (Sec. VIII; Eq. cr)
 //
 // Floating point: every binary64 operation is an explicit round-to-nearest
 // intrinsic (__dmul_rn, __dadd_rn, ...), so nothing is contracted into an FMA
 // and the results are the IEEE values of the operations in the stated order.
-// After the fixed-point conversion the path is integer only.
+// The final floor(x 2^32) of a peak position is taken exactly from the IEEE
+// fields of x with integer operations.  After it the path is integer only.
 #include <climits>
 #include <cstdint>
 #include <utility>
@@ -25,17 +28,43 @@ constexpr int kPosFfts = 8;
 constexpr int kPosThreads = 256;
 
 // ---------------------------------------------------------------- a1 + a2
+// floor(x 2^32) for |x| < 2^28, exactly: x = m 2^(e - 1075) with m the
+// significand (hidden bit included for normal numbers), so x 2^32 =
+// m 2^(e - 1043), a left shift by at most 7 bits, or a right shift whose
+// discarded bits round a negative value down.  Out-of-range inputs give some
+// value; the caller flags them.
+__device__ __forceinline__ int64_t floor_times_2p32(double x)
+{
+    const uint64_t bits = (uint64_t)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (ex ? (uint64_t(1) << 52) : 0);
+    const int sh = (ex ? ex : 1) - 1043;
+    uint64_t q;
+    bool frac;
+    if (sh >= 0) {
+        q = m << (sh < 10 ? sh : 10);
+        frac = false;
+    } else {
+        const int rs = -sh;
+        q = rs < 64 ? m >> rs : 0;
+        frac = rs < 64 ? (m & ((uint64_t(1) << rs) - 1)) != 0 : m != 0;
+    }
+    return (bits >> 63) ? -(int64_t)q - (frac ? 1 : 0) : (int64_t)q;
+}
+
 // grid (ceil(n_fft / 8), n_dir): the block computes r = 1 / (1 + v.n) for 8
 // FFTs of one direction, then the fixed-point position of each of their peaks
 // (a contiguous CSR range, so loads and stores are coalesced), then -- if an
 // index is wanted -- one warp per FFT builds that FFT's bucket index from the
-// positions just written (still in L1/L2).
+// positions just written (still in L1/L2).  With `validate`, the blocks of
+// direction 0 also flag frequencies that are not finite and positive
+// (kErrInvalid) or not strictly increasing within their FFT (kErrUnsorted).
 __global__ void __launch_bounds__(kPosThreads)
 positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
                  int64_t n_peaks, double f0_min, double kt, double cshift,
                  int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
-                 BucketIndex bix)
+                 BucketIndex bix, int32_t validate)
 {
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
@@ -57,25 +86,46 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
     __syncthreads();
     const int64_t p_begin = off_s[0], p_end = off_s[nf];
     int64_t *__restrict__ Ad = A + (int64_t)d * n_peaks;
+    const bool check = validate && d == 0;
+    const int lane = threadIdx.x & 31;
     bool bad = false;
-    for (int64_t p = p_begin + threadIdx.x; p < p_end; p += blockDim.x) {
+    int32_t ev = 0;
+    // whole warps step together (the shuffle below needs all lanes)
+    for (int64_t pw = p_begin + (threadIdx.x & ~31); pw < p_end; pw += blockDim.x) {
+        const int64_t p = pw + lane;
+        const bool in = p < p_end;
         int lo = 0, hi = nf;  // off_s[lo] <= p < off_s[hi]
         while (hi - lo > 1) {
             const int m = (lo + hi) >> 1;
             if (off_s[m] <= p) lo = m; else hi = m;
         }
-        const double u = __dmul_rn(freq[p], r_s[lo]);
-        const double x = __dsub_rn(u, f0_min);
-        const double y = __dmul_rn(x, kt);
-        const double a = __dadd_rn(y, cshift);
-        bad |= !(fabs(a) < (double)kFixedLimit);
-        Ad[p] = (int64_t)floor(__dmul_rn(a, kTwo32));
+        const double f = in ? freq[p] : 1.0;
+        if (check) {
+            // positive finite doubles order like their bit patterns
+            const int64_t fb = __double_as_longlong(f);
+            int64_t prev = __shfl_up_sync(kFull, fb, 1);
+            if (lane == 0 && in && p > p_begin) prev = __double_as_longlong(freq[p - 1]);
+            if (in) {
+                if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
+                if (p > off_s[lo] && !(fb > prev)) ev |= kErrUnsorted;
+            }
+        }
+        if (in) {
+            const double u = __dmul_rn(f, r_s[lo]);
+            const double x = __dsub_rn(u, f0_min);
+            const double y = __dmul_rn(x, kt);
+            const double a = __dadd_rn(y, cshift);
+            // |a| < 2^28 exactly when the biased exponent is below 1023 + 28
+            bad |= ((__double_as_longlong(a) >> 52) & 0x7FF) >= 1051;
+            Ad[p] = floor_times_2p32(a);
+        }
     }
+    if (ev) atomicOr(err, ev);
     if (bad) atomicOr(err, kErrRange);
     if (bix.idx == nullptr) return;
     __syncthreads();
     // bucket index: peak k of an FFT is the first of buckets (g_{k-1}, g_k]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = bix.nb;
     for (int f = warp; f < nf; f += nw) {
         const int64_t o0 = off_s[f];
@@ -99,6 +149,109 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
         }
         for (int g = (glast + 1 > 0 ? glast + 1 : 0) + lane; g < nb; g += 32) row[g] = n;
     }
+}
+
+// ---------------------------------------------------------------- a3 + per-call set-up
+// grid 1 + ceil(n_fft / 1024), 1024 threads (see PrepArgs).  Block 0 sanitises
+// the CSR and checks the sky directions; block b > 0 takes FFTs
+// (b - 1) * 1024 ... b * 1024 - 1.  The CSR pass takes 4 consecutive entries
+// per thread (4096 per pass): a running maximum inside the thread, a warp
+// scan and one block step carry it across the pass.
+__global__ void __launch_bounds__(1024) prep_kernel(const PrepArgs a)
+{
+    __shared__ int64_t wmax[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = a.n_fft;
+    int32_t e = 0;
+    if (blockIdx.x == 0 && a.offsets_in) {
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (int base = 0; base <= n; base += 4 * 1024) {
+            const int i0 = base + 4 * threadIdx.x;
+            int64_t x[4];
+            int64_t prev_raw = (i0 > 0 && i0 <= n) ? a.offsets_in[i0 - 1] : 0;
+            int64_t run = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = i0 + j;
+                int64_t y = 0;
+                if (i <= n) {
+                    const int64_t raw = a.offsets_in[i];
+                    if (raw < 0 || raw > a.n_peaks) e |= kErrCsr;
+                    if (i == 0 && raw != 0) e |= kErrCsr;
+                    if (i == n && raw != a.n_peaks) e |= kErrCsr;
+                    if (i > 0 && raw < prev_raw) e |= kErrCsr;
+                    prev_raw = raw;
+                    y = raw < 0 ? 0 : (raw > a.n_peaks ? a.n_peaks : raw);
+                    if (i == 0) y = 0;
+                }
+                run = y > run ? y : run;
+                x[j] = run;
+            }
+            // exclusive running maximum of the threads before this one
+            int64_t inc = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o && y > inc) inc = y;
+            }
+            int64_t exc = __shfl_up_sync(kFull, inc, 1);
+            if (lane == 0) exc = 0;
+            if (lane == 31) wmax[warp] = inc;
+            __syncthreads();
+            int64_t pre = carry;
+            for (int w = 0; w < warp; ++w) pre = wmax[w] > pre ? wmax[w] : pre;
+            pre = exc > pre ? exc : pre;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = i0 + j;
+                if (i <= n) a.offsets_out[i] = (i == n) ? a.n_peaks : (x[j] > pre ? x[j] : pre);
+            }
+            __syncthreads();
+            if (threadIdx.x == 1023) carry = inc > pre ? inc : pre;
+            __syncthreads();
+        }
+    }
+    // shift tables (and per-FFT checks)
+    const double f_last = __dadd_rn(a.fdot_min, __dmul_rn((double)(a.n_fdot - 1), a.fdot_step));
+    const double absmax = fabs(a.fdot_min) > fabs(f_last) ? fabs(a.fdot_min) : fabs(f_last);
+    unsigned long long amax = 0;
+    const int i = (int)(blockIdx.x - 1) * 1024 + (int)threadIdx.x;
+    if (blockIdx.x > 0 && i < n) {
+        const double ti = a.t[i];
+        const double dt = __dsub_rn(ti, a.t_ref);
+        const double c = __dmul_rn(dt, a.kt);
+        const double s0 = __dmul_rn(a.fdot_min, c);
+        const double dd = __dmul_rn(a.fdot_step, c);
+        if (!(fabs(c) * absmax < (double)kFixedLimit)) e |= kErrRange;
+        a.S0[i] = (int64_t)floor(__dmul_rn(s0, kTwo32));
+        const int64_t Di = (int64_t)floor(__dmul_rn(dd, kTwo32));
+        a.D[i] = Di;
+        const unsigned long long m = (unsigned long long)(Di < 0 ? -Di : Di);
+        amax = m > amax ? m : amax;
+        if (a.validate) {
+            if (!isfinite(ti) || (i > 0 && !(ti > a.t[i - 1]))) e |= kErrUnsorted;
+            for (int k = 0; k < 3; ++k)
+                if (!(fabs(a.v[3 * (int64_t)i + k]) < 0.1)) e |= kErrInvalid;
+        }
+    }
+    if (blockIdx.x == 0 && a.validate) {
+        for (int d = threadIdx.x; d < a.n_dir; d += 1024) {
+            const double x = a.sky[3 * (int64_t)d], y = a.sky[3 * (int64_t)d + 1],
+                         z = a.sky[3 * (int64_t)d + 2];
+            if (!(fabs(x) <= 1.000001 && fabs(y) <= 1.000001 && fabs(z) <= 1.000001))
+                e |= kErrInvalid;
+        }
+    }
+    // largest per-row drift, for the transform's guard cells
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(kFull, amax, o);
+        amax = y > amax ? y : amax;
+    }
+    if (lane == 0 && amax) atomicMax(a.dmax, amax);
+    e = (int32_t)__reduce_or_sync(kFull, (unsigned)e);
+    if (lane == 0 && e) atomicOr(a.err, e);
 }
 
 // ---------------------------------------------------------------- a3
@@ -364,20 +517,27 @@ __device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
     }
 }
 
-// The transform's peak window of every (direction, slab, tile, FFT).  A block
-// takes 8 FFTs of one direction, one warp per FFT; the warp copies its FFT's
-// ascending positions into shared memory once, between two sentinels (an FFT
-// with more than kWinPeaks - 2 peaks is read from global memory instead, with
+// The transform's peak window of every (direction, slab, tile, FFT), to whole
+// cells: the peaks whose cell floor(A / 2^32) lies in
+// [floor(lo / 2^32), ceil(hi / 2^32)), where [lo, hi) is the hull of the
+// positions whose stripe reaches the tile on some row of the slab.  The
+// window is a superset of the peaks that reach the tile, by less than one cell
+// on each side; those extra peaks reach only guard cells (the transform's
+// guard keeps a margin of two cells), so they change no count.
+//
+// A block takes 8 FFTs of one direction, one warp per FFT; the warp copies its
+// FFT's peak cells (ascending) into shared memory once, between two sentinels
+// (an FFT with more than kWinPeaks - 2 peaks is read from global memory, with
 // bounds checks).  Lanes take tiles, 64 at a time, and walk the slabs in
 // order: the first slab's bounds come from a binary search, each later one
-// from a short linear step away from the previous slab's bounds (a slab moves
-// a window by 32 D, a few cells).  Each (slab, 64 tiles) result is staged as
-// [tile][FFT] and written as 64-byte runs of 8 FFTs, the layout the transform
-// reads with one 8-byte load per lane.
+// from a short step in the direction of the FFT's drift D (both bounds move
+// monotonically with the slab, by 32 D).  Each (slab, 64 tiles) result is
+// staged as [tile][FFT] and written as 64-byte runs of 8 FFTs, the layout the
+// transform reads with one 8-byte load per lane.
 // grid (ceil(n_fft / 8), n_dir), 256 threads.
-constexpr int kWinPeaks = 640;
+constexpr int kWinPeaks = 1024;
 constexpr int kWinTiles = 64;
-__device__ __forceinline__ int lower_bound_pos(const int64_t *a, int n, int64_t x)
+__device__ __forceinline__ int lower_bound_cell(const int32_t *a, int n, int x)
 {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -386,25 +546,21 @@ __device__ __forceinline__ int lower_bound_pos(const int64_t *a, int n, int64_t 
     }
     return lo;
 }
-// first index q with a[q] >= x, starting from a nearby q; unchecked: a[-1] and
-// a[n] are sentinels (smallest and largest int64)
-template <bool CHECKED>
-__device__ __forceinline__ int step_bound(const int64_t *a, int n, int q, int64_t x)
+__device__ __forceinline__ int global_cell(const int64_t *A, int k) { return (int)(A[k] >> 32); }
+__device__ __forceinline__ int lower_bound_cell_g(const int64_t *A, int n, int x)
 {
-    if (CHECKED) {
-        while (q < n && a[q] < x) ++q;
-        while (q > 0 && a[q - 1] >= x) --q;
-    } else {
-        while (a[q] < x) ++q;
-        while (a[q - 1] >= x) --q;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (global_cell(A, m) < x) lo = m + 1; else hi = m;
     }
-    return q;
+    return lo;
 }
 
 __global__ void __launch_bounds__(256)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
-    __shared__ int64_t pos_s[8][kWinPeaks];
+    __shared__ int32_t cell_s[8][kWinPeaks];
     __shared__ int2 stage[kWinTiles][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * 8 + warp;
@@ -415,11 +571,13 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     const int64_t o0 = live ? J.offsets[i] : 0;
     const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
     const bool staged = n + 2 <= kWinPeaks;
+    const int64_t *Ai = Ad + o0;
+    int32_t *cs = &cell_s[warp][1];  // cs[-1], cs[n]: sentinels
     if (staged) {
-        for (int k = lane; k < n; k += 32) pos_s[warp][k + 1] = Ad[o0 + k];
+        for (int k = lane; k < n; k += 32) cs[k] = global_cell(Ai, k);
         if (lane == 0) {
-            pos_s[warp][0] = LLONG_MIN;
-            pos_s[warp][n + 1] = LLONG_MAX;
+            cs[-1] = INT_MIN;
+            cs[n] = INT_MAX;
         }
         __syncwarp();
     }
@@ -427,35 +585,53 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     const int64_t s0 = live ? J.S0[i] : 0;
     const int K = J.k_over, W = J.tile_cells;
     const int64_t nf = J.n_fft;
-    int2 *out = windows + (int64_t)d_rel * J.n_slabs * J.n_tiles * nf;
+    const int64_t slab_stride = (int64_t)J.n_tiles * nf;
+    int2 *out = windows + (int64_t)d_rel * J.n_slabs * slab_stride;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kWinTiles) {
         const int nt = min(kWinTiles, J.n_tiles - t0);
-        // per tile: c = S0 + (b0 - K + 1) 2^32 and the stripe extent E 2^32
-        int64_t c[2], ext[2];
-        int qa[2] = {0, 0}, qb[2] = {0, 0};
+        // per tile: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
+        int blo[2], bhi[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int b0 = (t0 + lane + 32 * h) * W;
-            c[h] = s0 + (int64_t)(b0 - K + 1) * 4294967296LL;
-            ext[h] = (int64_t)(min(W, J.n_f0 - b0) + K - 1) * 4294967296LL;
+            blo[h] = b0 - K + 1;
+            bhi[h] = b0 + min(W, J.n_f0 - b0);
+        }
+        int qa[2] = {0, 0}, qb[2] = {0, 0};
+        // this thread's two staged entries go to fixed (tile, FFT) places of every slab
+        int2 *dst[2];
+        bool dst_ok[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int e = threadIdx.x + 256 * r;
+            const int tt = e >> 3, fi = blockIdx.x * 8 + (e & 7);
+            dst_ok[r] = tt < nt && fi < J.n_fft;
+            dst[r] = out + (int64_t)(t0 + tt) * nf + fi;
         }
         int64_t jd = 0;  // j0 D
-        auto body = [&](auto checked_tag, int slab, int64_t smin, int64_t smax) {
-            constexpr bool CHK = decltype(checked_tag)::value;
-            const int64_t *pos = CHK ? Ad + o0 : &pos_s[warp][1];
+        // DIR = +1: bounds rise with the slab (D >= 0); -1: they fall
+        auto body = [&](auto chk_tag, auto dir_tag, int slab, int Lc, int Hc) {
+            constexpr bool CHK = decltype(chk_tag)::value;
+            constexpr int DIR = decltype(dir_tag)::value;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int tt = lane + 32 * h;
                 if (tt < nt) {
-                    const int64_t cb = c[h] + jd;
-                    const int64_t lo = cb + smin;
-                    const int64_t hi = cb + smax + ext[h];
+                    const int xl = Lc + blo[h], xh = Hc + bhi[h];
                     if (slab == 0) {
-                        qa[h] = lower_bound_pos(pos, n, lo);
-                        qb[h] = lower_bound_pos(pos, n, hi);
+                        qa[h] = CHK ? lower_bound_cell_g(Ai, n, xl) : lower_bound_cell(cs, n, xl);
+                        qb[h] = CHK ? lower_bound_cell_g(Ai, n, xh) : lower_bound_cell(cs, n, xh);
+                    } else if (CHK) {
+                        while (qa[h] < n && global_cell(Ai, qa[h]) < xl) ++qa[h];
+                        while (qa[h] > 0 && global_cell(Ai, qa[h] - 1) >= xl) --qa[h];
+                        while (qb[h] < n && global_cell(Ai, qb[h]) < xh) ++qb[h];
+                        while (qb[h] > 0 && global_cell(Ai, qb[h] - 1) >= xh) --qb[h];
+                    } else if (DIR > 0) {
+                        while (cs[qa[h]] < xl) ++qa[h];
+                        while (cs[qb[h]] < xh) ++qb[h];
                     } else {
-                        qa[h] = step_bound<CHK>(pos, n, qa[h], lo);
-                        qb[h] = step_bound<CHK>(pos, n, qb[h], hi);
+                        while (cs[qa[h] - 1] >= xl) --qa[h];
+                        while (cs[qb[h] - 1] >= xh) --qb[h];
                     }
                     stage[tt][warp] = make_int2((int)(o0 + qa[h]), (int)(o0 + max(qa[h], qb[h])));
                 }
@@ -464,19 +640,25 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
         for (int slab = 0; slab < J.n_slabs; ++slab) {
             const int R = min(kRows, J.n_fdot - slab * kRows);
             const int64_t span = (int64_t)(R - 1) * dv;
+            const int64_t u = s0 + jd + (span < 0 ? span : 0);
+            const int64_t w = s0 + jd + (span > 0 ? span : 0);
+            const int Lc = (int)(u >> 32);
+            const int Hc = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0);
             if (live) {
-                if (staged)
-                    body(std::false_type{}, slab, span < 0 ? span : 0, span > 0 ? span : 0);
+                if (!staged)
+                    body(std::true_type{}, std::integral_constant<int, 1>{}, slab, Lc, Hc);
+                else if (dv >= 0)
+                    body(std::false_type{}, std::integral_constant<int, 1>{}, slab, Lc, Hc);
                 else
-                    body(std::true_type{}, slab, span < 0 ? span : 0, span > 0 ? span : 0);
+                    body(std::false_type{}, std::integral_constant<int, -1>{}, slab, Lc, Hc);
             }
             jd += 32 * dv;
             __syncthreads();
-            for (int e = threadIdx.x; e < nt * 8; e += 256) {
-                const int tt = e >> 3, f = e & 7;
-                const int fi = blockIdx.x * 8 + f;
-                if (fi < J.n_fft)
-                    out[((int64_t)slab * J.n_tiles + t0 + tt) * nf + fi] = stage[tt][f];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = threadIdx.x + 256 * r;
+                if (dst_ok[r]) *dst[r] = stage[e >> 3][e & 7];
+                dst[r] += slab_stride;
             }
             __syncthreads();
         }
@@ -913,7 +1095,25 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
 
 // ---------------------------------------------------------------- a6
 // grid (n_sb, n_dir), 1024 threads: greedy picks of one sub-band of one direction.
+// Order of the picks: profile key descending (count, then smaller row), then
+// smaller cell.  A sub-band of up to kSelPer x 1024 cells is held in registers
+// (kSelPer cells per thread); each pick zeroes the keys within `excl` cells of
+// it, so later picks skip them.  Wider sub-bands rescan the profile per pick.
 constexpr int kSelThreads = 1024;
+constexpr int kSelPer = 8;
+
+// best (key, cell) of the warp: max key, then min cell.  Keys are nonzero
+// except for excluded / empty cells.
+__device__ __forceinline__ void warp_best(unsigned long long &k, int &c)
+{
+    const unsigned h = (unsigned)(k >> 32), l = (unsigned)k;
+    const unsigned mh = __reduce_max_sync(kFull, h);
+    const unsigned ml = __reduce_max_sync(kFull, h == mh ? l : 0u);
+    const unsigned mc = __reduce_min_sync(kFull, (h == mh && l == ml) ? (unsigned)c : 0x7FFFFFFFu);
+    k = ((unsigned long long)mh << 32) | ml;
+    c = (int)mc;
+}
+
 __global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectArgs a)
 {
     __shared__ int picks[64];
@@ -928,52 +1128,74 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectArgs a)
     const unsigned long long *prof =
         reinterpret_cast<const unsigned long long *>(a.profile) + (int64_t)d_abs * a.n_f0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool in_regs = hi - lo <= kSelPer * kSelThreads;
+    unsigned long long key[kSelPer];
+#pragma unroll
+    for (int j = 0; j < kSelPer; ++j) {
+        const int b = lo + threadIdx.x + j * kSelThreads;
+        key[j] = (in_regs && b < hi) ? prof[b] : 0ull;
+    }
     if (threadIdx.x == 0) { npick = 0; stop = 0; }
     __syncthreads();
     for (int k = 0; k < a.top_k; ++k) {
         unsigned long long bk = 0ull;
-        int bc = INT_MAX;
+        int bc = 0x7FFFFFFF;
         const int np = npick;
-        for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
-            bool ex = false;
-            for (int m = 0; m < np; ++m) {
-                const int dd = b > picks[m] ? b - picks[m] : picks[m] - b;
-                if (dd <= a.excl) ex = true;
+        if (in_regs) {
+            // a thread's cells ascend with j: a strict > keeps the smaller cell on ties
+#pragma unroll
+            for (int j = 0; j < kSelPer; ++j)
+                if (key[j] > bk) { bk = key[j]; bc = lo + threadIdx.x + j * kSelThreads; }
+        } else {
+            for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+                bool ex = false;
+                for (int m = 0; m < np; ++m) {
+                    const int dd = b > picks[m] ? b - picks[m] : picks[m] - b;
+                    if (dd <= a.excl) ex = true;
+                }
+                if (ex) continue;
+                const unsigned long long kb = prof[b];
+                if (kb > bk) { bk = kb; bc = b; }
             }
-            if (ex) continue;
-            const unsigned long long key = prof[b];
-            if (key > bk || (key == bk && b < bc)) { bk = key; bc = b; }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long k2 = __shfl_down_sync(kFull, bk, o);
-            const int c2 = __shfl_down_sync(kFull, bc, o);
-            if (k2 > bk || (k2 == bk && c2 < bc)) { bk = k2; bc = c2; }
-        }
+        warp_best(bk, bc);
         if (lane == 0) { wkey[warp] = bk; wcell[warp] = bc; }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < nw; ++w)
-                if (wkey[w] > bk || (wkey[w] == bk && wcell[w] < bc)) { bk = wkey[w]; bc = wcell[w]; }
-            if (bc == INT_MAX || bk == 0ull) {
-                stop = 1;
-            } else {
-                const int count = (int)(unsigned)(bk >> 32);
-                bool ok = count >= a.n_thr;
-                for (int m = 0; m < npick && ok; ++m) {
-                    const int dd = bc > picks[m] ? bc - picks[m] : picks[m] - bc;
-                    if (dd < a.sep) ok = false;
-                }
-                if (!ok) {
+        if (warp == 0) {
+            bk = lane < nw ? wkey[lane] : 0ull;
+            bc = lane < nw ? wcell[lane] : 0x7FFFFFFF;
+            warp_best(bk, bc);
+            if (lane == 0) {
+                if (bk == 0ull) {
                     stop = 1;
                 } else {
-                    picks[npick] = bc;
-                    pkey[npick] = bk;
-                    ++npick;
+                    const int count = (int)(unsigned)(bk >> 32);
+                    bool ok = count >= a.n_thr;
+                    for (int m = 0; m < np && ok; ++m) {
+                        const int dd = bc > picks[m] ? bc - picks[m] : picks[m] - bc;
+                        if (dd < a.sep) ok = false;
+                    }
+                    if (!ok) {
+                        stop = 1;
+                    } else {
+                        picks[np] = bc;
+                        pkey[np] = bk;
+                        npick = np + 1;
+                    }
                 }
             }
         }
         __syncthreads();
         if (stop) break;
+        if (in_regs) {
+            const int pc = picks[np];
+#pragma unroll
+            for (int j = 0; j < kSelPer; ++j) {
+                const int b = lo + threadIdx.x + j * kSelThreads;
+                const int dd = b > pc ? b - pc : pc - b;
+                if (dd <= a.excl) key[j] = 0ull;
+            }
+        }
     }
     const double np0 = __dmul_rn((double)a.n_fft, a.p0);
     const double sd = __dsqrt_rn(__dmul_rn(np0, __dsub_rn(1.0, a.p0)));
@@ -1051,16 +1273,26 @@ cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, do
     return cudaGetLastError();
 }
 
+cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s)
+{
+    if (a.n_fft <= 0 && !a.offsets_in && !(a.validate && a.n_dir > 0)) return cudaSuccess;
+    const int blocks = 1 + (a.n_fft > 0 ? (a.n_fft + 1023) / 1024 : 0);
+    prep_kernel<<<blocks, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, const BucketIndex &bix, cudaStream_t s)
+                             double *out_r, int32_t *err, const BucketIndex &bix, bool validate,
+                             cudaStream_t s)
 {
     if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
     dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
     positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
-                                                  kt, cshift, A, out_r, err, bix);
+                                                  kt, cshift, A, out_r, err, bix,
+                                                  validate ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -122,15 +122,29 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(profile, 0, sizeof(uint64_t) * (size_t)d.n_f0, s);
-    if (e == cudaSuccess) e = launch_sanitize_offsets(pm->offsets, n, np, offsets, err, s);
-    if (e == cudaSuccess)
-        e = launch_validate_device_inputs(pm->t_fft, pm->freq, offsets, v_over_c, sky_n, n, 1, err, s);
-    if (e == cudaSuccess)
-        e = launch_shift_tables(pm->t_fft, n, d.t_ref, kt, d.fdot_min, d.fdot_step, d.n_fdot, S0, D,
-                                dmax, err, s);
+    PrepArgs pa{};
+    pa.offsets_in = pm->offsets;
+    pa.offsets_out = offsets;
+    pa.t = pm->t_fft;
+    pa.v = v_over_c;
+    pa.sky = sky_n;
+    pa.n_fft = n;
+    pa.n_dir = 1;
+    pa.n_fdot = d.n_fdot;
+    pa.validate = 1;
+    pa.n_peaks = np;
+    pa.t_ref = d.t_ref;
+    pa.kt = kt;
+    pa.fdot_min = d.fdot_min;
+    pa.fdot_step = d.fdot_step;
+    pa.S0 = S0;
+    pa.D = D;
+    pa.dmax = dmax;
+    pa.err = err;
+    if (e == cudaSuccess) e = launch_prep(pa, s);
     if (e == cudaSuccess)
         e = launch_positions(pm->freq, offsets, v_over_c, sky_n, n, np, 1, d.f0_min, kt, d.k_over, A,
-                             nullptr, err, BucketIndex{}, s);
+                             nullptr, err, BucketIndex{}, true, s);
     if (e != cudaSuccess) return cuda_error(e, "fh_search_static set-up");
 
     const int32_t mode = d.mode == FH_MODE_DIFF ? FH_MODE_DIFF : FH_MODE_START;
