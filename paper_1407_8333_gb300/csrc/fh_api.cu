@@ -515,6 +515,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.profile = p->profile;
     job.bidx = nullptr;
     job.dmax = p->dmax;
+    job.err = p->err;
     job.bbase = p->bix.base;
     job.bgsh = p->bix.gsh;
     job.bnb = p->bix.nb;

@@ -46,6 +46,9 @@ struct TransformJob {
     int32_t *maps;           // nullable, [dir - dir_begin][n_fdot][n_f0]
     const int32_t *bidx;     // nullable bucket index [dir][n_fft][bnb]
     const unsigned long long *dmax;  // max_i |D_i| (32.32 cells per row), from a3
+    const int32_t *err;      // the job's device error word: the unclamped walk, which
+                             // trusts the peak windows (sorted positions), runs only
+                             // while it is 0
     const int2 *windows;     // nullable: precomputed peak windows (first, end) per
                              // [dir - dir_begin][slab][tile][fft]; else looked up
     int32_t bbase, bgsh, bnb;

@@ -525,18 +525,22 @@ __device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
 // on each side; those extra peaks reach only guard cells (the transform's
 // guard keeps a margin of two cells), so they change no count.
 //
-// A block takes 8 FFTs of one direction, one warp per FFT; the warp copies its
-// FFT's peak cells (ascending) into shared memory once, between two sentinels
-// (an FFT with more than kWinPeaks - 2 peaks is read from global memory, with
-// bounds checks).  Lanes take tiles, 64 at a time, and walk the slabs in
-// order: the first slab's bounds come from a binary search, each later one
-// from a short step in the direction of the FFT's drift D (both bounds move
-// monotonically with the slab, by 32 D).  Each (slab, 64 tiles) result is
-// staged as [tile][FFT] and written as 64-byte runs of 8 FFTs, the layout the
-// transform reads with one 8-byte load per lane.
-// grid (ceil(n_fft / 8), n_dir), 256 threads.
+// A block takes 8 FFTs of one direction, two warps per FFT; the FFT's peak
+// cells (ascending) are copied into shared memory once, between four sentinels
+// on each side (an FFT with more than kWinPeaks - 8 peaks is read from global
+// memory, with bounds checks).  Lanes take tiles, one each (64 per pass), and
+// walk the slabs in order: the first slab's bounds come from a binary search,
+// each later one from a step in the direction of the FFT's drift D (both
+// bounds move monotonically with the slab, by 32 D), two cells per look-up.
+// Each (slab, 64 tiles) result is staged as [FFT][tile] (row pitch 68 entries:
+// both the lanes' writes and the 8-FFT runs read back take the minimum of
+// shared-memory wavefronts) and written as 64-byte runs of 8 FFTs, the layout
+// the transform reads with one 8-byte load per lane.
+// grid (ceil(n_fft / 8), n_dir), 512 threads.
 constexpr int kWinPeaks = 1024;
 constexpr int kWinTiles = 64;
+constexpr int kWinPad = 2;
+constexpr int kWinPitch = 68;  // = 4 mod 16 eight-byte banks
 __device__ __forceinline__ int lower_bound_cell(const int32_t *a, int n, int x)
 {
     int lo = 0, hi = n;
@@ -556,31 +560,51 @@ __device__ __forceinline__ int lower_bound_cell_g(const int64_t *A, int n, int x
     }
     return lo;
 }
+// first index >= q whose cell is >= x (a[n], a[n + 1] are sentinels)
+__device__ __forceinline__ int step_up(const int32_t *a, int q, int x)
+{
+    for (;;) {
+        const int k = (a[q] < x) + (a[q + 1] < x);
+        q += k;
+        if (k < 2) return q;
+    }
+}
+// first index <= q whose cell is >= x, everything before it below x
+// (a[-2], a[-1] are sentinels)
+__device__ __forceinline__ int step_down(const int32_t *a, int q, int x)
+{
+    for (;;) {
+        const int k = (a[q - 1] >= x) + (a[q - 2] >= x);
+        q -= k;
+        if (k < 2) return q;
+    }
+}
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512, 2)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
     __shared__ int32_t cell_s[8][kWinPeaks];
-    __shared__ int2 stage[kWinTiles][8];
+    __shared__ int2 stage[8][kWinPitch];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * 8 + warp;
+    const int f = warp & 7, half = warp >> 3;  // FFT of the block, tile half
+    const int i = blockIdx.x * 8 + f;
     const bool live = i < J.n_fft;
     const int d_rel = blockIdx.y;
     const int d_abs = J.dir_begin + d_rel;
     const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
     const int64_t o0 = live ? J.offsets[i] : 0;
     const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
-    const bool staged = n + 2 <= kWinPeaks;
+    const bool staged = n + 2 * kWinPad <= kWinPeaks;
     const int64_t *Ai = Ad + o0;
-    int32_t *cs = &cell_s[warp][1];  // cs[-1], cs[n]: sentinels
+    int32_t *cs = &cell_s[f][kWinPad];
     if (staged) {
-        for (int k = lane; k < n; k += 32) cs[k] = global_cell(Ai, k);
-        if (lane == 0) {
-            cs[-1] = INT_MIN;
-            cs[n] = INT_MAX;
+        for (int k = half * 32 + lane; k < n; k += 64) cs[k] = global_cell(Ai, k);
+        if (half == 0 && lane < kWinPad) {
+            cs[-1 - lane] = INT_MIN;
+            cs[n + lane] = INT_MAX;
         }
-        __syncwarp();
     }
+    __syncthreads();
     const int64_t dv = live ? J.D[i] : 0;
     const int64_t s0 = live ? J.S0[i] : 0;
     const int K = J.k_over, W = J.tile_cells;
@@ -589,77 +613,52 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     int2 *out = windows + (int64_t)d_rel * J.n_slabs * slab_stride;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kWinTiles) {
         const int nt = min(kWinTiles, J.n_tiles - t0);
-        // per tile: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
-        int blo[2], bhi[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int b0 = (t0 + lane + 32 * h) * W;
-            blo[h] = b0 - K + 1;
-            bhi[h] = b0 + min(W, J.n_f0 - b0);
-        }
-        int qa[2] = {0, 0}, qb[2] = {0, 0};
-        // this thread's two staged entries go to fixed (tile, FFT) places of every slab
-        int2 *dst[2];
-        bool dst_ok[2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int e = threadIdx.x + 256 * r;
-            const int tt = e >> 3, fi = blockIdx.x * 8 + (e & 7);
-            dst_ok[r] = tt < nt && fi < J.n_fft;
-            dst[r] = out + (int64_t)(t0 + tt) * nf + fi;
-        }
+        // this lane's tile: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
+        const int tt = half * 32 + lane;
+        const bool tile_ok = live && tt < nt;
+        const int b0 = (t0 + tt) * W;
+        const int blo = b0 - K + 1;
+        const int bhi = b0 + min(W, J.n_f0 - b0);
+        int qa = 0, qb = 0;
+        // this thread's staged entry goes to a fixed (tile, FFT) place of every slab
+        const int est = threadIdx.x >> 3, efi = blockIdx.x * 8 + (threadIdx.x & 7);
+        const bool dst_ok = est < nt && efi < J.n_fft;
+        int2 *dst = out + (int64_t)(t0 + est) * nf + efi;
         int64_t jd = 0;  // j0 D
-        // DIR = +1: bounds rise with the slab (D >= 0); -1: they fall
-        auto body = [&](auto chk_tag, auto dir_tag, int slab, int Lc, int Hc) {
-            constexpr bool CHK = decltype(chk_tag)::value;
-            constexpr int DIR = decltype(dir_tag)::value;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int tt = lane + 32 * h;
-                if (tt < nt) {
-                    const int xl = Lc + blo[h], xh = Hc + bhi[h];
-                    if (slab == 0) {
-                        qa[h] = CHK ? lower_bound_cell_g(Ai, n, xl) : lower_bound_cell(cs, n, xl);
-                        qb[h] = CHK ? lower_bound_cell_g(Ai, n, xh) : lower_bound_cell(cs, n, xh);
-                    } else if (CHK) {
-                        while (qa[h] < n && global_cell(Ai, qa[h]) < xl) ++qa[h];
-                        while (qa[h] > 0 && global_cell(Ai, qa[h] - 1) >= xl) --qa[h];
-                        while (qb[h] < n && global_cell(Ai, qb[h]) < xh) ++qb[h];
-                        while (qb[h] > 0 && global_cell(Ai, qb[h] - 1) >= xh) --qb[h];
-                    } else if (DIR > 0) {
-                        while (cs[qa[h]] < xl) ++qa[h];
-                        while (cs[qb[h]] < xh) ++qb[h];
-                    } else {
-                        while (cs[qa[h] - 1] >= xl) --qa[h];
-                        while (cs[qb[h] - 1] >= xh) --qb[h];
-                    }
-                    stage[tt][warp] = make_int2((int)(o0 + qa[h]), (int)(o0 + max(qa[h], qb[h])));
-                }
-            }
-        };
         for (int slab = 0; slab < J.n_slabs; ++slab) {
             const int R = min(kRows, J.n_fdot - slab * kRows);
             const int64_t span = (int64_t)(R - 1) * dv;
             const int64_t u = s0 + jd + (span < 0 ? span : 0);
             const int64_t w = s0 + jd + (span > 0 ? span : 0);
-            const int Lc = (int)(u >> 32);
-            const int Hc = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0);
-            if (live) {
-                if (!staged)
-                    body(std::true_type{}, std::integral_constant<int, 1>{}, slab, Lc, Hc);
-                else if (dv >= 0)
-                    body(std::false_type{}, std::integral_constant<int, 1>{}, slab, Lc, Hc);
-                else
-                    body(std::false_type{}, std::integral_constant<int, -1>{}, slab, Lc, Hc);
+            const int xl = (int)(u >> 32) + blo;
+            const int xh = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0) + bhi;
+            if (tile_ok) {
+                if (!staged) {
+                    if (slab == 0) {
+                        qa = lower_bound_cell_g(Ai, n, xl);
+                        qb = lower_bound_cell_g(Ai, n, xh);
+                    } else {
+                        while (qa < n && global_cell(Ai, qa) < xl) ++qa;
+                        while (qa > 0 && global_cell(Ai, qa - 1) >= xl) --qa;
+                        while (qb < n && global_cell(Ai, qb) < xh) ++qb;
+                        while (qb > 0 && global_cell(Ai, qb - 1) >= xh) --qb;
+                    }
+                } else if (slab == 0) {
+                    qa = lower_bound_cell(cs, n, xl);
+                    qb = lower_bound_cell(cs, n, xh);
+                } else if (dv >= 0) {
+                    qa = step_up(cs, qa, xl);
+                    qb = step_up(cs, qb, xh);
+                } else {
+                    qa = step_down(cs, qa, xl);
+                    qb = step_down(cs, qb, xh);
+                }
+                stage[f][tt] = make_int2((int)(o0 + qa), (int)(o0 + max(qa, qb)));
             }
             jd += 32 * dv;
             __syncthreads();
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int e = threadIdx.x + 256 * r;
-                if (dst_ok[r]) *dst[r] = stage[e >> 3][e & 7];
-                dst[r] += slab_stride;
-            }
+            if (dst_ok) *dst = stage[threadIdx.x & 7][est];
+            dst += slab_stride;
             __syncthreads();
         }
     }
@@ -810,6 +809,19 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                                 (MODE == FH_MODE_DIFF ? nwarps * 32 : 0);
     const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
     const unsigned lanemask_lt = (1u << lane) - 1u;
+    // Per job: the unclamped walk runs when the job's largest drift over 32 rows
+    // stays inside the guards and no input check has failed.  Its windows then
+    // hold sorted positions, so every row of every windowed peak lands in the
+    // guard cells or the tile; after a failed check (unsorted or non-finite
+    // input) the windows can hold anything and the clamped walk, which keeps
+    // every update in [0, E], runs instead.
+    unsigned job_fast = 0;  // bit j: job j may take the unclamped walk
+    for (int j = 0; j < tbl.n_jobs; ++j) {
+        const TransformJob &Jt = tbl.job[j];
+        if (Jt.dmax != nullptr && Jt.err != nullptr && *Jt.err == 0 &&
+            guard_for(*Jt.dmax) <= guard)
+            job_fast |= 1u << j;
+    }
     // step table factors: e[b] = mult[b] * D, mult[b] = +-2^b, + when lane bit b is set
     int32_t mult[5];
 #pragma unroll
@@ -845,9 +857,7 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                                           n_fft
                        : nullptr;
         const bool row_ok = lane < R;
-        // fast path when the job's largest drift over 32 rows stays inside the guards
-        const bool fast = MODE == FH_MODE_START && J->dmax != nullptr &&
-                          guard_for(*J->dmax) <= guard;
+        const bool fast = MODE == FH_MODE_START && ((job_fast >> jb) & 1u);
 
         // zero the counters (with the guard cells in the fast path); reset the chunk counter
         {
@@ -1402,7 +1412,7 @@ cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t 
 {
     if (job.n_fft <= 0 || job.n_dir <= 0) return cudaSuccess;
     dim3 grid((job.n_fft + 7) / 8, job.n_dir);
-    windows_kernel<<<grid, 256, 0, s>>>(job, windows);
+    windows_kernel<<<grid, 512, 0, s>>>(job, windows);
     return cudaGetLastError();
 }
 

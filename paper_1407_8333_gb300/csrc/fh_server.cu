@@ -231,6 +231,7 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.maps = nullptr;
             t.bidx = j->bix.idx;
             t.dmax = j->d_dmax;
+            t.err = j->d_err;
             t.bbase = j->bix.base;
             t.bgsh = j->bix.gsh;
             t.bnb = j->bix.nb;

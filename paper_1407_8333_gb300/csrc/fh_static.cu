@@ -168,6 +168,7 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     job.maps = nullptr;
     job.bidx = nullptr;  // no bucket index in the fixed scratch: binary search
     job.dmax = dmax;
+    job.err = err;
     job.n_peaks = np;
     job.item_begin = 0;
     job.n_fft = n;

@@ -247,6 +247,19 @@ def test_device_input_errors_are_reported_not_faulted(fh):
         with pytest.raises(fh.FHError) as ei:
             fh.fh_sync(plan)
         assert ei.value.code == fh.FH_ERR_UNSORTED
+        # every FFT's frequencies in descending order, and a NaN: the peak
+        # windows can hold anything, so the transform must take its clamped
+        # walk (every update inside the tile's counters)
+        f = inp.freq.copy()
+        for i in range(inp.t.shape[0]):
+            a, b = int(inp.offsets[i]), int(inp.offsets[i + 1])
+            f[a:b] = f[a:b][::-1]
+        f[int(inp.offsets[2])] = np.nan
+        fh.fh_correct_doppler(plan, dev(inp.t), dev(inp.offsets), dev(f), dev(inp.v), dev(inp.sky))
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_select_candidates(plan, 0, 1)
+        assert ei.value.code in (fh.FH_ERR_UNSORTED, fh.FH_ERR_INVALID_ARG)
         # the plan stays usable after the reported error
         fh.fh_correct_doppler(plan, dev(inp.t), dev(inp.offsets), dev(inp.freq), dev(inp.v),
                               dev(inp.sky))
