@@ -531,7 +531,7 @@ __device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
 // memory, with bounds checks).  Lanes take tiles, one each (64 per pass), and
 // walk the slabs in order: the first slab's bounds come from a binary search,
 // each later one from a step in the direction of the FFT's drift D (both
-// bounds move monotonically with the slab, by 32 D), two cells per look-up.
+// bounds move monotonically with the slab, by 32 D).
 // Each (slab, 64 tiles) result is staged as [FFT][tile] (row pitch 68 entries:
 // both the lanes' writes and the 8-FFT runs read back take the minimum of
 // shared-memory wavefronts) and written as 64-byte runs of 8 FFTs, the layout
@@ -539,7 +539,7 @@ __device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
 // grid (ceil(n_fft / 8), n_dir), 512 threads.
 constexpr int kWinPeaks = 1024;
 constexpr int kWinTiles = 64;
-constexpr int kWinPad = 2;
+constexpr int kWinPad = 1;
 constexpr int kWinPitch = 68;  // = 4 mod 16 eight-byte banks
 __device__ __forceinline__ int lower_bound_cell(const int32_t *a, int n, int x)
 {
@@ -560,24 +560,21 @@ __device__ __forceinline__ int lower_bound_cell_g(const int64_t *A, int n, int x
     }
     return lo;
 }
-// first index >= q whose cell is >= x (a[n], a[n + 1] are sentinels)
+// first index >= q whose cell is >= x (a[n] is a sentinel): one predicated
+// step, then a loop for the rare longer moves
 __device__ __forceinline__ int step_up(const int32_t *a, int q, int x)
 {
-    for (;;) {
-        const int k = (a[q] < x) + (a[q + 1] < x);
-        q += k;
-        if (k < 2) return q;
-    }
+    q += a[q] < x;
+    while (a[q] < x) ++q;
+    return q;
 }
 // first index <= q whose cell is >= x, everything before it below x
-// (a[-2], a[-1] are sentinels)
+// (a[-1] is a sentinel)
 __device__ __forceinline__ int step_down(const int32_t *a, int q, int x)
 {
-    for (;;) {
-        const int k = (a[q - 1] >= x) + (a[q - 2] >= x);
-        q -= k;
-        if (k < 2) return q;
-    }
+    q -= a[q - 1] >= x;
+    while (a[q - 1] >= x) --q;
+    return q;
 }
 
 __global__ void __launch_bounds__(512, 2)
@@ -624,12 +621,21 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
         const int est = threadIdx.x >> 3, efi = blockIdx.x * 8 + (threadIdx.x & 7);
         const bool dst_ok = est < nt && efi < J.n_fft;
         int2 *dst = out + (int64_t)(t0 + est) * nf + efi;
-        int64_t jd = 0;  // j0 D
+        // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
+        // ceil((S0 + j0 D + max(0, (R-1) D)) / 2^32) (+ the tile's terms), kept
+        // as 64-bit sums that advance by 32 D per full slab
+        const int64_t span32 = 31 * dv;
+        int64_t u = s0 + (span32 < 0 ? span32 : 0);
+        int64_t w = s0 + (span32 > 0 ? span32 : 0);
         for (int slab = 0; slab < J.n_slabs; ++slab) {
-            const int R = min(kRows, J.n_fdot - slab * kRows);
-            const int64_t span = (int64_t)(R - 1) * dv;
-            const int64_t u = s0 + jd + (span < 0 ? span : 0);
-            const int64_t w = s0 + jd + (span > 0 ? span : 0);
+            if (slab == J.n_slabs - 1) {
+                // the last slab may hold fewer rows
+                const int R = J.n_fdot - slab * kRows;
+                const int64_t span = (int64_t)(R - 1) * dv;
+                const int64_t jd = (int64_t)slab * 32 * dv;
+                u = s0 + jd + (span < 0 ? span : 0);
+                w = s0 + jd + (span > 0 ? span : 0);
+            }
             const int xl = (int)(u >> 32) + blo;
             const int xh = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0) + bhi;
             if (tile_ok) {
@@ -655,7 +661,8 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
                 }
                 stage[f][tt] = make_int2((int)(o0 + qa), (int)(o0 + max(qa, qb)));
             }
-            jd += 32 * dv;
+            u += 32 * dv;
+            w += 32 * dv;
             __syncthreads();
             if (dst_ok) *dst = stage[threadIdx.x & 7][est];
             dst += slab_stride;
