@@ -733,36 +733,42 @@ __device__ __forceinline__ void start_steps(std::integer_sequence<int, Ts...>, u
     (start_step<CLAMP, Ts>(rbase, X, e, stride, E), ...);
 }
 
-// Two peaks per lane, same row walk: both share the step's row offset.
-template <int T>
-__device__ __forceinline__ void start_step2(uint32_t rbase, int64_t &X1, int64_t &X2,
-                                            const int64_t (&e1)[5], const int64_t (&e2)[5],
-                                            uint32_t stride)
+// Two peaks of one FFT per lane: they share the row walk, hence the step
+// table e and each step's row offset; CLAMP as in start_step.
+template <bool CLAMP, int T>
+__device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &X2,
+                                          const int64_t (&e)[5], uint32_t stride, uint32_t E)
 {
     constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
     const uint32_t rb = rbase ^ (gt << 2);
-    const uint32_t a1 = (uint32_t)(int32_t)(X1 >> 32) * stride + rb;
-    const uint32_t a2 = (uint32_t)(int32_t)(X2 >> 32) * stride + rb;
+    uint32_t c1 = (uint32_t)(int32_t)(X1 >> 32);
+    uint32_t c2 = (uint32_t)(int32_t)(X2 >> 32);
+    if (CLAMP) {
+        c1 = min(c1, E);
+        c2 = min(c2, E);
+    }
+    const uint32_t a1 = c1 * stride + rb;
+    const uint32_t a2 = c2 * stride + rb;
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a1) : "memory");
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a2) : "memory");
     if constexpr (T < 31) {
         constexpr int b = ctz5(T + 1);
         if constexpr ((gt >> b) & 1) {
-            X1 -= e1[b];
-            X2 -= e2[b];
+            X1 -= e[b];
+            X2 -= e[b];
         } else {
-            X1 += e1[b];
-            X2 += e2[b];
+            X1 += e[b];
+            X2 += e[b];
         }
     }
 }
 
-template <int... Ts>
-__device__ __forceinline__ void start_steps2(std::integer_sequence<int, Ts...>, uint32_t rbase,
-                                             int64_t X1, int64_t X2, const int64_t (&e1)[5],
-                                             const int64_t (&e2)[5], uint32_t stride)
+template <bool CLAMP, int... Ts>
+__device__ __forceinline__ void pair_steps(std::integer_sequence<int, Ts...>, uint32_t rbase,
+                                           int64_t X1, int64_t X2, const int64_t (&e)[5],
+                                           uint32_t stride, uint32_t E)
 {
-    (start_step2<Ts>(rbase, X1, X2, e1, e2, stride), ...);
+    (pair_step<CLAMP, Ts>(rbase, X1, X2, e, stride, E), ...);
 }
 
 template <int... Ts>
@@ -829,10 +835,6 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             guard_for(*Jt.dmax) <= guard)
             job_fast |= 1u << j;
     }
-    // step table factors: e[b] = mult[b] * D, mult[b] = +-2^b, + when lane bit b is set
-    int32_t mult[5];
-#pragma unroll
-    for (int b = 0; b < 5; ++b) mult[b] = ((lane >> b) & 1) ? (1 << b) : -(1 << b);
 
     for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
         int jb = 0;
@@ -912,95 +914,104 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 q0 = q01[0];
                 n = n1[0];
             }
-            // exclusive scan of the per-FFT counts, owner table of non-empty FFTs
-            int P = n;
+            // START mode deals the peaks out in pairs of one FFT (one slot = two
+            // consecutive peaks of the window; an odd count leaves the last slot's
+            // second peak empty), DIFF mode one peak per slot
+            constexpr bool kPairs = MODE == FH_MODE_START;
+            const int m = kPairs ? (n + 1) >> 1 : n;
+            // exclusive scan of the per-FFT slot counts, owner table of non-empty FFTs
+            int P = m;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(kFull, P, o);
                 if (lane >= o) P += y;
             }
             const int T = __shfl_sync(kFull, P, 31);
-            P -= n;
-            const bool has = n > 0;
+            P -= m;
+            const bool has = m > 0;
             const unsigned nonempty = __ballot_sync(kFull, has);
             if (has) tab[__popc(nonempty & lanemask_lt)] = lane;
-            // position index of slot g of this FFT: delta + g
-            const int64_t delta = q0 - P;
             __syncwarp();
 
-            // deal the T peaks out to the lanes: slot g = base + lane of a round
-            // belongs to the non-empty FFT whose range [P, P + n) holds it.
-            // `before` counts the non-empty FFTs starting below the base; bases
-            // are fetched in increasing order, 32 apart.
+            // Slot g = base + lane of a round belongs to the non-empty FFT whose
+            // range [P, P + m) holds it.  `before` counts the non-empty FFTs
+            // starting below the base; bases are fetched in increasing order, 32
+            // apart.  The slot's peaks are positions q0 + k, k = (pairs) 2 (g - P)
+            // and 2 (g - P) + 1 (if below n), or (singles) g - P.
             int before = 0;
-            auto fetch = [&](int base, int64_t &a, int &owner) {
+            auto fetch = [&](int base, int64_t &a1, int64_t &a2, bool &two, int &owner) {
                 const unsigned rel = (unsigned)(P - base);
                 const unsigned bits = __reduce_or_sync(kFull, (has && rel < 32u) ? (1u << rel) : 0u);
                 const int oc = before + __popc(bits & lanemask_le) - 1;
                 before += __popc(bits);
                 owner = tab[oc < 0 ? 0 : oc];
-                const int64_t od = __shfl_sync(kFull, delta, owner);
+                const int64_t oq0 = __shfl_sync(kFull, q0, owner);
+                const int oP = __shfl_sync(kFull, P, owner);
                 const int g = base + lane;
-                a = g < T ? __ldg(Ad + od + g) : 0;
+                const bool live = g < T;
+                if (kPairs) {
+                    const int on = __shfl_sync(kFull, n, owner);
+                    const int k = 2 * (g - oP);
+                    two = live && k + 1 < on;
+                    a1 = live ? __ldg(Ad + oq0 + k) : 0;
+                    a2 = two ? __ldg(Ad + oq0 + k + 1) : 0;
+                } else {
+                    two = false;
+                    a1 = live ? __ldg(Ad + oq0 + (g - oP)) : 0;
+                    a2 = 0;
+                }
             };
-            // X of the lane's row and its step table for the peak in slot g.  Slots
-            // beyond T are parked in guard cell -1 with zero steps (never read; the
-            // clamped walk sends them to the dump cell).  On the unclamped walk
-            // every windowed peak's 32 rows stay inside the guard cells: the
-            // window holds the peaks with A - cb in [min(0, (R-1) D), max(0,
-            // (R-1) D) + E 2^32), and |31 D| stays below guard - 1 cells.
-            auto setup = [&](int g, int64_t a, int owner, int64_t &X, int64_t (&e)[5]) {
+            // X of the lane's row for the slot's peaks and their step table.  An
+            // empty slot (g >= T) is parked in guard cell -1 with zero steps.  An
+            // empty second peak walks with the first one's steps from a start
+            // that keeps all 32 rows in guard cells -guard .. -1 on the unclamped
+            // walk (|31 D| is below guard - 1 cells there), and far below cell 0
+            // on the clamped walk (which sends it to the dump cell).  Never read.
+            // On the unclamped walk every windowed peak's 32 rows stay inside the
+            // guard cells: the window holds the peaks with A - cb in
+            // [min(0, (R-1) D), max(0, (R-1) D) + E 2^32) (to one cell), and
+            // |31 D| stays below guard - 2 cells.
+            auto setup = [&](int g, int64_t a1, int64_t a2, bool two, int owner, int64_t &X1,
+                             int64_t &X2, int64_t (&e)[5]) {
                 const int64_t ocb = __shfl_sync(kFull, cb, owner);
                 const int64_t odv0 = __shfl_sync(kFull, dv, owner);
                 const bool live = g < T;
                 const int64_t odv = live ? odv0 : 0;
+                // e[b] = +-(D << b), + when bit b of the lane is set
 #pragma unroll
-                for (int b = 0; b < 5; ++b) e[b] = (int64_t)mult[b] * odv;
-                X = live ? a - ocb - (int64_t)lane * odv : -(int64_t(1) << 32);
-            };
-            constexpr bool kTwoPeaks = MODE == FH_MODE_START && MAXT <= 512;
-            int64_t a_nx = 0, a2_nx = 0;
-            int own_nx = 0, own2_nx = 0;
-            if (T > 0) fetch(0, a_nx, own_nx);
-            if (kTwoPeaks && T > 32) fetch(32, a2_nx, own2_nx);
-            int base = 0;
-            if (kTwoPeaks) {
-                // rounds of 64 positions (two peaks per lane) while more than 32 remain
-                for (; T - base > 32; base += 64) {
-                    const int64_t a1 = a_nx, a2 = a2_nx;
-                    const int o1 = own_nx, o2 = own2_nx;
-                    if (base + 64 < T) fetch(base + 64, a_nx, own_nx);
-                    if (base + 96 < T) fetch(base + 96, a2_nx, own2_nx);
-                    int64_t X1, X2, e1[5], e2[5];
-                    setup(base + lane, a1, o1, X1, e1);
-                    setup(base + 32 + lane, a2, o2, X2, e2);
-                    if (fast) {
-                        start_steps2(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e1, e2,
-                                     cell_stride);
-                    } else {
-                        start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X1, e1,
-                                          cell_stride, (uint32_t)E);
-                        start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X2, e2,
-                                          cell_stride, (uint32_t)E);
-                    }
+                for (int b = 0; b < 5; ++b) {
+                    const int64_t sh = odv * (int64_t)(1 << b);
+                    e[b] = ((lane >> b) & 1) ? sh : -sh;
                 }
-            }
-            // rounds of 32 positions
-            for (; base < T; base += 32) {
-                const int64_t a = a_nx;
+                const int64_t lane_dv = (int64_t)lane * odv;
+                X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
+                if (kPairs) {
+                    const int64_t park =
+                        fast ? (odv > 0 ? -(int64_t(1) << 32) : -((int64_t)guard << 32)) - lane_dv
+                             : -(int64_t(1) << 62);
+                    X2 = two ? a2 - ocb - lane_dv : park;
+                }
+            };
+            int64_t a1_nx = 0, a2_nx = 0;
+            bool two_nx = false;
+            int own_nx = 0;
+            if (T > 0) fetch(0, a1_nx, a2_nx, two_nx, own_nx);
+            for (int base = 0; base < T; base += 32) {
+                const int64_t a1 = a1_nx, a2 = a2_nx;
+                const bool two = two_nx;
                 const int owner = own_nx;
-                if (!kTwoPeaks && base + 32 < T) fetch(base + 32, a_nx, own_nx);
-                int64_t X, e[5];
-                setup(base + lane, a, owner, X, e);
+                if (base + 32 < T) fetch(base + 32, a1_nx, a2_nx, two_nx, own_nx);
+                int64_t X1, X2 = 0, e[5];
+                setup(base + lane, a1, a2, two, owner, X1, X2, e);
                 if (MODE == FH_MODE_START) {
                     if (fast)
-                        start_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
-                                           cell_stride, (uint32_t)E);
-                    else
-                        start_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X, e,
+                        pair_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e,
                                           cell_stride, (uint32_t)E);
+                    else
+                        pair_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e,
+                                         cell_stride, (uint32_t)E);
                 } else if (base + lane < T) {
-                    diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X, e, E, Wt, K);
+                    diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X1, e, E, Wt, K);
                 }
             }
             __syncwarp();
