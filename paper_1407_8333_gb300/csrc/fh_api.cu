@@ -683,7 +683,8 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     }
     const int lim = max_optin_smem(p->device);
     std::vector<std::pair<int, int>> cands;
-    for (int nw : {32, 16}) {
+    for (int nw : {32, 24, 16}) {
+        if (nw == 24 && p->mode == FH_MODE_DIFF) continue;  // DIFF kernels: 512 / 1024 threads
         const int32_t wmax = default_tile(d, p->device, p->mode, nw, p->guard);
         for (int32_t w : {wmax, 1536, 1280, 1024, 768, 512}) {
             if (w > wmax || w > d.n_f0) continue;

@@ -1376,21 +1376,23 @@ BucketIndex bucket_geometry(int32_t n_f0, int32_t k_over, double cells_per_peak)
 }
 
 // Kernel instantiation for a counting mode and block size: blocks of up to 512
-// threads get up to 128 registers per thread, blocks of 1024 threads 64.
+// threads get up to 128 registers per thread, of up to 768 threads (START
+// mode) 80, of 1024 threads 64.
 template <typename F>
 static auto with_transform_kernel(int32_t mode, int32_t nwarps, F &&f)
 {
     if (mode == FH_MODE_DIFF)
         return nwarps > 16 ? f(transform_kernel<FH_MODE_DIFF, 1024>)
                            : f(transform_kernel<FH_MODE_DIFF, 512>);
-    return nwarps > 16 ? f(transform_kernel<FH_MODE_START, 1024>)
-                       : f(transform_kernel<FH_MODE_START, 512>);
+    return nwarps > 24   ? f(transform_kernel<FH_MODE_START, 1024>)
+           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 768>)
+                         : f(transform_kernel<FH_MODE_START, 512>);
 }
 
 cudaError_t transform_prepare(int32_t mode, size_t smem)
 {
     cudaError_t e = cudaSuccess;
-    for (int nw : {16, 32}) {
+    for (int nw : {16, 24, 32}) {
         const cudaError_t r = with_transform_kernel(mode, nw, [&](auto k) {
             return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         });
