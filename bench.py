@@ -320,7 +320,8 @@ def run_ours(args):
 
 def batched_vs_plain(fh, synth, torch):
     """256-direction sky patch (T_FFT 1024 s, 200 FFTs, 100-101 Hz): one launch
-    per direction vs one persistent launch over all directions."""
+    per direction vs one persistent launch over all directions, each issued
+    eagerly and replayed from a CUDA graph."""
     import numpy as np
     w = synth.WORKLOADS["sky_patch256_T1024_N200_100Hz"]
     inp = synth.make_inputs(w)
@@ -350,8 +351,35 @@ def batched_vs_plain(fh, synth, torch):
                 ts.append(e0.elapsed_time(e1))
         ms = statistics.median(ts)
         res[name] = {"ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3)}
+        # the same step captured once into a CUDA graph and replayed
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            fh.fh_correct_doppler(plan, *dev, stream=s)
+            fh.fh_transform(plan, 0, n_dir, None, stream=s)
+            fh.fh_select_candidates(plan, 0, n_dir, cand, stream=s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fh.fh_correct_doppler(plan, *dev, stream=s)
+            fh.fh_transform(plan, 0, n_dir, None, stream=s)
+            fh.fh_select_candidates(plan, 0, n_dir, cand, stream=s)
+        ts = []
+        for k in range(13):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(e0.elapsed_time(e1))
+        fh.fh_sync(plan)
+        ms = statistics.median(ts)
+        res[name + "_graph"] = {"ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3)}
+        del g
         fh.fh_destroy_plan(plan)
     res["speedup"] = res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"]
+    res["speedup_graph"] = res["plain_graph"]["ms_per_step"] / res["batched_graph"]["ms_per_step"]
     return res
 
 

@@ -198,6 +198,17 @@ int fh_select_candidates(fh_plan plan, int32_t dir_begin, int32_t n_dir, fh_cand
                          int64_t capacity, int64_t *n_out, int32_t out_mem_kind,
                          void *stream);
 
+/* CUDA graphs.  Once a plan has run a step of a given shape (directions,
+ * tile, schedule) -- which sizes its window table and sets its kernels'
+ * shared-memory limits -- fh_correct_doppler on DEVICE inputs, fh_transform and
+ * fh_select_candidates into DEVICE memory enqueue only kernels, memsets and
+ * device-to-device copies on the given stream, and none of them synchronises.
+ * Such a step can be captured into a CUDA graph and replayed; a replay reads
+ * the device inputs at the addresses given at capture time (update their
+ * contents in place), and fh_sync after it reports the device-side input
+ * checks as usual.  (Host inputs and host candidate output synchronise and
+ * cannot be captured.) */
+
 /* Synchronise the stream and report device-side input validation (FH_OK,
  * FH_ERR_UNSORTED, FH_ERR_INVALID_ARG) since the last fh_correct_doppler. */
 int fh_sync(fh_plan plan, void *stream);

@@ -38,6 +38,8 @@ using Clock = std::chrono::steady_clock;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr int32_t kServeWarps = 24;  // transform block size of served batches
+
 struct Job {
     fh_job_id id = 0;
     fh_plan_desc d{};
@@ -63,11 +65,13 @@ struct Job {
     int32_t *d_err = nullptr;
     unsigned long long *d_dmax = nullptr;
     int32_t guard = 0;
-    BucketIndex bix;
+    int2 *d_win = nullptr;  // peak windows [dir][slab][tile][fft] at the job's tile
     size_t pin_off = 0;  // offset of its candidates in the batch's pinned buffer
     size_t err_off = 0;
 
     int64_t cand_count() const { return (int64_t)n_dir * n_sb * d.top_k; }
+    int32_t n_slabs() const { return (d.n_fdot + kRows - 1) / kRows; }
+    int32_t n_tiles() const { return tile > 0 ? (d.n_f0 + tile - 1) / tile : 0; }
 
     // layout of the job's single device allocation
     int64_t layout(bool carve)
@@ -89,11 +93,12 @@ struct Job {
         const size_t a_prof = take(8 * (size_t)n_dir * (size_t)d.n_f0);
         const size_t a_cand = take(sizeof(fh_candidate) * (size_t)cand_count());
         const size_t a_err = take(16);
-        const size_t a_bidx = take(4 * (size_t)n_dir * (size_t)n_fft * (size_t)bix.nb);
+        const size_t a_win = take(sizeof(int2) * (size_t)n_dir * (size_t)n_slabs() *
+                                  (size_t)n_tiles() * (size_t)std::max(1, n_fft));
         const size_t a_dmax = take(16);
         if (carve) {
             d_dmax = (unsigned long long *)(dbuf + a_dmax);
-            bix.idx = (int32_t *)(dbuf + a_bidx);
+            d_win = (int2 *)(dbuf + a_win);
             d_off = (int64_t *)(dbuf + a_off);
             d_t = (double *)(dbuf + a_t);
             d_freq = (double *)(dbuf + a_freq);
@@ -202,26 +207,40 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
         if (e == cudaSuccess)
             e = launch_positions(j->d_freq, j->d_off, j->d_v, j->d_sky, j->n_fft, j->n_peaks,
                                  j->n_dir, d.f0_min, j->kt, d.k_over, j->d_A, nullptr, j->d_err,
-                                 j->bix, false, s);
+                                 BucketIndex{}, false, s);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(j->d_prof, 0, 8 * (size_t)j->n_dir * d.n_f0, s);
         if (e != cudaSuccess) return cuda_error(e, "job set-up");
     }
-    // one persistent transform launch per group of kMaxBatchJobs jobs; the group
-    // shares the largest guard its jobs need, and each job's tile is kept
-    // within shared memory with that guard
-    const int nwarps = 32;
-    for (size_t g = 0; g < batch.size(); g += kMaxBatchJobs) {
-        const size_t g_end = std::min(batch.size(), g + (size_t)kMaxBatchJobs);
-        int32_t guard = 2;
-        for (size_t k = g; k < g_end; ++k) guard = std::max(guard, batch[k]->guard);
+    // One persistent transform launch per group of up to kMaxBatchJobs jobs.
+    // A launch has one guard width (the largest its jobs need) and each job
+    // keeps the tile its window table was sized for, so jobs (in order of
+    // guard) join a group only while every member's tile still fits in shared
+    // memory with the group's guard.
+    const int nwarps = kServeWarps;
+    const size_t lim = (size_t)max_optin_smem(device);
+    std::vector<Job *> order(batch.begin(), batch.end());
+    std::stable_sort(order.begin(), order.end(),
+                     [](const Job *x, const Job *y) { return x->guard < y->guard; });
+    auto fits = [&](const Job *j, int32_t guard) {
+        return transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps, guard) <= lim;
+    };
+    for (size_t g = 0; g < order.size();) {
+        size_t g_end = g + 1;
+        int32_t guard = std::max<int32_t>(2, order[g]->guard);
+        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs) {
+            const int32_t gn = std::max(guard, order[g_end]->guard);
+            bool ok = true;
+            for (size_t k = g; k <= g_end && ok; ++k) ok = fits(order[k], gn);
+            if (!ok) break;
+            guard = gn;
+            ++g_end;
+        }
         JobTable tbl{};
         int64_t items = 0;
         size_t smem = 0;
         for (size_t k = g; k < g_end; ++k) {
-            Job *j = batch[k];
-            const int32_t tile =
-                std::min(j->tile, default_tile(j->d, device, FH_MODE_START, nwarps, guard));
+            Job *j = order[k];
             TransformJob &t = tbl.job[tbl.n_jobs++];
             t.A = j->d_A;
             t.offsets = j->d_off;
@@ -229,27 +248,27 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.D = j->d_D;
             t.profile = j->d_prof;
             t.maps = nullptr;
-            t.bidx = j->bix.idx;
+            t.bidx = nullptr;
             t.dmax = j->d_dmax;
             t.err = j->d_err;
-            t.bbase = j->bix.base;
-            t.bgsh = j->bix.gsh;
-            t.bnb = j->bix.nb;
             t.n_peaks = j->n_peaks;
             t.n_fft = j->n_fft;
             t.n_f0 = j->d.n_f0;
             t.n_fdot = j->d.n_fdot;
             t.k_over = j->d.k_over;
-            t.tile_cells = tile;
-            t.n_slabs = (j->d.n_fdot + kRows - 1) / kRows;
-            t.n_tiles = (j->d.n_f0 + tile - 1) / tile;
+            t.tile_cells = j->tile;
+            t.n_slabs = j->n_slabs();
+            t.n_tiles = j->n_tiles();
             t.dir_begin = 0;
             t.n_dir = j->n_dir;
+            t.windows = j->d_win;
             t.item_begin = items;
             t.n_items = (int64_t)t.n_slabs * t.n_tiles * j->n_dir;
             items += t.n_items;
-            smem = std::max(smem, transform_smem_bytes(tile, j->d.k_over, FH_MODE_START, nwarps,
+            smem = std::max(smem, transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps,
                                                        guard));
+            e = launch_windows(t, j->d_win, s);
+            if (e != cudaSuccess) return cuda_error(e, "windows launch");
         }
         if (smem > prepared_smem) {
             e = transform_prepare(FH_MODE_START, smem);
@@ -260,6 +279,7 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
         const int32_t grid = (int32_t)std::min<int64_t>(items, (int64_t)n_sm * bps);
         e = launch_transform(FH_MODE_START, tbl, items, grid, nwarps, smem, guard, s);
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
+        g = g_end;
     }
     for (Job *j : batch) {
         const fh_plan_desc &d = j->d;
@@ -422,7 +442,7 @@ void fh_server_s::run()
 
 namespace {
 
-int copy_job(const fh_job_desc *jd, Job &j)
+int copy_job(const fh_job_desc *jd, Job &j, int device)
 {
     const fh_peakmap &pm = jd->peaks;
     if (pm.mem_kind != FH_MEM_HOST)
@@ -451,14 +471,9 @@ int copy_job(const fh_job_desc *jd, Job &j)
     j.freq.assign(pm.freq, pm.freq + pm.n_peaks);
     j.v.assign(jd->v_over_c, jd->v_over_c + 3 * (size_t)pm.n_fft);
     j.sky.assign(jd->sky_n, jd->sky_n + 3 * (size_t)jd->n_dir);
-    {
-        const double cpp = ((double)j.d.n_f0 + 2.0 * j.d.k_over) * (double)std::max(1, j.n_fft) /
-                           (double)std::max<int64_t>(1, j.n_peaks);
-        const BucketIndex g = bucket_geometry(j.d.n_f0, j.d.k_over, cpp);
-        j.bix.base = g.base;
-        j.bix.gsh = g.gsh;
-        j.bix.nb = g.nb;
-    }
+    // the job runs with the library's default tile for its own guard cells
+    j.guard = std::max(default_guard(j.d), host_guard(j.d, j.kt, j.t.data(), j.n_fft));
+    j.tile = default_tile(j.d, device, FH_MODE_START, kServeWarps, j.guard);
     j.bytes = j.layout(false);
     return FH_OK;
 }
@@ -559,16 +574,13 @@ int fh_submit(fh_server sv, const fh_job_desc *jd, fh_job_id *out)
 {
     if (!sv || !jd || !out) return set_error(FH_ERR_INVALID_ARG, "null server, job or out");
     auto job = std::make_unique<Job>();
-    int rc = copy_job(jd, *job);
+    int rc = copy_job(jd, *job, sv->device);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return set_error(FH_ERR_BAD_HANDLE, "server is shutting down");
     if (job->bytes > sv->budget)
         return set_error(FH_ERR_TOO_LARGE, "job needs %lld device bytes, budget is %lld",
                          (long long)job->bytes, (long long)sv->budget);
-    // a job of this shape runs with the library's default tile for its guard
-    job->guard = std::max(default_guard(job->d), host_guard(job->d, job->kt, job->t.data(), job->n_fft));
-    job->tile = default_tile(job->d, sv->device, FH_MODE_START, 32, job->guard);
     job->id = sv->next_id++;
     job->submit_s = sv->now();
     *out = job->id;
