@@ -141,18 +141,12 @@ int validate_desc(const fh_plan_desc &d)
 namespace {
 
 struct Sizes {
-    int64_t t, offsets, tables, freq, v, sky, A, profile, cand, bidx;
+    int64_t t, offsets, tables, freq, v, sky, A, profile, cand;
     int64_t total() const
     {
-        return t + offsets + 2 * tables + freq + v + sky + A + profile + cand + bidx + 256;
+        return t + offsets + 2 * tables + freq + v + sky + A + profile + cand + 256;
     }
 };
-
-BucketIndex plan_buckets(const fh_plan_desc &d)
-{
-    const double cpp = ((double)d.n_f0 + 2.0 * d.k_over) * (double)d.max_fft / (double)d.max_peaks;
-    return bucket_geometry(d.n_f0, d.k_over, cpp);
-}
 
 Sizes plan_sizes(const fh_plan_desc &d)
 {
@@ -167,7 +161,6 @@ Sizes plan_sizes(const fh_plan_desc &d)
     s.A = 8 * (int64_t)d.max_dir * d.max_peaks;
     s.profile = 8 * (int64_t)d.max_dir * d.n_f0;
     s.cand = (int64_t)sizeof(fh_candidate) * d.max_dir * n_sb * d.top_k;
-    s.bidx = 0;  // plans search positions directly (see fh_correct_doppler)
     return s;
 }
 
@@ -192,7 +185,6 @@ struct fh_plan_s {
     int2 *win = nullptr;                 // peak windows of the directions being transformed
     size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path
-    BucketIndex bix;                     // bix.idx: [max_dir][max_fft][nb]
     int32_t n_fft = -1;
     int64_t n_peaks = 0;
     int32_t n_dir = 0;
@@ -201,7 +193,7 @@ struct fh_plan_s {
 
     void release()
     {
-        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, bix.idx, dmax, win};
+        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, dmax, win};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -210,7 +202,6 @@ struct fh_plan_s {
         profile = nullptr;
         cand = nullptr;
         err = h_err = nullptr;
-        bix.idx = nullptr;
         dmax = nullptr;
         win = nullptr;
         win_bytes = 0;
@@ -349,12 +340,6 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
         return set_error(FH_ERR_INVALID_ARG, "tile_cells too wide for shared memory");
     }
     const Sizes s = plan_sizes(*desc);
-    {
-        const BucketIndex g = plan_buckets(*desc);
-        p->bix.base = g.base;
-        p->bix.gsh = g.gsh;
-        p->bix.nb = g.nb;
-    }
     struct {
         void **ptr;
         int64_t bytes;
@@ -477,10 +462,8 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     pa.err = p->err;
     e = launch_prep(pa, s);
     if (e != cudaSuccess) return cuda_error(e, "prep launch");
-    // the plan's transform reads precomputed windows, whose pre-pass searches
-    // each FFT's positions directly: no bucket index needed
     e = launch_positions(f_src, p->offsets, v_src, sky_src, n, np, n_dir, d.f0_min, p->kt,
-                         d.k_over, p->A, out_r, p->err, BucketIndex{}, on_device, s);
+                         d.k_over, p->A, out_r, p->err, on_device, s);
     if (e != cudaSuccess) return cuda_error(e, "positions launch");
     p->launches += ((n > 0 || on_device) ? 1 : 0) + ((n > 0) ? 1 : 0);
     if (out_A && np > 0) {
@@ -513,12 +496,8 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.S0 = p->S0;
     job.D = p->D;
     job.profile = p->profile;
-    job.bidx = nullptr;
     job.dmax = p->dmax;
     job.err = p->err;
-    job.bbase = p->bix.base;
-    job.bgsh = p->bix.gsh;
-    job.bnb = p->bix.nb;
     job.n_peaks = p->n_peaks;
     job.n_fft = p->n_fft;
     job.n_f0 = d.n_f0;

@@ -21,21 +21,6 @@ constexpr int64_t kFixedLimit = int64_t(1) << 28;  // |cells| bound for 32.32 fi
 // error bits written by the device-side input checks
 enum : int32_t { kErrUnsorted = 1, kErrRange = 2, kErrInvalid = 4, kErrCsr = 8 };
 
-// Per-direction coarse index of each FFT's (ascending) positions: for bucket
-// g, the first peak of the FFT (counted from the FFT's first peak) whose cell
-// floor(A / 2^32) is >= base + g * 2^gsh.  It turns the transform's search
-// for the first relevant peak of an FFT into one load and a short scan.
-struct BucketIndex {
-    int32_t *idx = nullptr;  // [dir][n_fft][nb]; nullptr = no index (binary search)
-    int32_t base = 0;        // cell of bucket 0's lower edge
-    int32_t gsh = 8;         // log2 of the bucket width in cells
-    int32_t nb = 0;          // buckets per FFT
-};
-
-// bucket geometry for a map of n_f0 cells, K, and about cells_per_peak cells
-// between consecutive peaks of one FFT
-BucketIndex bucket_geometry(int32_t n_f0, int32_t k_over, double cells_per_peak);
-
 // One direction set of one plan, as the transform kernel sees it.
 struct TransformJob {
     const int64_t *A;        // positions, [dir][n_peaks] (absolute directions)
@@ -44,14 +29,12 @@ struct TransformJob {
     const int64_t *D;        // n_fft
     uint64_t *profile;       // [dir][n_f0] (absolute directions)
     int32_t *maps;           // nullable, [dir - dir_begin][n_fdot][n_f0]
-    const int32_t *bidx;     // nullable bucket index [dir][n_fft][bnb]
     const unsigned long long *dmax;  // max_i |D_i| (32.32 cells per row), from a3
     const int32_t *err;      // the job's device error word: the unclamped walk, which
                              // trusts the peak windows (sorted positions), runs only
                              // while it is 0
     const int2 *windows;     // nullable: precomputed peak windows (first, end) per
                              // [dir - dir_begin][slab][tile][fft]; else looked up
-    int32_t bbase, bgsh, bnb;
     int64_t n_peaks;
     int64_t item_begin;      // first work item of this job in the launch
     int64_t n_items;         // n_dir * n_slabs * n_tiles
@@ -100,8 +83,7 @@ cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, do
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, const BucketIndex &bix, bool validate,
-                             cudaStream_t s);
+                             double *out_r, int32_t *err, bool validate, cudaStream_t s);
 cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
                                     int64_t *out, int32_t *err, cudaStream_t s);
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,

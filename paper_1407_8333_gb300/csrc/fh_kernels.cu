@@ -54,9 +54,8 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
 
 // grid (ceil(n_fft / 8), n_dir): the block computes r = 1 / (1 + v.n) for 8
 // FFTs of one direction, then the fixed-point position of each of their peaks
-// (a contiguous CSR range, so loads and stores are coalesced), then -- if an
-// index is wanted -- one warp per FFT builds that FFT's bucket index from the
-// positions just written (still in L1/L2).  With `validate`, the blocks of
+// (a contiguous CSR range, so loads and stores are coalesced).  With
+// `validate`, the blocks of
 // direction 0 also flag frequencies that are not finite and positive
 // (kErrInvalid) or not strictly increasing within their FFT (kErrUnsorted).
 __global__ void __launch_bounds__(kPosThreads)
@@ -64,7 +63,7 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
                  int64_t n_peaks, double f0_min, double kt, double cshift,
                  int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
-                 BucketIndex bix, int32_t validate)
+                 int32_t validate)
 {
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
@@ -122,33 +121,6 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
     }
     if (ev) atomicOr(err, ev);
     if (bad) atomicOr(err, kErrRange);
-    if (bix.idx == nullptr) return;
-    __syncthreads();
-    // bucket index: peak k of an FFT is the first of buckets (g_{k-1}, g_k]
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nb = bix.nb;
-    for (int f = warp; f < nf; f += nw) {
-        const int64_t o0 = off_s[f];
-        const int n = (int)(off_s[f + 1] - o0);
-        int32_t *row = bix.idx + ((int64_t)d * n_fft + (i0 + f)) * nb;
-        int glast = -1;  // bucket of the last peak seen so far (warp-uniform)
-        for (int k0 = 0; k0 < n; k0 += 32) {
-            const int k = k0 + lane;
-            int gk = -1;
-            if (k < n) {
-                const int c = (int)(Ad[o0 + k] >> 32);
-                gk = (c - bix.base) >> bix.gsh;
-                gk = gk < -1 ? -1 : (gk > nb - 1 ? nb - 1 : gk);
-            }
-            int gp = __shfl_up_sync(kFull, gk, 1);
-            if (lane == 0) gp = glast;
-            if (k < n)
-                for (int g = (gp + 1 > 0 ? gp + 1 : 0); g <= gk; ++g) row[g] = k;
-            const int last = min(31, n - 1 - k0);
-            glast = __shfl_sync(kFull, gk, last);
-        }
-        for (int g = (glast + 1 > 0 ? glast + 1 : 0) + lane; g < nb; g += 32) row[g] = n;
-    }
 }
 
 // ---------------------------------------------------------------- a3 + per-call set-up
@@ -364,157 +336,41 @@ __global__ void validate_device_inputs_kernel(const double *__restrict__ t,
 }
 
 // ---------------------------------------------------------------- a4 + a5 + profile
-// First position >= X among the peaks [q_from, o1) of an FFT whose peaks are
-// [o0, o1) (ascending): one bucket-index load (entries count from o0) and a
-// forward scan four positions at a time, or a binary search when the plan keeps
-// no index.  For any input the result stays inside [q_from, o1].
-__device__ __forceinline__ int64_t first_at_least(const int64_t *__restrict__ Ad,
-                                                  const int32_t *__restrict__ brow, int32_t bbase,
-                                                  int32_t bgsh, int32_t bnb, int64_t o0,
-                                                  int64_t q_from, int64_t o1, int64_t X)
+// Peak window of FFT i on rows j0 .. j0 + R - 1 of a tile whose stripe starts
+// L lie in [0, E), found by binary search over the FFT's ascending positions:
+// the peaks with lo <= A < hi, lo = cb + min(0, (R-1) D), hi = cb + max(0,
+// (R-1) D) + E 2^32, cb = S0 + j0 D + tile origin.  Outputs cb, D, the first
+// peak q0 and the count n (0 for i >= n_fft).  Every index stays inside the
+// FFT's CSR range for any input.  (Used where no window table was built.)
+__device__ __forceinline__ void lookup_window(const int64_t *__restrict__ Ad,
+                                              const int64_t *__restrict__ offs,
+                                              const int64_t *__restrict__ S0,
+                                              const int64_t *__restrict__ Dt, int n_fft, int i,
+                                              int j0, int R, int64_t base_shift, int64_t e_fixed,
+                                              int64_t &cb, int64_t &dv, int64_t &q0, int &n)
 {
-    int64_t q = q_from;
-    if (brow != nullptr) {
-        const int c = (int)(X >> 32);
-        int g = (c - bbase) >> bgsh;
-        if (g >= 0) {
-            if (g > bnb - 1) g = bnb - 1;
-            int32_t r = brow[g];
-            const int32_t n = (int32_t)(o1 - o0);
-            r = r < 0 ? 0 : (r > n ? n : r);
-            if (o0 + r > q) q = o0 + r;
-        }
-        for (;;) {
-            const int64_t a0 = q < o1 ? __ldg(Ad + q) : LLONG_MAX;
-            const int64_t a1 = q + 1 < o1 ? __ldg(Ad + q + 1) : LLONG_MAX;
-            const int64_t a2 = q + 2 < o1 ? __ldg(Ad + q + 2) : LLONG_MAX;
-            const int64_t a3 = q + 3 < o1 ? __ldg(Ad + q + 3) : LLONG_MAX;
-            const int k = (a0 < X) + (a1 < X) + (a2 < X) + (a3 < X);
-            q += k;
-            if (k < 4) break;
-        }
-        return q;
+    const bool ok = i < n_fft;
+    const int ii = ok ? i : 0;
+    const int64_t o0 = ok ? __ldg(offs + ii) : 0;
+    const int64_t o1 = ok ? __ldg(offs + ii + 1) : 0;
+    dv = ok ? __ldg(Dt + ii) : 0;
+    const int64_t s0 = ok ? __ldg(S0 + ii) : 0;
+    cb = s0 + (int64_t)j0 * dv + base_shift;
+    const int64_t span = (int64_t)(R - 1) * dv;
+    const int64_t lo = cb + (span < 0 ? span : 0);
+    const int64_t hi = cb + (span > 0 ? span : 0) + e_fixed;
+    int64_t a = o0, b = o1;
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (__ldg(Ad + m) < lo) a = m + 1; else b = m;
     }
-    int64_t b = o1;
-    while (q < b) {
-        const int64_t m = (q + b) >> 1;
-        if (__ldg(Ad + m) < X) q = m + 1; else b = m;
+    q0 = a;
+    b = o1;
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (__ldg(Ad + m) < hi) a = m + 1; else b = m;
     }
-    return q;
-}
-
-// Adds the 32 row updates of one peak.  The lane visits rows lane ^ g(t),
-// g(t) = t ^ (t >> 1) (Gray code): for every step t the 32 lanes of the warp
-// visit 32 different rows, i.e. 32 different banks, and consecutive rows of
-// one lane differ in one bit b, so X moves by +-2^b D, with the sign fixed by
-// the lane's bit b and by g(t) (a compile-time constant).
-//   X    = A - shift of row `lane` - tile origin, 32.32 fixed point
-//   e[b] = +-(D << b), sign + when the lane's bit b is set
-// An update whose cell falls outside the tile goes to the dump cell E (never
-// read), so every step issues its atomic unconditionally -- no branch.
-// Peak windows of NF FFTs per lane, with every load of the NF lookups issued
-// together (three dependent rounds: CSR/shift tables, bucket entries, positions)
-// instead of one lookup after the other.  For FFT i on rows j0 .. j0 + R - 1 of
-// a tile whose stripe starts L lie in [0, E): the peaks with lo <= A < hi,
-// lo = cb + min(0, (R-1) D), hi = cb + max(0, (R-1) D) + E 2^32, cb = S0 + j0 D
-// + tile origin.  Outputs: cb, D, first peak q0 and count n (0 for i >= n_fft).
-// Every index stays inside the FFT's CSR range for any input.
-template <int NF>
-__device__ __forceinline__ void lookup_windows(const int64_t *__restrict__ Ad,
-                                               const int64_t *__restrict__ offs,
-                                               const int64_t *__restrict__ S0,
-                                               const int64_t *__restrict__ Dt,
-                                               const int32_t *__restrict__ bidx, int32_t bbase,
-                                               int32_t bgsh, int32_t bnb, int n_fft, int j0, int R,
-                                               int64_t base_shift, int64_t e_fixed,
-                                               const int (&fi)[NF], int64_t (&cb)[NF],
-                                               int64_t (&dv)[NF], int64_t (&q0)[NF], int (&n)[NF])
-{
-    int64_t o0[NF], o1[NF], lo[NF], hi[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        const bool ok = fi[f] < n_fft;
-        const int i = ok ? fi[f] : 0;
-        o0[f] = ok ? __ldg(offs + i) : 0;
-        o1[f] = ok ? __ldg(offs + i + 1) : 0;
-        dv[f] = ok ? __ldg(Dt + i) : 0;
-        const int64_t s0 = ok ? __ldg(S0 + i) : 0;
-        cb[f] = s0 + (int64_t)j0 * dv[f] + base_shift;
-        const int64_t span = (int64_t)(R - 1) * dv[f];
-        lo[f] = cb[f] + (span < 0 ? span : 0);
-        hi[f] = cb[f] + (span > 0 ? span : 0) + e_fixed;
-    }
-    if (bidx == nullptr) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            int64_t a = o0[f], b = o1[f];
-            while (a < b) {
-                const int64_t m = (a + b) >> 1;
-                if (__ldg(Ad + m) < lo[f]) a = m + 1; else b = m;
-            }
-            q0[f] = a;
-            b = o1[f];
-            while (a < b) {
-                const int64_t m = (a + b) >> 1;
-                if (__ldg(Ad + m) < hi[f]) a = m + 1; else b = m;
-            }
-            n[f] = (int)(a - q0[f]);
-        }
-        return;
-    }
-    // bucket entries: lower bounds of the first peak >= lo and >= hi
-    int64_t ql[NF], qh[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        const bool ok = fi[f] < n_fft;
-        const int32_t *brow = bidx + (int64_t)(ok ? fi[f] : 0) * bnb;
-        const int32_t cnt = (int32_t)(o1[f] - o0[f]);
-        int gl = ((int)(lo[f] >> 32) - bbase) >> bgsh;
-        int gh = ((int)(hi[f] >> 32) - bbase) >> bgsh;
-        const int32_t rl = (ok && gl >= 0) ? __ldg(brow + (gl < bnb ? gl : bnb - 1)) : 0;
-        const int32_t rh = (ok && gh >= 0) ? __ldg(brow + (gh < bnb ? gh : bnb - 1)) : 0;
-        ql[f] = o0[f] + (rl < 0 ? 0 : (rl > cnt ? cnt : rl));
-        qh[f] = o0[f] + (rh < 0 ? 0 : (rh > cnt ? cnt : rh));
-    }
-    // forward scans, four positions at a time, all NF x 2 scans' loads together
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        int64_t al[4], ah[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            al[m] = ql[f] + m < o1[f] ? __ldg(Ad + ql[f] + m) : LLONG_MAX;
-            ah[m] = qh[f] + m < o1[f] ? __ldg(Ad + qh[f] + m) : LLONG_MAX;
-        }
-        int kl = 0, kh = 0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            kl += al[m] < lo[f];
-            kh += ah[m] < hi[f];
-        }
-        ql[f] += kl;
-        qh[f] += kh;
-        // rare: more than four peaks inside one bucket before the bound
-        while (kl == 4) {
-            kl = 0;
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                kl += (ql[f] + m < o1[f] ? __ldg(Ad + ql[f] + m) : LLONG_MAX) < lo[f];
-            ql[f] += kl;
-        }
-        if (qh[f] < ql[f]) {
-            qh[f] = ql[f];
-            kh = 4;
-        }
-        while (kh == 4) {
-            kh = 0;
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                kh += (qh[f] + m < o1[f] ? __ldg(Ad + qh[f] + m) : LLONG_MAX) < hi[f];
-            qh[f] += kh;
-        }
-        q0[f] = ql[f];
-        n[f] = (int)(qh[f] - ql[f]);
-    }
+    n = (int)(a - q0);
 }
 
 // The transform's peak window of every (direction, slab, tile, FFT), to whole
@@ -785,20 +641,23 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // a stripe starting at cell s (so L in [0, W + K - 1) covers every stripe that
 // touches the tile), row stride 32 words: row r lives in bank r.
 //
-// Accumulate: each warp takes 32 FFTs at a time (lane <-> FFT) and finds, per
-// FFT, the peaks that can reach the tile on some row of the slab (bucket index
-// + short scan).  The peaks of the 32 FFTs are then dealt out to the lanes in
-// rounds of 32 (a warp scan of the per-FFT counts; each lane finds the FFT
-// owning its peak from the round's start bits), the next round's positions
-// are loaded while the current round is added, and every lane adds its own
-// peak's 32 row updates along the Gray-code row order (add_peak_rows), so the
-// 32 atomics of one warp instruction always go to 32 different banks.
+// Accumulate: each warp takes 32 FFTs at a time (lane <-> FFT) and reads, per
+// FFT, the window of peaks that can reach the tile on some row of the slab
+// (precomputed by windows_kernel, else a binary search).  The windowed peaks
+// of the 32 FFTs are dealt out to the lanes in rounds of 32 slots (a warp scan
+// of the per-FFT slot counts; each lane finds the FFT owning its slot from the
+// round's start bits); START mode puts two peaks of one FFT in a slot.  The
+// next round's positions are loaded while the current round is added, and
+// every lane adds its peaks' 32 row updates along the Gray-code row order
+// (start_step / pair_step / diff_step), so the 32 atomics of one warp
+// instruction always go to 32 different banks.
 //
-// Emit: lane l walks row l along f0 over a segment of the tile (one segment
-// per warp): START sums a K-cell window of starts, DIFF takes a running sum
-// with the other segments' totals as carry-in.  The count goes to the map
-// (optional) and the warp's max over rows (smallest row on ties) to the
-// direction's profile by a 64-bit atomicMax, which is order-independent.
+// Emit: warps take 16-cell groups along f0 (START, packed counts) or segments
+// (DIFF, or counts too large to pack); lane l walks row l: START sums a K-cell
+// window of starts, DIFF takes a running sum with the other segments' totals
+// as carry-in.  The count goes to the map (optional) and the warp's max over
+// rows (smallest row on ties) to the direction's profile by a 64-bit
+// atomicMax, which is order-independent.
 template <int MODE, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
 transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words,
@@ -858,9 +717,6 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int64_t *__restrict__ offs = J->offsets;
         const int64_t *__restrict__ S0 = J->S0;
         const int64_t *__restrict__ Dt = J->D;
-        const int32_t *__restrict__ bidx =
-            J->bidx ? J->bidx + (int64_t)d_abs * n_fft * J->bnb : nullptr;
-        const int32_t bbase = J->bbase, bgsh = J->bgsh, bnb = J->bnb;
         const int2 *__restrict__ wrow =
             J->windows ? J->windows + (((int64_t)d_rel * J->n_slabs + slab) * J->n_tiles + tile) *
                                           n_fft
@@ -904,15 +760,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     n = (int)(b - a);
                 }
             } else {
-                const int fi[1] = {(c << 5) + lane};
-                int64_t cb1[1], dv1[1], q01[1];
-                int n1[1];
-                lookup_windows<1>(Ad, offs, S0, Dt, bidx, bbase, bgsh, bnb, n_fft, j0, R,
-                                  base_shift, e_fixed, fi, cb1, dv1, q01, n1);
-                cb = cb1[0];
-                dv = dv1[0];
-                q0 = q01[0];
-                n = n1[0];
+                lookup_window(Ad, offs, S0, Dt, n_fft, (c << 5) + lane, j0, R, base_shift,
+                              e_fixed, cb, dv, q0, n);
             }
             // START mode deals the peaks out in pairs of one FFT (one slot = two
             // consecutive peaks of the window; an odd count leaves the last slot's
@@ -1312,15 +1161,13 @@ cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s)
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, const BucketIndex &bix, bool validate,
-                             cudaStream_t s)
+                             double *out_r, int32_t *err, bool validate, cudaStream_t s)
 {
     if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
     dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
     positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
-                                                  kt, cshift, A, out_r, err, bix,
-                                                  validate ? 1 : 0);
+                                                  kt, cshift, A, out_r, err, validate ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1361,18 +1208,6 @@ size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, in
     size_t words = (size_t)(tile_cells + k_over + 2 * guard) * kRows + (size_t)nwarps * 32;
     if (mode == FH_MODE_DIFF) words += (size_t)nwarps * 32;
     return (words + 4) * sizeof(int32_t) + 128;
-}
-
-BucketIndex bucket_geometry(int32_t n_f0, int32_t k_over, double cells_per_peak)
-{
-    BucketIndex b;
-    int gsh = 4;
-    while (gsh < 12 && (double)(1 << (gsh + 1)) <= cells_per_peak) ++gsh;
-    const int32_t margin = n_f0 / 2 > 1024 ? n_f0 / 2 : 1024;
-    b.gsh = gsh;
-    b.base = -k_over - margin;
-    b.nb = (int32_t)(((int64_t)n_f0 + k_over + 2 * (int64_t)margin) >> gsh) + 2;
-    return b;
 }
 
 // Kernel instantiation for a counting mode and block size: blocks of up to 512

@@ -207,7 +207,7 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
         if (e == cudaSuccess)
             e = launch_positions(j->d_freq, j->d_off, j->d_v, j->d_sky, j->n_fft, j->n_peaks,
                                  j->n_dir, d.f0_min, j->kt, d.k_over, j->d_A, nullptr, j->d_err,
-                                 BucketIndex{}, false, s);
+                                 false, s);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(j->d_prof, 0, 8 * (size_t)j->n_dir * d.n_f0, s);
         if (e != cudaSuccess) return cuda_error(e, "job set-up");
@@ -248,7 +248,6 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.D = j->d_D;
             t.profile = j->d_prof;
             t.maps = nullptr;
-            t.bidx = nullptr;
             t.dmax = j->d_dmax;
             t.err = j->d_err;
             t.n_peaks = j->n_peaks;

@@ -144,7 +144,7 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     if (e == cudaSuccess) e = launch_prep(pa, s);
     if (e == cudaSuccess)
         e = launch_positions(pm->freq, offsets, v_over_c, sky_n, n, np, 1, d.f0_min, kt, d.k_over, A,
-                             nullptr, err, BucketIndex{}, true, s);
+                             nullptr, err, true, s);
     if (e != cudaSuccess) return cuda_error(e, "fh_search_static set-up");
 
     const int32_t mode = d.mode == FH_MODE_DIFF ? FH_MODE_DIFF : FH_MODE_START;
@@ -166,7 +166,7 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     job.D = D;
     job.profile = profile;
     job.maps = nullptr;
-    job.bidx = nullptr;  // no bucket index in the fixed scratch: binary search
+    job.windows = nullptr;  // no window table in the fixed scratch: binary search
     job.dmax = dmax;
     job.err = err;
     job.n_peaks = np;
