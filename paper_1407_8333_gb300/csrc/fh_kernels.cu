@@ -527,6 +527,15 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     }
 }
 
+// Cell of a 32.32 fixed-point position: its high word, read straight from
+// the 64-bit register pair.
+__device__ __forceinline__ uint32_t cell_of(int64_t X)
+{
+    uint32_t lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(X));
+    return hi;
+}
+
 __host__ __device__ constexpr int ctz5(int x)
 {
     return (x & 1) ? 0 : (x & 2) ? 1 : (x & 4) ? 2 : (x & 8) ? 3 : 4;
@@ -551,7 +560,7 @@ __device__ __forceinline__ void start_step(uint32_t rbase, int64_t &X, const int
 {
     constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
     const uint32_t rb = rbase ^ (gt << 2);
-    uint32_t cell = (uint32_t)(int32_t)(X >> 32);
+    uint32_t cell = cell_of(X);
     if (CLAMP) cell = min(cell, E);
     const uint32_t addr = cell * stride + rb;
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
@@ -597,8 +606,8 @@ __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &
 {
     constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
     const uint32_t rb = rbase ^ (gt << 2);
-    uint32_t c1 = (uint32_t)(int32_t)(X1 >> 32);
-    uint32_t c2 = (uint32_t)(int32_t)(X2 >> 32);
+    uint32_t c1 = cell_of(X1);
+    uint32_t c2 = cell_of(X2);
     if (CLAMP) {
         c1 = min(c1, E);
         c2 = min(c2, E);
