@@ -224,6 +224,19 @@ int fh_autotune(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *tile_ce
  * plan creation). */
 int64_t fh_plan_launches(fh_plan plan);
 
+/* Kernel timing (measurement aid, off by default).  With timing on, every
+ * fh_transform records CUDA events on its stream around each direction
+ * group's window pre-pass and transform kernel (the last 256 groups are
+ * kept); switching it on (again) forgets earlier records.  Do not switch it
+ * on for a step that is being captured into a CUDA graph. */
+int fh_plan_set_timing(fh_plan plan, int32_t on);
+
+/* Sums, over the recorded groups, of the window pre-pass and transform kernel
+ * durations in milliseconds (waits for the last recorded group to finish);
+ * *n_groups receives the number of groups summed. */
+int fh_plan_kernel_times(fh_plan plan, int64_t *n_groups, double *windows_ms,
+                         double *transform_ms);
+
 /* ---- allocation-free search (one direction) ------------------------------ */
 
 /* fh_search_static: steps a1-a6 for ONE sky direction, like fh_correct_doppler

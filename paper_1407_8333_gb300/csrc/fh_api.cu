@@ -166,6 +166,8 @@ Sizes plan_sizes(const fh_plan_desc &d)
 
 }  // namespace
 
+constexpr int64_t kTimingSlots = 256;
+
 struct fh_plan_s {
     fh_plan_desc d{};
     int device = 0;
@@ -190,9 +192,16 @@ struct fh_plan_s {
     int32_t n_dir = 0;
     int64_t launches = 0;
     size_t prepared_smem[3] = {0, 0, 0};
+    // optional kernel timing: per direction group of fh_transform, events before
+    // the window pre-pass, between it and the transform, after the transform
+    int32_t timing = 0;
+    std::vector<cudaEvent_t> tev;  // 3 x kTimingSlots
+    int64_t tev_next = 0;          // groups recorded since timing was switched on
 
     void release()
     {
+        for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
+        tev.clear();
         void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, dmax, win};
         for (void *b : bufs)
             if (b) cudaFree(b);
@@ -385,6 +394,51 @@ int fh_destroy_plan(fh_plan p)
 
 int64_t fh_plan_launches(fh_plan p) { return p ? p->launches : -1; }
 
+int fh_plan_set_timing(fh_plan p, int32_t on)
+{
+    if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
+    DeviceGuard g(p->device);
+    if (on && p->tev.empty()) {
+        p->tev.resize(3 * (size_t)kTimingSlots, nullptr);
+        for (auto &ev : p->tev) {
+            const cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) {
+                for (cudaEvent_t x : p->tev)
+                    if (x) cudaEventDestroy(x);
+                p->tev.clear();
+                return cuda_error(e, "cudaEventCreate");
+            }
+        }
+    }
+    p->timing = on ? 1 : 0;
+    p->tev_next = 0;
+    return FH_OK;
+}
+
+int fh_plan_kernel_times(fh_plan p, int64_t *n_groups, double *windows_ms, double *transform_ms)
+{
+    if (!p || !n_groups || !windows_ms || !transform_ms)
+        return set_error(FH_ERR_INVALID_ARG, "null plan or output");
+    DeviceGuard g(p->device);
+    const int64_t n = std::min(p->tev_next, kTimingSlots);
+    double w = 0.0, t = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t slot = (p->tev_next - n + k) % kTimingSlots;
+        cudaEvent_t *ev = &p->tev[3 * (size_t)slot];
+        cudaError_t e = cudaEventSynchronize(ev[2]);
+        float a = 0.f, b = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+        if (e != cudaSuccess) return cuda_error(e, "kernel timing events");
+        w += a;
+        t += b;
+    }
+    *n_groups = n;
+    *windows_ms = w;
+    *transform_ms = t;
+    return FH_OK;
+}
+
 int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
                        const double *sky_n, int32_t n_dir, double *out_r, int64_t *out_A,
                        void *stream)
@@ -540,9 +594,16 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
         job.item_begin = 0;
         job.n_items = per_dir * gn;
         job.windows = p->win;
+        cudaEvent_t *ev = nullptr;
+        if (p->timing && !p->tev.empty()) {
+            ev = &p->tev[3 * (size_t)(p->tev_next % kTimingSlots)];
+            ++p->tev_next;
+            cudaEventRecord(ev[0], s);
+        }
         e = launch_windows(job, p->win, s);
         if (e != cudaSuccess) return cuda_error(e, "windows launch");
         ++p->launches;
+        if (ev) cudaEventRecord(ev[1], s);
         tbl.job[0] = job;
         if (schedule == FH_SCHED_PLAIN) {
             // one sky direction per launch, one block per work item
@@ -555,6 +616,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
         }
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
         ++p->launches;
+        if (ev) cudaEventRecord(ev[2], s);
     }
     return FH_OK;
 }

@@ -93,6 +93,9 @@ _SIGS = {
     "fh_sync": ([_P, _P], ctypes.c_int),
     "fh_autotune": ([_P, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P], ctypes.c_int),
     "fh_plan_launches": ([_P], _i64),
+    "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
+    "fh_plan_kernel_times": ([_P, ctypes.POINTER(_i64), ctypes.POINTER(_f64), ctypes.POINTER(_f64)],
+                             ctypes.c_int),
     "fh_server_create": ([_i64, _i32, ctypes.POINTER(_P)], ctypes.c_int),
     "fh_server_destroy": ([_P], ctypes.c_int),
     "fh_submit": ([_P, ctypes.POINTER(fh_job_desc), ctypes.POINTER(_i64)], ctypes.c_int),
@@ -275,6 +278,21 @@ def fh_autotune(plan, dir_begin: int, n_dir: int, stream=None) -> tuple:
 
 def fh_plan_launches(plan) -> int:
     return int(load().fh_plan_launches(plan))
+
+
+def fh_plan_set_timing(plan, on: bool = True) -> None:
+    _check(load().fh_plan_set_timing(plan, 1 if on else 0), "fh_plan_set_timing")
+
+
+def fh_plan_kernel_times(plan) -> tuple:
+    """(groups, window pre-pass ms, transform kernel ms), summed over the groups
+    recorded since timing was switched on."""
+    n = _i64(0)
+    w = ctypes.c_double(0.0)
+    t = ctypes.c_double(0.0)
+    _check(load().fh_plan_kernel_times(plan, ctypes.byref(n), ctypes.byref(w), ctypes.byref(t)),
+           "fh_plan_kernel_times")
+    return int(n.value), float(w.value), float(t.value)
 
 
 def fh_bench_smem_atomics(variant: int = 0, iters: int = 4096, stream=None) -> tuple:
