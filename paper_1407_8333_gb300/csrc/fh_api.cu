@@ -261,17 +261,42 @@ int validate_host_inputs(const fh_plan_desc &d, double kt, const fh_peakmap *pm,
     if (pm->offsets[n] != pm->n_peaks)
         return set_error(FH_ERR_UNSORTED, "offsets[n_fft] = %lld != n_peaks = %lld",
                          (long long)pm->offsets[n], (long long)pm->n_peaks);
+    // Screening pass without branches (positive finite doubles order like their
+    // bit patterns, read as unsigned integers); the detailed pass that names the
+    // first bad peak runs only when the screen fails.  With every FFT's
+    // frequencies ascending, the band's range comes from first and last peaks.
+    {
+        const uint64_t *fb = reinterpret_cast<const uint64_t *>(pm->freq);
+        // bits - 1 of a positive finite double lies in [0, bits(DBL_MAX) - 1]; zero,
+        // negatives, infinities and NaNs fall outside
+        const uint64_t kPosFiniteMax = 0x7FEFFFFFFFFFFFFEull;
+        uint64_t bad = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t a = pm->offsets[i], b = pm->offsets[i + 1];
+            if (a >= b) continue;
+            bad |= (uint64_t)((fb[a] - 1) > kPosFiniteMax);
+            for (int64_t q = a + 1; q < b; ++q)
+                bad |= (uint64_t)((fb[q] - 1) > kPosFiniteMax) | (uint64_t)(fb[q] <= fb[q - 1]);
+        }
+        if (bad) {
+            for (int32_t i = 0; i < n; ++i) {
+                for (int64_t q = pm->offsets[i]; q < pm->offsets[i + 1]; ++q) {
+                    const double f = pm->freq[q];
+                    if (!(std::isfinite(f) && f > 0.0))
+                        return set_error(FH_ERR_INVALID_ARG, "freq[%lld] must be finite and > 0",
+                                         (long long)q);
+                    if (q > pm->offsets[i] && !(f > pm->freq[q - 1]))
+                        return set_error(FH_ERR_UNSORTED, "freq not ascending within FFT %d", i);
+                }
+            }
+        }
+    }
     double fmin = INFINITY, fmax = 0.0;
     for (int32_t i = 0; i < n; ++i) {
-        for (int64_t q = pm->offsets[i]; q < pm->offsets[i + 1]; ++q) {
-            const double f = pm->freq[q];
-            if (!(std::isfinite(f) && f > 0.0))
-                return set_error(FH_ERR_INVALID_ARG, "freq[%lld] must be finite and > 0",
-                                 (long long)q);
-            if (q > pm->offsets[i] && !(f > pm->freq[q - 1]))
-                return set_error(FH_ERR_UNSORTED, "freq not ascending within FFT %d", i);
-            fmin = std::min(fmin, f);
-            fmax = std::max(fmax, f);
+        const int64_t a = pm->offsets[i], b = pm->offsets[i + 1];
+        if (a < b) {
+            fmin = std::min(fmin, pm->freq[a]);
+            fmax = std::max(fmax, pm->freq[b - 1]);
         }
     }
     double vmax = 0.0, nmax = 0.0, tmax = 0.0;

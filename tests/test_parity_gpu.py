@@ -201,6 +201,23 @@ def test_host_input_errors(fh):
         with pytest.raises(fh.FHError) as ei:
             fh.fh_correct_doppler(plan, inp.t, inp.offsets, f, inp.v, inp.sky)
         assert ei.value.code == fh.FH_ERR_INVALID_ARG
+        # the edges of the host screen: +inf, 0, a negative value, and each of
+        # them as the first or the last peak of an FFT
+        first, last = int(inp.offsets[4]), int(inp.offsets[5]) - 1
+        for where in (first, last):
+            for bad_value in (np.inf, 0.0, -1.0, -0.0):
+                f = inp.freq.copy()
+                f[where] = bad_value
+                with pytest.raises(fh.FHError) as ei:
+                    fh.fh_correct_doppler(plan, inp.t, inp.offsets, f, inp.v, inp.sky)
+                assert ei.value.code in (fh.FH_ERR_INVALID_ARG, fh.FH_ERR_UNSORTED), \
+                    (where, bad_value)
+        # equal neighbours are not strictly ascending
+        f = inp.freq.copy()
+        f[first + 1] = f[first]
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_correct_doppler(plan, inp.t, inp.offsets, f, inp.v, inp.sky)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
         t = inp.t.copy()
         t[4] = t[3]
         with pytest.raises(fh.FHError) as ei:
