@@ -169,7 +169,10 @@ int64_t fh_plan_device_bytes(const fh_plan_desc *desc);
  *   n_dir     1 .. max_dir
  *   out_r     nullable device n_dir x n_fft: copy of the Doppler factors
  *   out_A     nullable device n_dir x n_peaks: copy of the positions A
- * Host-input errors: FH_ERR_INVALID_ARG, FH_ERR_UNSORTED, FH_ERR_RANGE. */
+ * Host-input errors: FH_ERR_INVALID_ARG, FH_ERR_UNSORTED, FH_ERR_RANGE; after
+ * one the plan holds no peakmap (fh_transform refuses until the next
+ * successful call), since its device copies of the inputs were already being
+ * overwritten. */
 int fh_correct_doppler(fh_plan plan, const fh_peakmap *pm, const double *v_over_c,
                        const double *sky_n, int32_t n_dir, double *out_r,
                        int64_t *out_A, void *stream);

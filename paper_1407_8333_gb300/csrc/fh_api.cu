@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <future>
 #include <map>
 #include <mutex>
 #include <new>
@@ -270,13 +271,31 @@ int validate_host_inputs(const fh_plan_desc &d, double kt, const fh_peakmap *pm,
         // bits - 1 of a positive finite double lies in [0, bits(DBL_MAX) - 1]; zero,
         // negatives, infinities and NaNs fall outside
         const uint64_t kPosFiniteMax = 0x7FEFFFFFFFFFFFFEull;
+        auto screen = [&](int32_t i0, int32_t i1) {
+            uint64_t bad = 0;
+            for (int32_t i = i0; i < i1; ++i) {
+                const int64_t a = pm->offsets[i], b = pm->offsets[i + 1];
+                if (a >= b) continue;
+                bad |= (uint64_t)((fb[a] - 1) > kPosFiniteMax);
+                for (int64_t q = a + 1; q < b; ++q)
+                    bad |= (uint64_t)((fb[q] - 1) > kPosFiniteMax) | (uint64_t)(fb[q] <= fb[q - 1]);
+            }
+            return bad;
+        };
+        // large peakmaps: FFT ranges on up to 8 threads
+        const int parts =
+            (int)std::min<int64_t>(8, std::max<int64_t>(1, pm->n_peaks / ((int64_t)1 << 18)));
         uint64_t bad = 0;
-        for (int32_t i = 0; i < n; ++i) {
-            const int64_t a = pm->offsets[i], b = pm->offsets[i + 1];
-            if (a >= b) continue;
-            bad |= (uint64_t)((fb[a] - 1) > kPosFiniteMax);
-            for (int64_t q = a + 1; q < b; ++q)
-                bad |= (uint64_t)((fb[q] - 1) > kPosFiniteMax) | (uint64_t)(fb[q] <= fb[q - 1]);
+        if (parts > 1 && n >= parts) {
+            std::vector<std::future<uint64_t>> fut;
+            for (int k = 1; k < parts; ++k)
+                fut.push_back(std::async(std::launch::async, screen,
+                                         (int32_t)((int64_t)n * k / parts),
+                                         (int32_t)((int64_t)n * (k + 1) / parts)));
+            bad = screen(0, (int32_t)((int64_t)n / parts));
+            for (auto &f : fut) bad |= f.get();
+        } else {
+            bad = screen(0, n);
         }
         if (bad) {
             for (int32_t i = 0; i < n; ++i) {
@@ -489,9 +508,10 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     if (e == cudaSuccess) e = cudaMemsetAsync(p->dmax, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
     if (pm->mem_kind == FH_MEM_HOST) {
-        int rc = validate_host_inputs(p->d, p->kt, pm, v_over_c, sky_n, n_dir);
-        if (rc) return rc;
-        p->guard = std::max(default_guard(p->d), host_guard(p->d, p->kt, pm->t_fft, n));
+        if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
+            return set_error(FH_ERR_INVALID_ARG, "null peakmap array");
+        // the copies are enqueued first, so that the host checks below run while
+        // the inputs move; a failed check leaves the plan without a peakmap
         struct {
             void *dst;
             const void *src;
@@ -501,11 +521,15 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
                   {p->freq, pm->freq, 8 * (size_t)np},
                   {p->v, v_over_c, 24 * (size_t)n},
                   {p->sky, sky_n, 24 * (size_t)n_dir}};
+        p->n_fft = -1;
         for (auto &c : cp) {
             if (c.bytes == 0) continue;
             e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(H2D inputs)");
         }
+        int rc = validate_host_inputs(p->d, p->kt, pm, v_over_c, sky_n, n_dir);
+        if (rc) return rc;
+        p->guard = std::max(default_guard(p->d), host_guard(p->d, p->kt, pm->t_fft, n));
         t_src = p->t;
         f_src = p->freq;
         v_src = p->v;
