@@ -64,8 +64,8 @@ def _load():
             lib.fho_doppler_factor.argtypes = [i32, P, i32, P, P]
             lib.fho_positions.argtypes = [i32, P, P, i32, P, f64, f64, i32, P]
             lib.fho_shift_tables.argtypes = [i32, P, f64, f64, f64, f64, P, P]
-            lib.fho_hough_map.argtypes = [i32, P, P, P, P, i32, i32, i32, P, P]
-            lib.fho_hough_map_direct.argtypes = [i32, P, P, P, P, i32, i32, i32, P]
+            lib.fho_hough_map.argtypes = [i32, P, P, P, P, i32, i32, i32, P, P, P]
+            lib.fho_hough_map_direct.argtypes = [i32, P, P, P, P, i32, i32, i32, P, P]
             lib.fho_profile.argtypes = [P, i32, i32, P, P]
             lib.fho_select.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, P, P]
             _lib = lib
@@ -123,8 +123,10 @@ def shift_tables(t, t_ref: float, kt: float, fdot_min: float, fdot_step: float):
 
 # ---------------------------------------------------------------- a4 + a5
 def hough_map(offsets, A_dir, S0, D, k_over: int, n_f0: int, n_fdot: int = None,
-              rows=None) -> np.ndarray:
-    """a4 + a5: number counts of one direction (differential +1/-1, cumulative sum)."""
+              rows=None, weights=None) -> np.ndarray:
+    """a4 + a5: number counts of one direction (differential +1/-1, cumulative
+    sum); with ``weights`` (n_fft integers, already quantised) the adaptive
+    map of Eq. ncountadap: each FFT's peaks add its weight instead of 1."""
     offsets = _c(offsets, np.int64)
     A_dir = _c(A_dir, np.int64)
     S0 = _c(S0, np.int64)
@@ -136,22 +138,50 @@ def hough_map(offsets, A_dir, S0, D, k_over: int, n_f0: int, n_fdot: int = None,
         rows = _c(rows, np.int32)
         n_rows = rows.shape[0]
         rp = _p(rows)
+    wp = None
+    if weights is not None:
+        weights = _c(weights, np.int32)
+        wp = _p(weights)
     m = np.empty((n_rows, int(n_f0)), dtype=np.int32)
     _load().fho_hough_map(offsets.shape[0] - 1, _p(offsets), _p(A_dir), _p(S0), _p(D),
-                          int(k_over), int(n_f0), n_rows, rp, _p(m))
+                          int(k_over), int(n_f0), n_rows, rp, wp, _p(m))
     return m
 
 
-def hough_map_direct(offsets, A_dir, S0, D, k_over: int, n_f0: int, n_fdot: int) -> np.ndarray:
-    """Direct per-cell counting (tiny inputs): the plain definition of Eq. ncount."""
+def hough_map_direct(offsets, A_dir, S0, D, k_over: int, n_f0: int, n_fdot: int,
+                     weights=None) -> np.ndarray:
+    """Direct per-cell counting (tiny inputs): the plain definition of Eq. ncount
+    (Eq. ncountadap with ``weights``)."""
     offsets = _c(offsets, np.int64)
     A_dir = _c(A_dir, np.int64)
     S0 = _c(S0, np.int64)
     D = _c(D, np.int64)
+    wp = None
+    if weights is not None:
+        weights = _c(weights, np.int32)
+        wp = _p(weights)
     m = np.empty((int(n_fdot), int(n_f0)), dtype=np.int32)
     _load().fho_hough_map_direct(offsets.shape[0] - 1, _p(offsets), _p(A_dir), _p(S0),
-                                 _p(D), int(k_over), int(n_f0), int(n_fdot), _p(m))
+                                 _p(D), int(k_over), int(n_f0), int(n_fdot), wp, _p(m))
     return m
+
+
+WEIGHT_SUM_LIMIT = 1 << 30
+
+
+def quantize_weights(w, frac_bits: int) -> np.ndarray:
+    """Adaptive weights (Eq. ncountadap) as integers: W = rint(w 2^F), binary64,
+    ties to even.  Weights must be finite and >= 0 and each direction's sum of
+    W at most 2^30 (so that no count can leave int32)."""
+    w = np.asarray(w, dtype=np.float64)
+    if not (0 <= int(frac_bits) <= 24):
+        raise ValueError("frac_bits must be in [0, 24]")
+    if not np.all(np.isfinite(w)) or np.any(w < 0):
+        raise ValueError("weights must be finite and >= 0")
+    W = np.rint(w * float(2 ** int(frac_bits)))
+    if np.any(W.reshape(W.shape[0] if W.ndim > 1 else 1, -1).sum(axis=1) > WEIGHT_SUM_LIMIT):
+        raise ValueError("a direction's quantised weights sum above 2^30")
+    return W.astype(np.int64)
 
 
 # ---------------------------------------------------------------- a6
@@ -180,27 +210,39 @@ def select(pcount, prow, subband_cells: int, top_k: int, excl: int, sep: int, n_
 
 
 def report(cell, row, cnt, f0_min: float, kt: float, fdot_min: float, fdot_step: float,
-           n_fft: int, p0: float):
+           n_fft: int, p0: float, s1=None, s2=None):
     """Reporting columns of each pick, binary64: cell-centre frequency, row
-    spin-down and critical ratio CR = (n - N p0) / sqrt(N p0 (1 - p0)) (Eq. cr)."""
+    spin-down and critical ratio CR = (n - N p0) / sqrt(N p0 (1 - p0)) (Eq. cr).
+    Adaptive map (``s1``, ``s2`` = per-direction sums of the integer weights
+    and of their squares): mean p0 S1 and variance p0 (1 - p0) S2 of the
+    weighted noise count, CR = (n - S1 p0) / sqrt((S2 p0) (1 - p0)); for unit
+    weights S1 = S2 = N and this is Eq. cr, operation for operation."""
     cell = np.asarray(cell)
     row = np.asarray(row)
     cnt = np.asarray(cnt)
     valid = cnt >= 0
     f0 = np.where(valid, f0_min + (cell.astype(np.float64) + 0.5) / kt, 0.0)
     fdot = np.where(valid, fdot_min + row.astype(np.float64) * fdot_step, 0.0)
-    np0 = float(n_fft) * p0
-    var = np0 * (1.0 - p0)
+    if s1 is None:
+        np0 = float(n_fft) * p0
+        var = np0 * (1.0 - p0)
+    else:
+        shape = (-1,) + (1,) * (cnt.ndim - 1)
+        np0 = (np.asarray(s1, dtype=np.int64).astype(np.float64) * p0).reshape(shape)
+        var = ((np.asarray(s2, dtype=np.int64).astype(np.float64) * p0) * (1.0 - p0)).reshape(shape)
     cr = np.where(valid, (cnt.astype(np.float64) - np0) / np.sqrt(var), 0.0)
     return f0, fdot, cr
 
 
 # ---------------------------------------------------------------- whole path
-def search(inp, params: dict, want_maps: bool = False, dirs=None):
+def search(inp, params: dict, want_maps: bool = False, dirs=None, weights=None,
+           frac_bits: int = 0):
     """Steps a1-a6 for every direction of ``inp`` (a synth.Inputs).
 
     Returns a dict with r, A, S0, D, per-direction profiles, candidate arrays
-    (n_dir, n_sb, top_k) and, if asked, the maps (n_dir, n_fdot, n_f0).
+    (n_dir, n_sb, top_k) and, if asked, the maps (n_dir, n_fdot, n_f0).  With
+    ``weights`` (n_dir x n_fft reals) the adaptive map (Eq. ncountadap) of the
+    weights quantised by ``quantize_weights(weights, frac_bits)``.
     """
     kt = float(params["k_over"]) * float(params["t_fft"])
     sky = inp.sky if dirs is None else inp.sky[np.asarray(dirs)]
@@ -209,9 +251,16 @@ def search(inp, params: dict, want_maps: bool = False, dirs=None):
     S0, D = shift_tables(inp.t, params["t_ref"], kt, params["fdot_min"], params["fdot_step"])
     out = dict(r=r, A=A, S0=S0, D=D, pcount=[], prow=[], cell=[], row=[], count=[])
     maps = []
+    W = None
+    if weights is not None:
+        W = quantize_weights(np.asarray(weights, dtype=np.float64).reshape(sky.shape[0], -1),
+                             frac_bits)
+        out["W"] = W
+        out["s1"] = W.sum(axis=1)
+        out["s2"] = (W * W).sum(axis=1)
     for d in range(sky.shape[0]):
         m = hough_map(inp.offsets, A[d], S0, D, params["k_over"], params["n_f0"],
-                      params["n_fdot"])
+                      params["n_fdot"], weights=None if W is None else W[d])
         pc, pr = profile(m)
         c, rr, n = select(pc, pr, params["subband_cells"], params["top_k"],
                           params["excl_cells"], params["sep_cells"], params["n_thr"])
@@ -227,7 +276,7 @@ def search(inp, params: dict, want_maps: bool = False, dirs=None):
         out[k] = np.stack(out[k])
     f0, fdot, cr = report(out["cell"], out["row"], out["count"], params["f0_min"], kt,
                           params["fdot_min"], params["fdot_step"], inp.t.shape[0],
-                          params["p0"])
+                          params["p0"], out.get("s1"), out.get("s2"))
     out.update(f0=f0, fdot=fdot, cr=cr)
     if want_maps:
         out["maps"] = np.stack(maps)

@@ -161,10 +161,15 @@ static int64_t stripe_start(int64_t Ap, int64_t S0i, int64_t Di, int64_t j)
  * (Eq. ncount: +1 in every cell a stripe touches).
  * A: n_peaks positions of this direction (from a2).  rows: the n_rows row
  * indices to compute (NULL = all n_fdot rows in order).  map: n_rows x n_f0.
+ * w: NULL for the plain map, or the adaptive map's integer weights of this
+ * direction, one per FFT (Eq. ncountadap: n = sum_i w_i n_i, the FFT's peaks
+ * adding w_i instead of 1; the weights are given already quantised to fixed
+ * point, so the map stays an exact integer).
  */
 void fho_hough_map(int32_t n_fft, const int64_t *offsets, const int64_t *A,
                    const int64_t *S0, const int64_t *D, int32_t k_over,
-                   int32_t n_f0, int32_t n_rows, const int32_t *rows, int32_t *map)
+                   int32_t n_f0, int32_t n_rows, const int32_t *rows, const int32_t *w,
+                   int32_t *map)
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t q = 0; q < n_rows; ++q) {
@@ -172,11 +177,12 @@ void fho_hough_map(int32_t n_fft, const int64_t *offsets, const int64_t *A,
         int32_t *row = map + (int64_t)q * n_f0;
         memset(row, 0, sizeof(int32_t) * (size_t)n_f0);
         for (int32_t i = 0; i < n_fft; ++i) {
+            const int32_t wi = w ? w[i] : 1;
             for (int64_t p = offsets[i]; p < offsets[i + 1]; ++p) {
                 const int64_t s = stripe_start(A[p], S0[i], D[i], j);
                 const int64_t e = s + k_over;
-                if (s < n_f0 && e > 0) row[s > 0 ? s : 0] += 1;
-                if (e > 0 && e < n_f0) row[e] -= 1;
+                if (s < n_f0 && e > 0) row[s > 0 ? s : 0] += wi;
+                if (e > 0 && e < n_f0) row[e] -= wi;
             }
         }
         int32_t acc = 0;
@@ -188,21 +194,23 @@ void fho_hough_map(int32_t n_fft, const int64_t *offsets, const int64_t *A,
 }
 
 /*
- * The same map by direct counting: every (peak, row) adds 1 to each cell of
- * [s, s + K) inside [0, n_f0).  For tiny inputs only; it is the plain
- * definition of the number count that the differential method must reproduce.
+ * The same map by direct counting: every (peak, row) adds 1 (or its FFT's
+ * weight w[i]) to each cell of [s, s + K) inside [0, n_f0).  For tiny inputs
+ * only; it is the plain definition of the number count that the differential
+ * method must reproduce.
  */
 void fho_hough_map_direct(int32_t n_fft, const int64_t *offsets, const int64_t *A,
                           const int64_t *S0, const int64_t *D, int32_t k_over,
-                          int32_t n_f0, int32_t n_fdot, int32_t *map)
+                          int32_t n_f0, int32_t n_fdot, const int32_t *w, int32_t *map)
 {
     memset(map, 0, sizeof(int32_t) * (size_t)n_fdot * (size_t)n_f0);
     for (int32_t j = 0; j < n_fdot; ++j) {
         for (int32_t i = 0; i < n_fft; ++i) {
+            const int32_t wi = w ? w[i] : 1;
             for (int64_t p = offsets[i]; p < offsets[i + 1]; ++p) {
                 const int64_t s = stripe_start(A[p], S0[i], D[i], j);
                 for (int64_t b = s; b < s + k_over; ++b)
-                    if (b >= 0 && b < n_f0) map[(int64_t)j * n_f0 + b] += 1;
+                    if (b >= 0 && b < n_f0) map[(int64_t)j * n_f0 + b] += wi;
             }
         }
     }
