@@ -166,13 +166,16 @@ def hough_map_direct(offsets, A_dir, S0, D, k_over: int, n_f0: int, n_fdot: int,
     return m
 
 
-WEIGHT_SUM_LIMIT = 1 << 30
+# A cell receives at most two stripes from one FFT (neighbouring peaks of an
+# FFT lie at least 0.9 K cells apart once |v.n| < 0.1), so a weighted count is
+# at most 2 sum(W): sums below 2^30 keep every count inside int32.
+WEIGHT_SUM_LIMIT = (1 << 30) - 1
 
 
 def quantize_weights(w, frac_bits: int) -> np.ndarray:
     """Adaptive weights (Eq. ncountadap) as integers: W = rint(w 2^F), binary64,
     ties to even.  Weights must be finite and >= 0 and each direction's sum of
-    W at most 2^30 (so that no count can leave int32)."""
+    W below 2^30 (so that no count can leave int32)."""
     w = np.asarray(w, dtype=np.float64)
     if not (0 <= int(frac_bits) <= 24):
         raise ValueError("frac_bits must be in [0, 24]")
@@ -180,7 +183,7 @@ def quantize_weights(w, frac_bits: int) -> np.ndarray:
         raise ValueError("weights must be finite and >= 0")
     W = np.rint(w * float(2 ** int(frac_bits)))
     if np.any(W.reshape(W.shape[0] if W.ndim > 1 else 1, -1).sum(axis=1) > WEIGHT_SUM_LIMIT):
-        raise ValueError("a direction's quantised weights sum above 2^30")
+        raise ValueError("a direction's quantised weights sum to 2^30 or more")
     return W.astype(np.int64)
 
 

@@ -118,10 +118,12 @@ def test_quantisation_rejects_bad_weights(oracle_mod, bad):
         oracle_mod.quantize_weights(np.array([bad]), 4)
 
 
-def test_quantisation_rejects_a_sum_above_2_30(oracle_mod):
+def test_quantisation_rejects_a_sum_of_2_30(oracle_mod):
+    """Counts are int32 and a cell takes at most two stripes of one FFT, so each
+    direction's weights must sum below 2^30."""
     with pytest.raises(ValueError):
-        oracle_mod.quantize_weights(np.array([[2.0 ** 29, 2.0 ** 29 + 1.0]]), 0)
-    oracle_mod.quantize_weights(np.array([[2.0 ** 29, 2.0 ** 29]]), 0)
+        oracle_mod.quantize_weights(np.array([[2.0 ** 29, 2.0 ** 29]]), 0)
+    oracle_mod.quantize_weights(np.array([[2.0 ** 29, 2.0 ** 29 - 1.0]]), 0)
 
 
 def test_adaptive_cr_reduces_to_eq_cr_and_is_scale_free(oracle_mod):
