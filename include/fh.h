@@ -185,6 +185,24 @@ int fh_correct_doppler(fh_plan plan, const fh_peakmap *pm, const double *v_over_
 int fh_transform(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
                  void *stream);
 
+/* Adaptive map (Eq. ncountadap: n = sum_i w_i n_i) for the directions of the
+ * last fh_correct_doppler call.
+ *   w          HOST n_dir x n_fft weights (direction-major), finite and >= 0;
+ *              NULL returns the plan to the plain map
+ *   n_dir      must equal the n_dir of that call
+ *   frac_bits  F in [0, 24]: the weights are quantised to integers
+ *              W = rint(w 2^F) (binary64, ties to even), so that maps stay
+ *              exact integers; each direction's W must sum below 2^30
+ * Until the next fh_correct_doppler (which returns the plan to unit
+ * weights), fh_transform adds W_i for every stripe of FFT i instead of 1:
+ * maps, profiles, candidate counts and n_thr are in units of 2^-F, and the
+ * critical ratio becomes (n - S1 p0) / sqrt((S2 p0)(1 - p0)), S1 and S2 the
+ * direction's sums of W and of W^2 (for unit weights S1 = S2 = N: Eq. cr).
+ * Errors: FH_ERR_INVALID_ARG (bad weight, wrong n_dir, no peakmap),
+ * FH_ERR_RANGE (a weight or a direction's sum reaching 2^30). */
+int fh_set_weights(fh_plan plan, const double *w, int32_t n_dir, int32_t frac_bits,
+                   void *stream);
+
 /* Copy the profile of directions [dir_begin, dir_begin + n_dir) into
  * out (device, n_dir x n_f0 uint64): key = (count << 32) | (0xFFFFFFFF - row). */
 int fh_copy_profile(fh_plan plan, int32_t dir_begin, int32_t n_dir, uint64_t *out,

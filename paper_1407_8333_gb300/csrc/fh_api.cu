@@ -193,6 +193,12 @@ struct fh_plan_s {
     int32_t n_dir = 0;
     int64_t launches = 0;
     size_t prepared_smem[3] = {0, 0, 0};
+    // adaptive weights (Eq. ncountadap), set by fh_set_weights until the next
+    // fh_correct_doppler: W [max_dir][max_fft] and per-direction sums S1, S2
+    int32_t *wq = nullptr;
+    int64_t *ws = nullptr;       // [2][max_dir]: S1 then S2
+    bool weighted = false;
+    int64_t w_bound = 0;         // 2 max S1: no weighted count exceeds it
     // optional kernel timing: per direction group of fh_transform, events before
     // the window pre-pass, between it and the transform, after the transform
     int32_t timing = 0;
@@ -203,7 +209,7 @@ struct fh_plan_s {
     {
         for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
         tev.clear();
-        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, dmax, win};
+        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, dmax, win, wq, ws};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -215,6 +221,8 @@ struct fh_plan_s {
         dmax = nullptr;
         win = nullptr;
         win_bytes = 0;
+        wq = nullptr;
+        ws = nullptr;
     }
 };
 
@@ -438,6 +446,75 @@ int fh_destroy_plan(fh_plan p)
 
 int64_t fh_plan_launches(fh_plan p) { return p ? p->launches : -1; }
 
+int fh_set_weights(fh_plan p, const double *w, int32_t n_dir, int32_t frac_bits, void *stream)
+{
+    if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
+    if (p->n_fft < 0)
+        return set_error(FH_ERR_INVALID_ARG, "fh_correct_doppler has not been called on this plan");
+    if (!w) {
+        p->weighted = false;
+        return FH_OK;
+    }
+    if (n_dir != p->n_dir)
+        return set_error(FH_ERR_INVALID_ARG, "weights for %d directions, the plan holds %d", n_dir,
+                         p->n_dir);
+    if (frac_bits < 0 || frac_bits > 24)
+        return set_error(FH_ERR_INVALID_ARG, "frac_bits must be in [0, 24]");
+    const int32_t n = p->n_fft;
+    const fh_plan_desc &d = p->d;
+    // quantise on the host: W = rint(w 2^F) (binary64, ties to even; the product
+    // by a power of two is exact), every weight finite and >= 0, and each
+    // direction's sum below 2^30 (a cell takes at most two stripes of one FFT,
+    // so every count stays inside int32)
+    const double scale = std::ldexp(1.0, frac_bits);
+    std::vector<int32_t> W((size_t)n_dir * (size_t)std::max(1, n));
+    std::vector<int64_t> sums(2 * (size_t)d.max_dir, 0);
+    int64_t smax = 0;
+    for (int32_t k = 0; k < n_dir; ++k) {
+        int64_t s1 = 0, s2 = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const double x = w[(int64_t)k * n + i];
+            if (!(std::isfinite(x) && x >= 0.0))
+                return set_error(FH_ERR_INVALID_ARG, "weight [%d][%d] must be finite and >= 0", k,
+                                 i);
+            const double q = std::nearbyint(x * scale);
+            if (!(q < 1073741824.0))
+                return set_error(FH_ERR_RANGE, "weight [%d][%d] is 2^30 or more after scaling", k,
+                                 i);
+            const int64_t qi = (int64_t)q;
+            s1 += qi;
+            if (s1 >= ((int64_t)1 << 30))
+                return set_error(FH_ERR_RANGE, "direction %d: weights sum to 2^30 or more", k);
+            s2 += qi * qi;
+            W[(size_t)k * n + i] = (int32_t)qi;
+        }
+        sums[k] = s1;
+        sums[d.max_dir + k] = s2;
+        smax = std::max(smax, s1);
+    }
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaSuccess;
+    if (!p->wq) {
+        e = cudaMalloc(&p->wq, sizeof(int32_t) * (size_t)d.max_dir * (size_t)std::max(1, d.max_fft));
+        if (e == cudaSuccess) e = cudaMalloc(&p->ws, sizeof(int64_t) * 2 * (size_t)d.max_dir);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FH_ERR_NOMEM, "cudaMalloc (weights) failed");
+        }
+    }
+    cudaStream_t s = as_stream(stream);
+    // pageable sources: each copy has taken its data when it returns
+    if (n > 0)
+        e = cudaMemcpyAsync(p->wq, W.data(), sizeof(int32_t) * W.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->ws, sums.data(), sizeof(int64_t) * sums.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(weights)");
+    p->weighted = true;
+    p->w_bound = 2 * smax;
+    return FH_OK;
+}
+
 int fh_plan_set_timing(fh_plan p, int32_t on)
 {
     if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
@@ -504,6 +581,7 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     const int32_t n = pm->n_fft;
     const int64_t np = pm->n_peaks;
     const double *t_src, *f_src, *v_src, *sky_src;
+    p->weighted = false;  // a new peakmap starts with unit weights
     cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->dmax, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
@@ -601,6 +679,8 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.profile = p->profile;
     job.dmax = p->dmax;
     job.err = p->err;
+    job.weights = p->weighted ? p->wq : nullptr;
+    job.count_bound = p->weighted ? p->w_bound : p->n_peaks;
     job.n_peaks = p->n_peaks;
     job.n_fft = p->n_fft;
     job.n_f0 = d.n_f0;
@@ -737,6 +817,8 @@ int fh_select_candidates(fh_plan p, int32_t dir_begin, int32_t n_dir, fh_candida
     a.fdot_min = d.fdot_min;
     a.fdot_step = d.fdot_step;
     a.p0 = d.p0;
+    a.s1 = p->weighted ? p->ws : nullptr;
+    a.s2 = p->weighted ? p->ws + d.max_dir : nullptr;
     cudaError_t e = launch_select(a, s);
     if (e != cudaSuccess) return cuda_error(e, "select launch");
     ++p->launches;

@@ -33,6 +33,9 @@ struct TransformJob {
     const int32_t *err;      // the job's device error word: the unclamped walk, which
                              // trusts the peak windows (sorted positions), runs only
                              // while it is 0
+    const int32_t *weights;  // nullable (plain map): adaptive integer weights, [dir][n_fft]
+                             // (absolute directions); each update adds its FFT's weight
+    int64_t count_bound;     // no count of the job's maps exceeds it
     const int2 *windows;     // nullable: precomputed peak windows (first, end) per
                              // [dir - dir_begin][slab][tile][fft]; else looked up
     int64_t n_peaks;
@@ -55,6 +58,8 @@ struct SelectArgs {
     int32_t n_f0, subband_cells, top_k, excl, sep, n_thr, n_sb;
     int32_t dir_begin, n_dir, n_fft;
     double f0_min, kt, fdot_min, fdot_step, p0;
+    const int64_t *s1, *s2;  // nullable (plain map): per absolute direction, sums of the
+                             // adaptive weights and of their squares
 };
 
 // ---- launchers (fh_kernels.cu); all return cudaGetLastError() ----

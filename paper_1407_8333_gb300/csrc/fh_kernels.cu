@@ -541,7 +541,27 @@ __host__ __device__ constexpr int ctz5(int x)
     return (x & 1) ? 0 : (x & 2) ? 1 : (x & 4) ? 2 : (x & 8) ? 3 : 4;
 }
 
-// Step T of one peak's 32 row updates.  The lane visits row lane ^ g(T),
+// DIFF mode (+1 at the first covered cell of the tile, -1 after the stripe)
+// always clamps: the differential form itself cuts stripes at the tile edges.
+template <int T>
+__device__ __forceinline__ void diff_step(int32_t *H0, int lane, int64_t &X, const int64_t (&e)[5],
+                                          int E, int Wt, int K, int32_t w)
+{
+    constexpr int gt = T ^ (T >> 1);
+    const int row = lane ^ gt;
+    const int L = (int)(X >> 32);
+    const bool in = (unsigned)L < (unsigned)E;
+    const int st = in ? max(L - K + 1, 0) : E;
+    const int en = (in && L + 1 < Wt) ? L + 1 : E;
+    atomicAdd(&H0[st * kRows + row], w);
+    atomicAdd(&H0[en * kRows + row], -w);
+    if constexpr (T < 31) {
+        constexpr int b = ctz5(T + 1);
+        if constexpr ((gt >> b) & 1) X -= e[b]; else X += e[b];
+    }
+}
+
+// Step T of a peak's 32 row updates.  The lane visits row lane ^ g(T),
 // g(T) = T ^ (T >> 1) (a Gray code; T, g(T), the bit b that flips next and its
 // sign are compile-time constants): for every step the 32 lanes of a warp
 // visit 32 different rows, i.e. 32 different banks of the [cell][row]
@@ -554,55 +574,13 @@ __host__ __device__ constexpr int ctz5(int x)
 // CLAMP = false: the caller guarantees every cell of the 32 rows lies inside
 // the guard cells around the tile, so the atomic needs no bounds clamp.
 // CLAMP = true: cells outside [0, E) go to the dump cell E (never read).
-template <bool CLAMP, int T>
-__device__ __forceinline__ void start_step(uint32_t rbase, int64_t &X, const int64_t (&e)[5],
-                                           uint32_t stride, uint32_t E)
-{
-    constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
-    const uint32_t rb = rbase ^ (gt << 2);
-    uint32_t cell = cell_of(X);
-    if (CLAMP) cell = min(cell, E);
-    const uint32_t addr = cell * stride + rb;
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
-    if constexpr (T < 31) {
-        constexpr int b = ctz5(T + 1);
-        if constexpr ((gt >> b) & 1) X -= e[b]; else X += e[b];
-    }
-}
-
-// DIFF mode (+1 at the first covered cell of the tile, -1 after the stripe)
-// always clamps: the differential form itself cuts stripes at the tile edges.
-template <int T>
-__device__ __forceinline__ void diff_step(int32_t *H0, int lane, int64_t &X, const int64_t (&e)[5],
-                                          int E, int Wt, int K)
-{
-    constexpr int gt = T ^ (T >> 1);
-    const int row = lane ^ gt;
-    const int L = (int)(X >> 32);
-    const bool in = (unsigned)L < (unsigned)E;
-    const int st = in ? max(L - K + 1, 0) : E;
-    const int en = (in && L + 1 < Wt) ? L + 1 : E;
-    atomicAdd(&H0[st * kRows + row], 1);
-    atomicAdd(&H0[en * kRows + row], -1);
-    if constexpr (T < 31) {
-        constexpr int b = ctz5(T + 1);
-        if constexpr ((gt >> b) & 1) X -= e[b]; else X += e[b];
-    }
-}
-
-template <bool CLAMP, int... Ts>
-__device__ __forceinline__ void start_steps(std::integer_sequence<int, Ts...>, uint32_t rbase,
-                                            int64_t X, const int64_t (&e)[5], uint32_t stride,
-                                            uint32_t E)
-{
-    (start_step<CLAMP, Ts>(rbase, X, e, stride, E), ...);
-}
-
-// Two peaks of one FFT per lane: they share the row walk, hence the step
-// table e and each step's row offset; CLAMP as in start_step.
+// Two peaks of one FFT per lane share the row walk, hence the step table e and
+// each step's row offset.  Each update adds w, the FFT's weight (1 for the
+// plain map; Eq. ncountadap for the adaptive one).
 template <bool CLAMP, int T>
 __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &X2,
-                                          const int64_t (&e)[5], uint32_t stride, uint32_t E)
+                                          const int64_t (&e)[5], uint32_t stride, uint32_t E,
+                                          uint32_t w)
 {
     constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
     const uint32_t rb = rbase ^ (gt << 2);
@@ -614,8 +592,8 @@ __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &
     }
     const uint32_t a1 = c1 * stride + rb;
     const uint32_t a2 = c2 * stride + rb;
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a1) : "memory");
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a2) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a1), "r"(w) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a2), "r"(w) : "memory");
     if constexpr (T < 31) {
         constexpr int b = ctz5(T + 1);
         if constexpr ((gt >> b) & 1) {
@@ -631,16 +609,17 @@ __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &
 template <bool CLAMP, int... Ts>
 __device__ __forceinline__ void pair_steps(std::integer_sequence<int, Ts...>, uint32_t rbase,
                                            int64_t X1, int64_t X2, const int64_t (&e)[5],
-                                           uint32_t stride, uint32_t E)
+                                           uint32_t stride, uint32_t E, uint32_t w)
 {
-    (pair_step<CLAMP, Ts>(rbase, X1, X2, e, stride, E), ...);
+    (pair_step<CLAMP, Ts>(rbase, X1, X2, e, stride, E, w), ...);
 }
 
 template <int... Ts>
 __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, int32_t *H0, int lane,
-                                           int64_t X, const int64_t (&e)[5], int E, int Wt, int K)
+                                           int64_t X, const int64_t (&e)[5], int E, int Wt, int K,
+                                           int32_t w)
 {
-    (diff_step<Ts>(H0, lane, X, e, E, Wt, K), ...);
+    (diff_step<Ts>(H0, lane, X, e, E, Wt, K, w), ...);
 }
 
 // One block per work item (direction, slab of 32 spin-down rows, tile of W
@@ -658,7 +637,7 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // round's start bits); START mode puts two peaks of one FFT in a slot.  The
 // next round's positions are loaded while the current round is added, and
 // every lane adds its peaks' 32 row updates along the Gray-code row order
-// (start_step / pair_step / diff_step), so the 32 atomics of one warp
+// (pair_step / diff_step), so the 32 atomics of one warp
 // instruction always go to 32 different banks.
 //
 // Emit: warps take 16-cell groups along f0 (START, packed counts) or segments
@@ -730,6 +709,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             J->windows ? J->windows + (((int64_t)d_rel * J->n_slabs + slab) * J->n_tiles + tile) *
                                           n_fft
                        : nullptr;
+        const int32_t *__restrict__ wts =
+            J->weights ? J->weights + (int64_t)d_abs * n_fft : nullptr;
         const bool row_ok = lane < R;
         const bool fast = MODE == FH_MODE_START && ((job_fast >> jb) & 1u);
 
@@ -751,6 +732,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         for (int c = warp; c < nchunks;) {
             int64_t cb, dv, q0;
             int n;
+            // the FFT's weight on this direction (adaptive map), 1 for the plain map
+            int32_t wt = 1;
+            if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
             if (wrow != nullptr) {
                 // precomputed window: one coalesced load, clamped into the FFT's CSR range
                 const int i = (c << 5) + lane;
@@ -830,7 +814,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             // [min(0, (R-1) D), max(0, (R-1) D) + E 2^32) (to one cell), and
             // |31 D| stays below guard - 2 cells.
             auto setup = [&](int g, int64_t a1, int64_t a2, bool two, int owner, int64_t &X1,
-                             int64_t &X2, int64_t (&e)[5]) {
+                             int64_t &X2, int64_t (&e)[5], int32_t &ow) {
+                ow = __shfl_sync(kFull, wt, owner);
                 const int64_t ocb = __shfl_sync(kFull, cb, owner);
                 const int64_t odv0 = __shfl_sync(kFull, dv, owner);
                 const bool live = g < T;
@@ -860,16 +845,17 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 const int owner = own_nx;
                 if (base + 32 < T) fetch(base + 32, a1_nx, a2_nx, two_nx, own_nx);
                 int64_t X1, X2 = 0, e[5];
-                setup(base + lane, a1, a2, two, owner, X1, X2, e);
+                int32_t ow;
+                setup(base + lane, a1, a2, two, owner, X1, X2, e, ow);
                 if (MODE == FH_MODE_START) {
                     if (fast)
                         pair_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e,
-                                          cell_stride, (uint32_t)E);
+                                          cell_stride, (uint32_t)E, (uint32_t)ow);
                     else
                         pair_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e,
-                                         cell_stride, (uint32_t)E);
+                                         cell_stride, (uint32_t)E, (uint32_t)ow);
                 } else if (base + lane < T) {
-                    diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X1, e, E, Wt, K);
+                    diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X1, e, E, Wt, K, ow);
                 }
             }
             __syncwarp();
@@ -889,7 +875,7 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         // on ties.  Counts below 2^26 fit one packed signed reduction
         // 32 count + (31 - lane); rows beyond the slab start their window at
         // -2^26, so they stay negative and never win.
-        const bool packed = J->n_peaks < (int64_t(1) << 26);
+        const bool packed = J->count_bound < (int64_t(1) << 26);
         const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 31u;
         auto key_of = [&](int v) {
             return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
@@ -1083,8 +1069,17 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectArgs a)
             }
         }
     }
-    const double np0 = __dmul_rn((double)a.n_fft, a.p0);
-    const double sd = __dsqrt_rn(__dmul_rn(np0, __dsub_rn(1.0, a.p0)));
+    // CR (Eq. cr); adaptive map: mean S1 p0 and variance (S2 p0)(1 - p0) of the
+    // weighted noise count, S1 / S2 = the direction's sums of W and W^2 (unit
+    // weights give Eq. cr operation for operation)
+    double np0, sd;
+    if (a.s1 != nullptr) {
+        np0 = __dmul_rn((double)a.s1[d_abs], a.p0);
+        sd = __dsqrt_rn(__dmul_rn(__dmul_rn((double)a.s2[d_abs], a.p0), __dsub_rn(1.0, a.p0)));
+    } else {
+        np0 = __dmul_rn((double)a.n_fft, a.p0);
+        sd = __dsqrt_rn(__dmul_rn(np0, __dsub_rn(1.0, a.p0)));
+    }
     for (int k = threadIdx.x; k < a.top_k; k += blockDim.x) {
         fh_candidate c;
         c.dir = d_abs;

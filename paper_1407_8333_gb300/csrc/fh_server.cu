@@ -250,6 +250,8 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.maps = nullptr;
             t.dmax = j->d_dmax;
             t.err = j->d_err;
+            t.weights = nullptr;  // served jobs use the plain map
+            t.count_bound = j->n_peaks;
             t.n_peaks = j->n_peaks;
             t.n_fft = j->n_fft;
             t.n_f0 = j->d.n_f0;

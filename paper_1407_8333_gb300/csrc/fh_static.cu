@@ -169,6 +169,8 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     job.windows = nullptr;  // no window table in the fixed scratch: binary search
     job.dmax = dmax;
     job.err = err;
+    job.weights = nullptr;
+    job.count_bound = np;
     job.n_peaks = np;
     job.item_begin = 0;
     job.n_fft = n;

@@ -93,6 +93,7 @@ _SIGS = {
     "fh_sync": ([_P, _P], ctypes.c_int),
     "fh_autotune": ([_P, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P], ctypes.c_int),
     "fh_plan_launches": ([_P], _i64),
+    "fh_set_weights": ([_P, _P, _i32, _i32, _P], ctypes.c_int),
     "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
     "fh_plan_kernel_times": ([_P, ctypes.POINTER(_i64), ctypes.POINTER(_f64), ctypes.POINTER(_f64)],
                              ctypes.c_int),
@@ -278,6 +279,18 @@ def fh_autotune(plan, dir_begin: int, n_dir: int, stream=None) -> tuple:
 
 def fh_plan_launches(plan) -> int:
     return int(load().fh_plan_launches(plan))
+
+
+def fh_set_weights(plan, w, frac_bits: int = 0, stream=None) -> None:
+    """Adaptive weights (n_dir x n_fft host reals, or None for the plain map)."""
+    if w is None:
+        _check(load().fh_set_weights(plan, None, 0, 0, _stream(stream)), "fh_set_weights")
+        return
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if w.ndim != 2:
+        raise ValueError("weights must be n_dir x n_fft")
+    _check(load().fh_set_weights(plan, w.ctypes.data_as(_P), int(w.shape[0]), int(frac_bits),
+                                 _stream(stream)), "fh_set_weights")
 
 
 def fh_plan_set_timing(plan, on: bool = True) -> None:
