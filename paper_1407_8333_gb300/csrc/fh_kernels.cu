@@ -577,7 +577,7 @@ __device__ __forceinline__ void diff_step(int32_t *H0, int lane, int64_t &X, con
 // Two peaks of one FFT per lane share the row walk, hence the step table e and
 // each step's row offset.  Each update adds w, the FFT's weight (1 for the
 // plain map; Eq. ncountadap for the adaptive one).
-template <bool CLAMP, int T>
+template <bool CLAMP, bool WEIGHTED, int T>
 __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &X2,
                                           const int64_t (&e)[5], uint32_t stride, uint32_t E,
                                           uint32_t w)
@@ -592,8 +592,13 @@ __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &
     }
     const uint32_t a1 = c1 * stride + rb;
     const uint32_t a2 = c2 * stride + rb;
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a1), "r"(w) : "memory");
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a2), "r"(w) : "memory");
+    if constexpr (WEIGHTED) {
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a1), "r"(w) : "memory");
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a2), "r"(w) : "memory");
+    } else {
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a1) : "memory");
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a2) : "memory");
+    }
     if constexpr (T < 31) {
         constexpr int b = ctz5(T + 1);
         if constexpr ((gt >> b) & 1) {
@@ -606,12 +611,12 @@ __device__ __forceinline__ void pair_step(uint32_t rbase, int64_t &X1, int64_t &
     }
 }
 
-template <bool CLAMP, int... Ts>
+template <bool CLAMP, bool WEIGHTED, int... Ts>
 __device__ __forceinline__ void pair_steps(std::integer_sequence<int, Ts...>, uint32_t rbase,
                                            int64_t X1, int64_t X2, const int64_t (&e)[5],
                                            uint32_t stride, uint32_t E, uint32_t w)
 {
-    (pair_step<CLAMP, Ts>(rbase, X1, X2, e, stride, E, w), ...);
+    (pair_step<CLAMP, WEIGHTED, Ts>(rbase, X1, X2, e, stride, E, w), ...);
 }
 
 template <int... Ts>
@@ -646,7 +651,7 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // as carry-in.  The count goes to the map (optional) and the warp's max over
 // rows (smallest row on ties) to the direction's profile by a 64-bit
 // atomicMax, which is order-independent.
-template <int MODE, int MAXT>
+template <int MODE, int MAXT, bool WEIGHTED>
 __global__ void __launch_bounds__(MAXT, 1)
 transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words,
                  int32_t guard, uint32_t cell_stride)
@@ -734,7 +739,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             int n;
             // the FFT's weight on this direction (adaptive map), 1 for the plain map
             int32_t wt = 1;
-            if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
+            if constexpr (WEIGHTED)
+                if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
             if (wrow != nullptr) {
                 // precomputed window: one coalesced load, clamped into the FFT's CSR range
                 const int i = (c << 5) + lane;
@@ -815,7 +821,10 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             // |31 D| stays below guard - 2 cells.
             auto setup = [&](int g, int64_t a1, int64_t a2, bool two, int owner, int64_t &X1,
                              int64_t &X2, int64_t (&e)[5], int32_t &ow) {
-                ow = __shfl_sync(kFull, wt, owner);
+                if constexpr (WEIGHTED)
+                    ow = __shfl_sync(kFull, wt, owner);
+                else
+                    ow = 1;
                 const int64_t ocb = __shfl_sync(kFull, cb, owner);
                 const int64_t odv0 = __shfl_sync(kFull, dv, owner);
                 const bool live = g < T;
@@ -849,11 +858,11 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 setup(base + lane, a1, a2, two, owner, X1, X2, e, ow);
                 if (MODE == FH_MODE_START) {
                     if (fast)
-                        pair_steps<false>(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e,
-                                          cell_stride, (uint32_t)E, (uint32_t)ow);
+                        pair_steps<false, WEIGHTED>(std::make_integer_sequence<int, 32>{}, rbase, X1,
+                                                    X2, e, cell_stride, (uint32_t)E, (uint32_t)ow);
                     else
-                        pair_steps<true>(std::make_integer_sequence<int, 32>{}, rbase, X1, X2, e,
-                                         cell_stride, (uint32_t)E, (uint32_t)ow);
+                        pair_steps<true, WEIGHTED>(std::make_integer_sequence<int, 32>{}, rbase, X1,
+                                                   X2, e, cell_stride, (uint32_t)E, (uint32_t)ow);
                 } else if (base + lane < T) {
                     diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X1, e, E, Wt, K, ow);
                 }
@@ -1217,33 +1226,44 @@ size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, in
 // Kernel instantiation for a counting mode and block size: blocks of up to 512
 // threads get up to 128 registers per thread, of up to 768 threads (START
 // mode) 80, of 1024 threads 64.
-template <typename F>
-static auto with_transform_kernel(int32_t mode, int32_t nwarps, F &&f)
+template <bool WEIGHTED, typename F>
+static auto with_transform_kernel_w(int32_t mode, int32_t nwarps, F &&f)
 {
     if (mode == FH_MODE_DIFF)
-        return nwarps > 16 ? f(transform_kernel<FH_MODE_DIFF, 1024>)
-                           : f(transform_kernel<FH_MODE_DIFF, 512>);
-    return nwarps > 24   ? f(transform_kernel<FH_MODE_START, 1024>)
-           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 768>)
-                         : f(transform_kernel<FH_MODE_START, 512>);
+        return nwarps > 16 ? f(transform_kernel<FH_MODE_DIFF, 1024, WEIGHTED>)
+                           : f(transform_kernel<FH_MODE_DIFF, 512, WEIGHTED>);
+    return nwarps > 24   ? f(transform_kernel<FH_MODE_START, 1024, WEIGHTED>)
+           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 768, WEIGHTED>)
+                         : f(transform_kernel<FH_MODE_START, 512, WEIGHTED>);
+}
+// weighted: instantiation that adds per-FFT weights (adaptive map); plain: +1
+template <typename F>
+static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, F &&f)
+{
+    return weighted ? with_transform_kernel_w<true>(mode, nwarps, f)
+                    : with_transform_kernel_w<false>(mode, nwarps, f);
 }
 
 cudaError_t transform_prepare(int32_t mode, size_t smem)
 {
     cudaError_t e = cudaSuccess;
-    for (int nw : {16, 24, 32}) {
-        const cudaError_t r = with_transform_kernel(mode, nw, [&](auto k) {
-            return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        });
-        if (r != cudaSuccess) e = r;
-    }
+    for (int nw : {16, 24, 32})
+        for (bool wt : {false, true}) {
+            const cudaError_t r = with_transform_kernel(mode, nw, wt, [&](auto k) {
+                return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem);
+            });
+            if (r != cudaSuccess) e = r;
+        }
     return e;
 }
 
 int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem)
 {
     int n = 0;
-    const cudaError_t e = with_transform_kernel(mode, nwarps, [&](auto k) {
+    // (both instantiations are bounded to one block of nwarps warps per SM by
+    // their launch bounds; shared memory decides the rest)
+    const cudaError_t e = with_transform_kernel(mode, nwarps, false, [&](auto k) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, nwarps * 32, smem);
     });
     return e == cudaSuccess ? n : 0;
@@ -1260,7 +1280,9 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
         const int32_t w = (tbl.job[j].tile_cells + tbl.job[j].k_over + 2 * guard) * kRows;
         hist_words = w > hist_words ? w : hist_words;
     }
-    with_transform_kernel(mode, nwarps, [&](auto k) {
+    bool weighted = false;
+    for (int j = 0; j < tbl.n_jobs; ++j) weighted = weighted || tbl.job[j].weights != nullptr;
+    with_transform_kernel(mode, nwarps, weighted, [&](auto k) {
         k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u);
         return cudaSuccess;
     });
