@@ -321,6 +321,7 @@ def run_ours(args):
     fh.fh_destroy_plan(plan)
 
     if rank == 0 and world == 1 and not args.no_extras:
+        out["adaptive"] = adaptive_leg(fh, inp, pp, dev, cand, flush, torch, args.steps)
         out["batched_vs_plain"] = batched_vs_plain(fh, synth, torch)
         try:
             out["serving"] = serving_leg(fh, synth, torch, args.serve_seconds)
@@ -331,6 +332,44 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def adaptive_leg(fh, inp, pp, dev, cand, flush, torch, steps):
+    """The same workload as the adaptive map (Eq. ncountadap): weights with a
+    sidereal-day modulation, 12 fraction bits, set after every correction (a
+    new peakmap returns the plan to unit weights)."""
+    import numpy as np
+    n = inp.t.shape[0]
+    w = (1.0 + 0.5 * np.cos(2 * np.pi * inp.t / 86164.09)).reshape(1, n)
+    plan = fh.fh_create_plan(fh.make_desc(pp, n, 1, inp.n_peaks))
+    try:
+        fh.fh_correct_doppler(plan, *dev)
+        fh.fh_autotune(plan, 0, 1)
+        ts, kern = [], []
+        fh.fh_plan_set_timing(plan, True)
+        for k in range(3 + steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fh.fh_correct_doppler(plan, *dev)
+            fh.fh_set_weights(plan, w, 12)
+            fh.fh_transform(plan, 0, 1, None)
+            fh.fh_select_candidates(plan, 0, 1, cand)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(e0.elapsed_time(e1))
+            if k == 2:
+                fh.fh_plan_set_timing(plan, True)
+        n_g, _, kms = fh.fh_plan_kernel_times(plan)
+    finally:
+        fh.fh_destroy_plan(plan)
+    upd = inp.n_peaks * pp["n_fdot"]
+    ms = statistics.mean(ts)
+    return {"weights": "1 + 0.5 cos(2 pi t / sidereal day), 12 fraction bits",
+            "ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3),
+            "transform_kernel_ms": kms / n_g}
 
 
 def batched_vs_plain(fh, synth, torch):
