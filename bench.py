@@ -178,7 +178,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_1407_8333_gb300 import build, fh, synth
+    from paper_1407_8333_gb300 import build, fh, replicas, synth
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -230,7 +230,7 @@ def run_ours(args):
     fh.fh_plan_set_timing(plan, True)
     l0 = fh.fh_plan_launches(plan)
     if world > 1:
-        torch.distributed.barrier()
+        replicas.barrier()
     torch.cuda.synchronize()
     nvtx.range_push("timed")
     for k in range(args.steps):
@@ -239,7 +239,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     nvtx.range_pop()
     if world > 1:
-        torch.distributed.barrier()
+        replicas.barrier()
     launches = fh.fh_plan_launches(plan) - l0
     clocks = sampler.stop()
     n_groups, win_ms_sum, kern_ms_sum = fh.fh_plan_kernel_times(plan)
@@ -250,11 +250,8 @@ def run_ours(args):
     tr_ms = [e[1].elapsed_time(e[2]) for e in evs]
     dop_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sel_ms = [e[2].elapsed_time(e[3]) for e in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # the slowest replica's time (replicas: no data-path collective)
+    total_ms = replicas.max_over_ranks(sum(step_ms))
     value = upd_step * args.steps * world / (total_ms * 1e-3)
 
     # roofline of the transform kernel (dominant): shared-memory atomics, one per
