@@ -433,7 +433,7 @@ __device__ __forceinline__ int step_down(const int32_t *a, int q, int x)
     return q;
 }
 
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(512, 3)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
     __shared__ int32_t cell_s[8][kWinPeaks];
