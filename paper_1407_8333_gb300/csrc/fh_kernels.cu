@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(512, 3)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
     __shared__ int32_t cell_s[8][kWinPeaks];
-    __shared__ int2 stage[8][kWinPitch];
+    __shared__ int2 stage[2][8][kWinPitch];  // double buffer: one barrier per slab
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int f = warp & 7, half = warp >> 3;  // FFT of the block, tile half
     const int i = blockIdx.x * 8 + f;
@@ -515,15 +515,17 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
                     qa = step_down(cs, qa, xl);
                     qb = step_down(cs, qb, xh);
                 }
-                stage[f][tt] = make_int2((int)(o0 + qa), (int)(o0 + max(qa, qb)));
+                stage[slab & 1][f][tt] = make_int2((int)(o0 + qa), (int)(o0 + max(qa, qb)));
             }
             u += 32 * dv;
             w += 32 * dv;
+            // this slab's entries are complete; the buffer is written again two
+            // slabs later, after the next barrier
             __syncthreads();
-            if (dst_ok) *dst = stage[threadIdx.x & 7][est];
+            if (dst_ok) *dst = stage[slab & 1][threadIdx.x & 7][est];
             dst += slab_stride;
-            __syncthreads();
         }
+        __syncthreads();  // the next pass of tiles reuses both buffers
     }
 }
 
