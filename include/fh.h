@@ -135,10 +135,12 @@ typedef struct {
     int32_t rank;     /* 0 .. top_k - 1 within the sub-band                       */
     int32_t row;      /* spin-down row j                                          */
     int32_t cell;     /* frequency cell b                                         */
-    int32_t count;    /* number count n (Eq. ncount)                              */
+    int32_t count;    /* number count n (Eq. ncount; weighted, in units of 2^-F,
+                         after fh_set_weights)                                   */
     double f0;        /* f0_min + (b + 0.5) / KT [Hz], cell centre                */
     double fdot;      /* fdot_min + j * fdot_step [Hz/s]                          */
-    double cr;        /* (n - N p0) / sqrt(N p0 (1 - p0)), N = n_fft (Eq. cr)    */
+    double cr;        /* (n - N p0) / sqrt(N p0 (1 - p0)), N = n_fft (Eq. cr);
+                         adaptive map: see fh_set_weights                        */
 } fh_candidate;
 
 /* ---- plan -------------------------------------------------------------- */
@@ -198,8 +200,10 @@ int fh_transform(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *out_ma
  * maps, profiles, candidate counts and n_thr are in units of 2^-F, and the
  * critical ratio becomes (n - S1 p0) / sqrt((S2 p0)(1 - p0)), S1 and S2 the
  * direction's sums of W and of W^2 (for unit weights S1 = S2 = N: Eq. cr).
- * Errors: FH_ERR_INVALID_ARG (bad weight, wrong n_dir, no peakmap),
- * FH_ERR_RANGE (a weight or a direction's sum reaching 2^30). */
+ * The weights are checked and quantised on the host and their copy to the
+ * device is enqueued on stream.  Errors: FH_ERR_INVALID_ARG (bad weight,
+ * wrong n_dir, no peakmap), FH_ERR_RANGE (a weight or a direction's sum
+ * reaching 2^30). */
 int fh_set_weights(fh_plan plan, const double *w, int32_t n_dir, int32_t frac_bits,
                    void *stream);
 
@@ -293,8 +297,9 @@ enum { FH_JOB_QUEUED = 0, FH_JOB_RUNNING = 1, FH_JOB_DONE = 2, FH_JOB_FAILED = 3
        FH_JOB_CANCELLED = 4 };
 
 /* One Hough job: a band x T_FFT x sky patch (configuration 4 of the paper's
- * workload mix).  All arrays are host memory; fh_submit copies them before it
- * returns, so the caller may free them at once. */
+ * workload mix), searched with the plain map.  All arrays are host memory;
+ * fh_submit copies them before it returns, so the caller may free them at
+ * once. */
 typedef struct {
     fh_plan_desc plan;      /* grids and selection; max_* are ignored          */
     fh_peakmap peaks;       /* mem_kind must be FH_MEM_HOST                    */
