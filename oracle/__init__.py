@@ -23,6 +23,7 @@ sort-and-take-k and hand-computed cases.  Nothing here is "parity unpinned".
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -283,4 +284,64 @@ def search(inp, params: dict, want_maps: bool = False, dirs=None, weights=None,
     out.update(f0=f0, fdot=fdot, cr=cr)
     if want_maps:
         out["maps"] = np.stack(maps)
+    return out
+
+
+# ---------------------------------------------------------------- refined grid
+def refine_maps(inp, params: dict, cell: int, row: int, sky_dirs, k_fdot: int):
+    """Refined-grid FH maps around one coarse candidate (cell b_c, row j_c of
+    the coarse grid), Sec. "Refined Grid in the parameter space".
+
+    Frequency: the same K-over-resolved cells, +-1 coarse bin around the
+    candidate: cells b_c - K .. b_c + K (refined cell 0 = coarse cell b_c - K).
+    Spin-down: step fdot_step / K_fdot, 2 K_fdot rows below the coarse value and
+    2 K_fdot - 1 above (4 K_fdot rows): refined row 0 lies on coarse row
+    j_c - 2, i.e. its shift is S0_i + (j_c - 2) D_i, and a refined row step is
+    D'_i = floor((fdot_step / K_fdot) c_i 2^32).  Sky: the given refined
+    directions.  Every peak of the peakmap takes part.
+    Returns maps (n_ref, 4 K_fdot, 2 K + 1)."""
+    K = int(params["k_over"])
+    kt = float(K) * float(params["t_fft"])
+    sky_dirs = np.asarray(sky_dirs, dtype=np.float64).reshape(-1, 3)
+    S0, D = shift_tables(inp.t, params["t_ref"], kt, params["fdot_min"], params["fdot_step"])
+    _, Dr = shift_tables(inp.t, params["t_ref"], kt, 0.0,
+                         float(params["fdot_step"]) / float(k_fdot))
+    lo = int(cell) - K
+    S0r = S0 + (int(row) - 2) * D + (np.int64(lo) << np.int64(32))
+    r = doppler_factor(inp.v, sky_dirs)
+    A = positions(inp.offsets, inp.freq, r, params["f0_min"], kt, K)
+    return np.stack([hough_map(inp.offsets, A[d], S0r, Dr, K, 2 * K + 1, 4 * int(k_fdot))
+                     for d in range(sky_dirs.shape[0])])
+
+
+def refine(inp, params: dict, cells, rows, sky_ref, k_fdot: int):
+    """One refined candidate per coarse candidate (cells[c], rows[c]): the cell
+    of largest count of refine_maps over all refined directions sky_ref[c],
+    rows and cells (ties: smallest direction, then row, then cell).
+
+    Returns arrays per candidate: dir, row, cell (coarse-grid index), count,
+    f0 = f0_min + (cell + 0.5) / KT, fdot = (fdot_min + (j_c - 2) fdot_step) +
+    row (fdot_step / K_fdot) and CR (Eq. cr), binary64.
+    """
+    K = int(params["k_over"])
+    kt = float(K) * float(params["t_fft"])
+    cells = np.asarray(cells, dtype=np.int64)
+    rows = np.asarray(rows, dtype=np.int64)
+    sky_ref = np.asarray(sky_ref, dtype=np.float64)
+    n_cand = sky_ref.shape[0]
+    step_ref = float(params["fdot_step"]) / float(k_fdot)
+    out = {k: np.zeros(n_cand, dtype=np.int64) for k in ("dir", "row", "cell", "count")}
+    for k in ("f0", "fdot", "cr"):
+        out[k] = np.zeros(n_cand)
+    for c in range(n_cand):
+        maps = refine_maps(inp, params, int(cells[c]), int(rows[c]), sky_ref[c], k_fdot)
+        cnt = int(maps.max())
+        d, j, b = (int(x) for x in np.argwhere(maps == cnt)[0])   # lexicographic: dir, row, cell
+        lo = int(cells[c]) - K
+        out["dir"][c], out["row"][c], out["cell"][c], out["count"][c] = d, j, lo + b, cnt
+        out["f0"][c] = params["f0_min"] + (float(lo + b) + 0.5) / kt
+        fdot_lo = params["fdot_min"] + float(int(rows[c]) - 2) * params["fdot_step"]
+        out["fdot"][c] = fdot_lo + float(j) * step_ref
+        np0 = float(inp.t.shape[0]) * params["p0"]
+        out["cr"][c] = (float(cnt) - np0) / math.sqrt(np0 * (1.0 - params["p0"]))
     return out

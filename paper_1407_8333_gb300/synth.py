@@ -290,6 +290,30 @@ def ecliptic_grid(n_d: float) -> np.ndarray:
     return np.asarray(pts, dtype=np.float64)
 
 
+def refined_sky(n_hat, n_d: float, k_sky: int) -> np.ndarray:
+    """Refined sky directions around a coarse direction (Sec. "Refined grid in
+    the sky"): a k_sky x k_sky rectangle in ecliptic (lambda, beta) centred on
+    it, k_sky = 2 N_layers + 1 odd, whose steps are the local coarse-grid
+    spacings of ecliptic_grid divided by k_sky: beta step 1 / (N_D sin(beta)),
+    longitude step 2 pi / ceil(2 pi N_D cos(beta)).  Rows of beta, then lambda;
+    the centre (the coarse direction) is index (k_sky^2 - 1) / 2."""
+    x, y, z = (float(c) for c in np.asarray(n_hat, dtype=np.float64).reshape(3))
+    beta = math.asin(max(-1.0, min(1.0, z)))
+    lam = math.atan2(y, x)
+    db = min(1.0 / (n_d * max(abs(math.sin(beta)), 1e-3)), math.pi / 8)
+    dl = 2.0 * math.pi / max(1, int(math.ceil(2.0 * math.pi * n_d * math.cos(beta) - 1e-12)))
+    half = (int(k_sky) - 1) // 2
+    pts = []
+    for b in range(-half, half + 1):
+        bb = beta + b * db / k_sky
+        for a in range(-half, half + 1):
+            ll = lam + a * dl / k_sky
+            pts.append((math.cos(bb) * math.cos(ll), math.cos(bb) * math.sin(ll), math.sin(bb)))
+    pts = np.asarray(pts, dtype=np.float64)
+    pts[(k_sky * k_sky - 1) // 2] = (x, y, z)   # the coarse direction itself, exactly
+    return pts
+
+
 def sky_patch(w: Workload) -> np.ndarray:
     """``w.n_dir`` grid directions nearest a seeded centre, shape (n_dir, 3)."""
     if not w.doppler and w.n_dir == 1:
