@@ -262,6 +262,35 @@ int fh_plan_set_timing(fh_plan plan, int32_t on);
 int fh_plan_kernel_times(fh_plan plan, int64_t *n_groups, double *windows_ms,
                          double *transform_ms);
 
+/* ---- refined grid around coarse candidates -------------------------------- */
+
+/* Refined-grid search (Sec. "Refined Grid in the parameter space"): one
+ * refined candidate per coarse candidate (cand_cell[c], cand_row[c] of the
+ * plan's grid).  The transform runs again on the same K-over-resolved cells,
+ * +-1 coarse bin around the candidate (cells b_c - K .. b_c + K), on a
+ * spin-down step refined by k_fdot with 2 k_fdot rows below the coarse value
+ * and 2 k_fdot - 1 above (refined row 0 lies on coarse row j_c - 2: shift
+ * S0_i + (j_c - 2) D_i, refined step D'_i = floor((fdot_step / k_fdot) c_i
+ * 2^32)), and on the n_ref refined sky directions sky_ref[c] of each
+ * candidate.  The refined candidate is the largest count over all refined
+ * directions, rows and cells (ties: smallest direction, then row, then cell).
+ *   plan      the coarse grid and selection parameters (its buffers are not
+ *             used, and its peakmap is not changed)
+ *   pm, v_over_c  HOST peakmap and velocities, checked as by fh_correct_doppler
+ *   sky_ref   HOST n_cand x n_ref x 3 unit vectors
+ *   k_fdot    1 .. 64
+ *   out       HOST n_cand slots: dir = refined direction index, subband = c,
+ *             rank = 0, row = refined row, cell = cell of the plan's grid,
+ *             count, f0 = f0_min + (cell + 0.5) / KT, fdot = (fdot_min +
+ *             (j_c - 2) fdot_step) + row (fdot_step / k_fdot), cr (Eq. cr)
+ * Synchronises the stream; device memory is taken and returned stream-ordered.
+ * Errors: FH_ERR_INVALID_ARG, FH_ERR_UNSORTED, FH_ERR_RANGE, FH_ERR_CAPACITY
+ * (capacity < n_cand). */
+int fh_refine(fh_plan plan, const fh_peakmap *pm, const double *v_over_c,
+              const int32_t *cand_cell, const int32_t *cand_row, int32_t n_cand,
+              const double *sky_ref, int32_t n_ref, int32_t k_fdot, fh_candidate *out,
+              int64_t capacity, void *stream);
+
 /* ---- allocation-free search (one direction) ------------------------------ */
 
 /* fh_search_static: steps a1-a6 for ONE sky direction, like fh_correct_doppler

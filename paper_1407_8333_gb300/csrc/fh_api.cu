@@ -446,6 +446,31 @@ int fh_destroy_plan(fh_plan p)
 
 int64_t fh_plan_launches(fh_plan p) { return p ? p->launches : -1; }
 
+int fh_refine(fh_plan p, const fh_peakmap *pm, const double *v_over_c, const int32_t *cand_cell,
+              const int32_t *cand_row, int32_t n_cand, const double *sky_ref, int32_t n_ref,
+              int32_t k_fdot, fh_candidate *out, int64_t capacity, void *stream)
+{
+    if (!p || !pm || !v_over_c || (n_cand > 0 && (!cand_cell || !cand_row || !sky_ref || !out)))
+        return set_error(FH_ERR_INVALID_ARG, "null plan, peakmap, velocity or candidate array");
+    if (pm->mem_kind != FH_MEM_HOST)
+        return set_error(FH_ERR_INVALID_ARG, "fh_refine takes host-memory inputs");
+    if (n_cand < 0 || n_ref < 1 || n_ref > 65535 || k_fdot < 1 || k_fdot > 64)
+        return set_error(FH_ERR_INVALID_ARG, "need n_cand >= 0, n_ref in [1, 65535], "
+                                             "k_fdot in [1, 64]");
+    if ((int64_t)n_cand * n_ref > 1000000000)
+        return set_error(FH_ERR_INVALID_ARG, "n_cand x n_ref too large");
+    if (pm->n_fft < 0 || pm->n_peaks < 0 || !pm->offsets || (pm->n_fft > 0 && !pm->t_fft) ||
+        (pm->n_peaks > 0 && !pm->freq))
+        return set_error(FH_ERR_INVALID_ARG, "bad peakmap");
+    if (capacity < n_cand)
+        return set_error(FH_ERR_CAPACITY, "need %d refined candidate slots, capacity %lld", n_cand,
+                         (long long)capacity);
+    if (n_cand == 0) return FH_OK;
+    DeviceGuard g(p->device);
+    return refine_impl(p->d, p->n_sm, pm, v_over_c, cand_cell, cand_row, n_cand, sky_ref, n_ref,
+                       k_fdot, out, as_stream(stream));
+}
+
 int fh_set_weights(fh_plan p, const double *w, int32_t n_dir, int32_t frac_bits, void *stream)
 {
     if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");

@@ -81,6 +81,12 @@ struct PrepArgs {
     int32_t *err;
 };
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
+
+// fh_refine on the plan's grid d (host inputs, host output; synchronises)
+int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm, const double *v_over_c,
+                const int32_t *cand_cell, const int32_t *cand_row, int32_t n_cand,
+                const double *sky_ref, int32_t n_ref, int32_t k_fdot, fh_candidate *out,
+                cudaStream_t s);
 cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
                                 double fdot_min, double fdot_step, int32_t n_fdot,
                                 int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,
@@ -88,7 +94,8 @@ cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, do
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, bool validate, cudaStream_t s);
+                             double *out_r, int32_t *err, bool validate, cudaStream_t s,
+                             const int64_t *src = nullptr);
 cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
                                     int64_t *out, int32_t *err, cudaStream_t s);
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,

@@ -54,8 +54,9 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
 
 // grid (ceil(n_fft / 8), n_dir): the block computes r = 1 / (1 + v.n) for 8
 // FFTs of one direction, then the fixed-point position of each of their peaks
-// (a contiguous CSR range, so loads and stores are coalesced).  With
-// `validate`, the blocks of
+// (a contiguous CSR range, so loads and stores are coalesced).  With `src`,
+// FFT i's peaks are read from freq[src[i] ...] (a sub-range of a larger
+// peakmap) and written compactly by `offsets`.  With `validate`, the blocks of
 // direction 0 also flag frequencies that are not finite and positive
 // (kErrInvalid) or not strictly increasing within their FFT (kErrUnsorted).
 __global__ void __launch_bounds__(kPosThreads)
@@ -63,10 +64,11 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
                  int64_t n_peaks, double f0_min, double kt, double cshift,
                  int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
-                 int32_t validate)
+                 int32_t validate, const int64_t *__restrict__ src)
 {
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
+    __shared__ int64_t src_s[kPosFfts];  // where each FFT's peaks start in freq
     const int d = blockIdx.y;
     const int i0 = blockIdx.x * kPosFfts;
     const int nf = min(kPosFfts, n_fft - i0);
@@ -82,6 +84,8 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
         if (out_r) out_r[(int64_t)d * n_fft + i] = r;
     }
     if (threadIdx.x <= nf) off_s[threadIdx.x] = offsets[i0 + threadIdx.x];
+    if (threadIdx.x < nf)
+        src_s[threadIdx.x] = src ? src[i0 + threadIdx.x] : offsets[i0 + threadIdx.x];
     __syncthreads();
     const int64_t p_begin = off_s[0], p_end = off_s[nf];
     int64_t *__restrict__ Ad = A + (int64_t)d * n_peaks;
@@ -98,12 +102,13 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
             const int m = (lo + hi) >> 1;
             if (off_s[m] <= p) lo = m; else hi = m;
         }
-        const double f = in ? freq[p] : 1.0;
+        const int64_t fp = src_s[lo] + (p - off_s[lo]);
+        const double f = in ? freq[fp] : 1.0;
         if (check) {
             // positive finite doubles order like their bit patterns
             const int64_t fb = __double_as_longlong(f);
             int64_t prev = __shfl_up_sync(kFull, fb, 1);
-            if (lane == 0 && in && p > p_begin) prev = __double_as_longlong(freq[p - 1]);
+            if (lane == 0 && in && p > p_begin) prev = __double_as_longlong(freq[fp - 1]);
             if (in) {
                 if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
                 if (p > off_s[lo] && !(fb > prev)) ev |= kErrUnsorted;
@@ -1176,13 +1181,15 @@ cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s)
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, bool validate, cudaStream_t s)
+                             double *out_r, int32_t *err, bool validate, cudaStream_t s,
+                             const int64_t *src)
 {
     if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
     dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
     positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
-                                                  kt, cshift, A, out_r, err, validate ? 1 : 0);
+                                                  kt, cshift, A, out_r, err, validate ? 1 : 0,
+                                                  src);
     return cudaGetLastError();
 }
 

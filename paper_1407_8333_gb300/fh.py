@@ -94,6 +94,8 @@ _SIGS = {
     "fh_autotune": ([_P, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P], ctypes.c_int),
     "fh_plan_launches": ([_P], _i64),
     "fh_set_weights": ([_P, _P, _i32, _i32, _P], ctypes.c_int),
+    "fh_refine": ([_P, ctypes.POINTER(fh_peakmap), _P, _P, _P, _i32, _P, _i32, _i32, _P, _i64, _P],
+                  ctypes.c_int),
     "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
     "fh_plan_kernel_times": ([_P, ctypes.POINTER(_i64), ctypes.POINTER(_f64), ctypes.POINTER(_f64)],
                              ctypes.c_int),
@@ -279,6 +281,27 @@ def fh_autotune(plan, dir_begin: int, n_dir: int, stream=None) -> tuple:
 
 def fh_plan_launches(plan) -> int:
     return int(load().fh_plan_launches(plan))
+
+
+def fh_refine(plan, t, offsets, freq, v_over_c, cells, rows, sky_ref, k_fdot: int,
+              stream=None) -> np.ndarray:
+    """Refined candidates (host arrays in, structured array out), one per
+    coarse candidate; sky_ref is n_cand x n_ref x 3."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    freq = np.ascontiguousarray(freq, dtype=np.float64)
+    v = np.ascontiguousarray(v_over_c, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    sky = np.ascontiguousarray(sky_ref, dtype=np.float64)
+    n_cand, n_ref = int(sky.shape[0]), int(sky.shape[1])
+    pm = make_peakmap(t, offsets, freq)
+    out = np.zeros(n_cand, dtype=CANDIDATE_DTYPE)
+    _check(load().fh_refine(plan, ctypes.byref(pm), v.ctypes.data_as(_P),
+                            cells.ctypes.data_as(_P), rows.ctypes.data_as(_P), n_cand,
+                            sky.ctypes.data_as(_P), n_ref, int(k_fdot), out.ctypes.data_as(_P),
+                            n_cand, _stream(stream)), "fh_refine")
+    return out
 
 
 def fh_set_weights(plan, w, frac_bits: int = 0, stream=None) -> None:
