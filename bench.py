@@ -159,10 +159,21 @@ def peaks_path():
     return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def cpu_baseline_leg(inp, pp, budget_s=12.0):
-    """The oracle as it stands, whole path a1-a6 on the same workload."""
+def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None):
+    """The oracle as it stands, whole path a1-a6 on the same workload (and, given
+    refine_args = (cells, rows, sky_ref, k_fdot), its refined-grid search on a
+    few of the workload's candidates)."""
     import oracle
     oracle.build()
+    ref = None
+    if refine_args is not None:
+        cells, rows, sky_ref, k_fdot = refine_args
+        t0 = time.perf_counter()
+        oracle.refine(inp, pp, cells, rows, sky_ref, k_fdot)
+        dt = time.perf_counter() - t0
+        ref = {"candidates_per_s": len(cells) / dt, "cores": oracle.num_threads(),
+               "sample": "%d candidates, %d refined directions, K_fdot = %d, one run (%.2f s)"
+                         % (len(cells), sky_ref.shape[1], k_fdot, dt)}
     upd = inp.n_peaks * pp["n_fdot"] * inp.sky.shape[0]
     times = []
     t_start = time.perf_counter()
@@ -173,9 +184,12 @@ def cpu_baseline_leg(inp, pp, budget_s=12.0):
         if time.perf_counter() - t_start > budget_s or len(times) >= 5:
             break
     best = min(times)
-    return {"value": upd / best, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "whole path a1-a6 (maps, profile, selection) on the full workload, "
-                      "1 direction, best of %d runs (%.2f s each)" % (len(times), best)}
+    out = {"value": upd / best, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "whole path a1-a6 (maps, profile, selection) on the full workload, "
+                     "1 direction, best of %d runs (%.2f s each)" % (len(times), best)}
+    if ref is not None:
+        out["refine"] = ref
+    return out
 
 
 # ----------------------------------------------------------------------------- ours
@@ -329,7 +343,12 @@ def run_ours(args):
             out["serving"] = serving_leg(fh, synth, torch, args.serve_seconds)
         except Exception as e:  # report, do not hide
             out["serving"] = {"error": str(e)[:300]}
-        out["cpu_baseline"] = cpu_baseline_leg(inp, pp)
+        ref_args = None
+        try:
+            out["refine"], ref_args = refine_leg(fh, synth, w, inp, pp, host_out, args.steps)
+        except Exception as e:  # report, do not hide
+            out["refine"] = {"error": str(e)[:300]}
+        out["cpu_baseline"] = cpu_baseline_leg(inp, pp, refine_args=ref_args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -372,6 +391,38 @@ def adaptive_leg(fh, inp, pp, dev, cand, flush, torch, steps):
     return {"weights": "1 + 0.5 cos(2 pi t / sidereal day), 12 fraction bits",
             "ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3),
             "transform_kernel_ms": kms / n_g}
+
+
+def refine_leg(fh, synth, w, inp, pp, host_out, steps):
+    """Refined-grid search (Sec. "Refined Grid in the parameter space") of every
+    candidate the coarse step selected: a 3 x 3 refined sky rectangle around
+    its direction, the spin-down step refined by 4, through the host API
+    (host peakmap and candidates in, refined candidates out, copies included)."""
+    import numpy as np
+    cand = host_out[host_out["count"] >= 0]
+    cells = cand["cell"].astype(np.int32)
+    rows = cand["row"].astype(np.int32)
+    n_d = synth.doppler_number(w.f_hi, w.t_fft)
+    sky = np.stack([synth.refined_sky(inp.sky[int(c["dir"])], n_d, 3) for c in cand])
+    k_fdot = 4
+    plan = fh.fh_create_plan(fh.make_desc(pp, inp.t.shape[0], 1, inp.n_peaks))
+    try:
+        ts = []
+        for k in range(2 + steps):
+            t0 = time.perf_counter()
+            r = fh.fh_refine(plan, inp.t, inp.offsets, inp.freq, inp.v, cells, rows, sky, k_fdot)
+            if k >= 2:
+                ts.append((time.perf_counter() - t0) * 1e3)
+    finally:
+        fh.fh_destroy_plan(plan)
+    ms = statistics.median(ts)
+    gain = r["count"].astype(np.int64) - cand["count"].astype(np.int64)
+    res = {"n_cand": int(cand.shape[0]), "n_ref": int(sky.shape[1]), "k_fdot": k_fdot,
+           "ms_per_call": ms, "candidates_per_s": cand.shape[0] / (ms * 1e-3),
+           "count_gain_median": float(np.median(gain)) if gain.size else None,
+           "inputs": "host (pageable) peakmap, copied every call"}
+    sel = slice(0, min(3, cand.shape[0]))
+    return res, (cells[sel], rows[sel], sky[sel], k_fdot)
 
 
 def batched_vs_plain(fh, synth, torch):

@@ -29,10 +29,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct RangeArgs {
-    const double *t, *freq, *v;
+    const double *t, *freq, *v, *sky;  // sky: [cand][n_ref][3]
     const int64_t *offsets, *S0, *D, *Dr;
     const int32_t *cell, *row;
-    int32_t n_fft, n_cand, k_over, n_rows;
+    int32_t n_fft, n_cand, k_over, n_rows, n_ref;
     double f0_min, kt;
     int64_t *start;   // [cand][fft]: first peak of the range
     int32_t *count;   // [cand][fft]: peaks in the range
@@ -43,10 +43,12 @@ struct RangeArgs {
 // s touches it iff s in [1 - K, 2K].  With the refined shifts X_j = S0r + j D'
 // (j < n_rows), positions A in [min_j X_j + (1 - K) 2^32, max_j X_j + (2K + 1)
 // 2^32) can touch it; one extra cell on each side covers rounding.  A position
-// is about ((f r - f0_min) KT + 0.5 - 0.5 K) 2^32 and r = 1 / (1 + v.n) with
-// |v.n| <= |v| (unit sky vectors), so the frequencies f = u (1 + v.n) of the
-// peaks that can take part lie between the extremes of u (1 -+ |v|') over
-// u in [u_lo, u_hi], |v|' = 1.0001 |v|.  The window is a superset: the transform decides exactly.
+// is about ((f r - f0_min) KT + 0.5 - 0.5 K) 2^32 with r = 1 / (1 + v.n), so
+// the frequencies f = u (1 + v.n) of the peaks that can take part lie between
+// the extremes of that product over u in [u_lo, u_hi] and v.n between its
+// least and largest value over the candidate's refined directions (a bilinear
+// form: the extremes are at the corners).  The margin of a cell is far above
+// the rounding of these products; the transform decides exactly.
 __global__ void refine_ranges_kernel(const RangeArgs a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,10 +66,17 @@ __global__ void refine_ranges_kernel(const RangeArgs a)
     const double u_hi = a.f0_min + (xmax + (double)(2 * K + 1) + 1.0 - c_off) / a.kt;
     const double vx = a.v[3 * (int64_t)i], vy = a.v[3 * (int64_t)i + 1],
                  vz = a.v[3 * (int64_t)i + 2];
-    const double vm = 1.0001 * sqrt(vx * vx + vy * vy + vz * vz);
-    // f = u (1 + v.n): the extremes over |v.n| <= vm, for either sign of u
-    const double f_lo = fmin(u_lo * (1.0 - vm), u_lo * (1.0 + vm));
-    const double f_hi = fmax(u_hi * (1.0 - vm), u_hi * (1.0 + vm));
+    double vn_lo = 0.0, vn_hi = 0.0;
+    const double *n = a.sky + 3 * (int64_t)c * a.n_ref;
+    for (int d = 0; d < a.n_ref; ++d, n += 3) {
+        const double vn = vx * n[0] + vy * n[1] + vz * n[2];
+        vn_lo = d ? fmin(vn_lo, vn) : vn;
+        vn_hi = d ? fmax(vn_hi, vn) : vn;
+    }
+    const double f_lo = fmin(fmin(u_lo * (1.0 + vn_lo), u_lo * (1.0 + vn_hi)),
+                             fmin(u_hi * (1.0 + vn_lo), u_hi * (1.0 + vn_hi)));
+    const double f_hi = fmax(fmax(u_lo * (1.0 + vn_lo), u_lo * (1.0 + vn_hi)),
+                             fmax(u_hi * (1.0 + vn_lo), u_hi * (1.0 + vn_hi)));
     int64_t lo = a.offsets[i], hi = a.offsets[i + 1];
     int64_t b = hi;
     while (lo < b) {  // first peak with f >= f_lo
@@ -267,6 +276,8 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     ra.t = t;
     ra.freq = freq;
     ra.v = v;
+    ra.sky = sky;
+    ra.n_ref = n_ref;
     ra.offsets = off;
     ra.S0 = S0;
     ra.D = D;
