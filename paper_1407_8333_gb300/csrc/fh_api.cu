@@ -459,9 +459,9 @@ int fh_refine(fh_plan p, const fh_peakmap *pm, const double *v_over_c, const int
                                              "k_fdot in [1, 64]");
     if ((int64_t)n_cand * n_ref > 1000000000)
         return set_error(FH_ERR_INVALID_ARG, "n_cand x n_ref too large");
-    if (pm->n_fft < 0 || pm->n_peaks < 0 || !pm->offsets || (pm->n_fft > 0 && !pm->t_fft) ||
-        (pm->n_peaks > 0 && !pm->freq))
-        return set_error(FH_ERR_INVALID_ARG, "bad peakmap");
+    if (pm->n_fft < 0 || pm->n_peaks < 0 || pm->n_peaks >= ((int64_t)1 << 31) || !pm->offsets ||
+        (pm->n_fft > 0 && !pm->t_fft) || (pm->n_peaks > 0 && !pm->freq))
+        return set_error(FH_ERR_INVALID_ARG, "bad peakmap (n_fft >= 0, n_peaks in [0, 2^31))");
     if (capacity < n_cand)
         return set_error(FH_ERR_CAPACITY, "need %d refined candidate slots, capacity %lld", n_cand,
                          (long long)capacity);

@@ -749,7 +749,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             if constexpr (WEIGHTED)
                 if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
             if (wrow != nullptr) {
-                // precomputed window: one coalesced load, clamped into the FFT's CSR range
+                // precomputed window: one coalesced load; trusted on the unclamped walk
+                // (the input checks passed and the table was built from the sanitised
+                // CSR), else clamped into the FFT's CSR range
                 const int i = (c << 5) + lane;
                 cb = 0;
                 dv = 0;
@@ -757,13 +759,18 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 n = 0;
                 if (i < n_fft) {
                     const int2 wv = wrow[i];
-                    const int64_t o0 = __ldg(offs + i), o1 = __ldg(offs + i + 1);
                     dv = __ldg(Dt + i);
                     cb = __ldg(S0 + i) + (int64_t)j0 * dv + base_shift;
-                    const int64_t a = wv.x < o0 ? o0 : (wv.x > o1 ? o1 : wv.x);
-                    const int64_t b = wv.y < a ? a : (wv.y > o1 ? o1 : wv.y);
-                    q0 = a;
-                    n = (int)(b - a);
+                    if (fast) {
+                        q0 = wv.x;
+                        n = wv.y - wv.x;
+                    } else {
+                        const int64_t o0 = __ldg(offs + i), o1 = __ldg(offs + i + 1);
+                        const int64_t a = wv.x < o0 ? o0 : (wv.x > o1 ? o1 : wv.x);
+                        const int64_t b = wv.y < a ? a : (wv.y > o1 ? o1 : wv.y);
+                        q0 = a;
+                        n = (int)(b - a);
+                    }
                 }
             } else {
                 lookup_window(Ad, offs, S0, Dt, n_fft, (c << 5) + lane, j0, R, base_shift,
@@ -784,6 +791,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             const int T = __shfl_sync(kFull, P, 31);
             P -= m;
             const bool has = m > 0;
+            // the slot's first peak is kq + (pairs ? 2 : 1) g; the window ends at qe
+            const int kq = (int)q0 - (kPairs ? 2 * P : P);
+            const int qe = (int)q0 + n;
             const unsigned nonempty = __ballot_sync(kFull, has);
             if (has) tab[__popc(nonempty & lanemask_lt)] = lane;
             __syncwarp();
@@ -792,7 +802,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             // range [P, P + m) holds it.  `before` counts the non-empty FFTs
             // starting below the base; bases are fetched in increasing order, 32
             // apart.  The slot's peaks are positions q0 + k, k = (pairs) 2 (g - P)
-            // and 2 (g - P) + 1 (if below n), or (singles) g - P.
+            // and 2 (g - P) + 1 (if below q0 + n), or (singles) g - P: the owner
+            // publishes kq = q0 - 2 P (q0 - P) and its window end qe.
             int before = 0;
             auto fetch = [&](int base, int64_t &a1, int64_t &a2, bool &two, int &owner) {
                 const unsigned rel = (unsigned)(P - base);
@@ -800,19 +811,18 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 const int oc = before + __popc(bits & lanemask_le) - 1;
                 before += __popc(bits);
                 owner = tab[oc < 0 ? 0 : oc];
-                const int64_t oq0 = __shfl_sync(kFull, q0, owner);
-                const int oP = __shfl_sync(kFull, P, owner);
+                const int okq = __shfl_sync(kFull, kq, owner);
                 const int g = base + lane;
                 const bool live = g < T;
                 if (kPairs) {
-                    const int on = __shfl_sync(kFull, n, owner);
-                    const int k = 2 * (g - oP);
-                    two = live && k + 1 < on;
-                    a1 = live ? __ldg(Ad + oq0 + k) : 0;
-                    a2 = two ? __ldg(Ad + oq0 + k + 1) : 0;
+                    const int oqe = __shfl_sync(kFull, qe, owner);
+                    const int k = okq + 2 * g;
+                    two = live && k + 1 < oqe;
+                    a1 = live ? __ldg(Ad + k) : 0;
+                    a2 = two ? __ldg(Ad + k + 1) : 0;
                 } else {
                     two = false;
-                    a1 = live ? __ldg(Ad + oq0 + (g - oP)) : 0;
+                    a1 = live ? __ldg(Ad + (okq + g)) : 0;
                     a2 = 0;
                 }
             };
@@ -837,11 +847,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 const bool live = g < T;
                 const int64_t odv = live ? odv0 : 0;
                 // e[b] = +-(D << b), + when bit b of the lane is set
+                const int64_t ndv = -odv;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) {
-                    const int64_t sh = odv * (int64_t)(1 << b);
-                    e[b] = ((lane >> b) & 1) ? sh : -sh;
-                }
+                for (int b = 0; b < 5; ++b) e[b] = (((lane >> b) & 1) ? odv : ndv) * (int64_t)(1 << b);
                 const int64_t lane_dv = (int64_t)lane * odv;
                 X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
                 if (kPairs) {
