@@ -276,7 +276,8 @@ int fh_plan_kernel_times(fh_plan plan, int64_t *n_groups, double *windows_ms,
  * directions, rows and cells (ties: smallest direction, then row, then cell).
  *   plan      the coarse grid and selection parameters (its buffers are not
  *             used, and its peakmap is not changed)
- *   pm, v_over_c  HOST peakmap and velocities, checked as by fh_correct_doppler
+ *   pm, v_over_c  HOST peakmap (n_peaks < 2^31) and velocities, checked as by
+ *             fh_correct_doppler; the refined maps are plain (unweighted) counts
  *   sky_ref   HOST n_cand x n_ref x 3 unit vectors
  *   k_fdot    1 .. 64
  *   out       HOST n_cand slots: dir = refined direction index, subband = c,
