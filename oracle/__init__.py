@@ -30,6 +30,8 @@ import threading
 
 import numpy as np
 
+from . import peakmap  # noqa: F401  (peakmap construction and cleaning)
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fh_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")

@@ -9,6 +9,9 @@ Each function restates one equation of the paper in binary64:
 * ``n_thr_gauss``  count threshold for a false-alarm probability (Eq. nthr_gauss)
 * ``cr_thr``       CR threshold for N_cand of N_tot points (Eq. crthr)
 * ``n_tot``        number of coarse parameter-space points (Eq. Ntot, Sec. VIII)
+* ``gross_points`` points N of one gross-histogram cell and its noise mean and
+                   standard deviation E_H = N p0, sigma_H = sqrt(N p0 (1 - p0))
+                   (Sec. "Removal of spectral wandering lines")
 """
 from __future__ import annotations
 
@@ -57,3 +60,15 @@ def n_tot(k_f: float, k_sky: float, t_fft: float, dt: float, t_obs: float,
         prod *= (t_obs / tau_min) ** j
         j += 1
     return 5.6 * math.pi * 1e-9 * k_f * k_sky * base ** (3 + j_max) * prod, j_max
+
+
+def gross_points(dt_h: float, df_h: float, t_fft: float, interlaced: bool = True) -> float:
+    """N = (Delta t_H / T_FFT)(Delta f_H / delta f) points per gross cell, delta f =
+    1 / T_FFT; FFTs overlapping by half double it (N = 2 Delta t_H Delta f_H)."""
+    n = (dt_h / t_fft) * (df_h * t_fft)
+    return 2.0 * n if interlaced else n
+
+
+def gross_noise(n_points: float, p: float) -> tuple:
+    """(E_H, sigma_H) = (N p0, sqrt(N p0 (1 - p0))) of a noise-only gross cell."""
+    return n_points * p, math.sqrt(n_points * p * (1.0 - p))

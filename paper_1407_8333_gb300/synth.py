@@ -486,3 +486,91 @@ def random_case(seed: int, n_fft: int = 20, n_bins: int = 40, k_over: int = 10,
     inp = Inputs(w=w, t=t, offsets=offsets, freq=np.ascontiguousarray(freq),
                  v=np.ascontiguousarray(v), sky=np.ascontiguousarray(sky))
     return inp, params
+
+
+# --------------------------------------------------------------------------
+# Spectra for peakmap construction (periodogram and AR average spectrum)
+# --------------------------------------------------------------------------
+_S_SPEC_E, _S_SPEC_G = 8, 9
+
+
+@dataclass
+class Spectra:
+    """Per-FFT spectra of one band: s_p (periodogram) and s_ar (average
+    spectrum estimate), both (n_fft, n_bins) binary32; t (n_fft) FFT start
+    times; bin b of the band is frequency (k0 + b) / t_fft."""
+    s_p: np.ndarray
+    s_ar: np.ndarray
+    t: np.ndarray
+    k0: int
+    t_fft: float
+    wander_bins: np.ndarray   # per FFT, the wandering line's bin (-1: none)
+    const_bins: np.ndarray    # bins of the constant lines
+    signal_bins: np.ndarray   # per FFT, the signal track's bin (-1: none)
+
+
+def spectra_case(seed: int, n_fft: int, n_bins: int, t_fft: float = 8192.0,
+                 f_lo: float = 50.0, interlaced: bool = True, signal_lambda: float = 0.0,
+                 signal_f0: float = None, signal_fdot: float = 0.0, wander_amp: float = 0.0,
+                 wander_f: tuple = None, wander_width: int = 1, const_lines: tuple = (),
+                 const_amp: float = 40.0,
+                 const_frac: float = 0.8) -> Spectra:
+    """Seeded spectra with the statistics the peakmap section describes:
+    s_ar a smooth positive curve over the band and s_p = s_ar x, where x is the
+    equalised periodogram, exponential with mean 1 for noise and normalised
+    non-central chi^2 with 2 degrees of freedom and non-centrality lambda
+    (mean 1 + lambda / 2) in the bins of a signal track f0 + fdot (t - t_mid).
+
+    Disturbances: a wandering line (``wander_width`` bins per FFT drifting
+    between the two frequencies of ``wander_f``, x = wander_amp in every other
+    one of them, so that each is a local maximum) and constant lines at
+    the frequencies ``const_lines`` (x = const_amp in a fraction const_frac of
+    the FFTs).  Draws: SplitMix64 counter streams; exponentials as -log(1 - u),
+    Gaussians by Box-Muller."""
+    k0 = int(round(f_lo * t_fft))
+    step = 0.5 * t_fft if interlaced else t_fft
+    t = np.arange(n_fft, dtype=np.float64) * step
+    m = n_fft * n_bins
+    u = uniform(seed, _S_SPEC_E, np.arange(m)).reshape(n_fft, n_bins)
+    x = -np.log1p(-u)
+    j = np.arange(n_bins, dtype=np.float64)
+    s_ar = (1.0 + 0.3 * np.sin(2.0 * np.pi * j / max(n_bins, 1)) + 0.1 * j / max(n_bins, 1))
+    s_ar = np.broadcast_to(s_ar, (n_fft, n_bins)) * (1.0 + 0.05 * np.cos(
+        2.0 * np.pi * t / max(t[-1], 1.0)))[:, None]
+    sig = np.full(n_fft, -1, dtype=np.int64)
+    if signal_lambda > 0.0:
+        f0 = f_lo + 0.5 * n_bins / t_fft if signal_f0 is None else signal_f0
+        tm = 0.5 * (t[0] + t[-1])
+        sig = np.rint((f0 + signal_fdot * (t - tm)) * t_fft).astype(np.int64) - k0
+        ok = (sig >= 0) & (sig < n_bins)
+        g = uniform(seed, _S_SPEC_G, np.arange(4 * n_fft)).reshape(4, n_fft)
+        r = np.sqrt(-2.0 * np.log1p(-g[0]))
+        g1 = r * np.cos(2.0 * np.pi * g[1])
+        g2 = r * np.sin(2.0 * np.pi * g[1])
+        xs = ((np.sqrt(signal_lambda) + g1) ** 2 + g2 ** 2) / 2.0
+        rows = np.nonzero(ok)[0]
+        x[rows, sig[rows]] = xs[rows]
+        sig[~ok] = -1
+    wand = np.full(n_fft, -1, dtype=np.int64)
+    if wander_amp > 0.0 and wander_f is not None:
+        fa, fb = wander_f
+        ph = np.arange(n_fft) / max(n_fft - 1, 1)
+        fw = fa + (fb - fa) * (0.5 - 0.5 * np.cos(np.pi * ph))
+        wand = np.rint(fw * t_fft).astype(np.int64) - k0
+        for q in range(0, int(wander_width), 2):
+            wb = wand + q
+            rows = np.nonzero((wb >= 0) & (wb < n_bins))[0]
+            x[rows, wb[rows]] = wander_amp
+        wand[(wand < 0) | (wand >= n_bins)] = -1
+    cb = np.array([int(round(f * t_fft)) - k0 for f in const_lines], dtype=np.int64)
+    if cb.size:
+        on = uniform(seed, _S_SPEC_G + 1, np.arange(n_fft * cb.size)).reshape(n_fft, cb.size)
+        for q, b in enumerate(cb):
+            if 0 <= b < n_bins:
+                rows = np.nonzero(on[:, q] < const_frac)[0]
+                x[rows, b] = const_amp
+    s_ar32 = s_ar.astype(np.float32)
+    s_p32 = (s_ar * x).astype(np.float32)
+    return Spectra(s_p=np.ascontiguousarray(s_p32), s_ar=np.ascontiguousarray(s_ar32), t=t,
+                   k0=k0, t_fft=float(t_fft), wander_bins=wand, const_bins=cb,
+                   signal_bins=sig)
