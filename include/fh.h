@@ -262,6 +262,58 @@ int fh_plan_set_timing(fh_plan plan, int32_t on);
 int fh_plan_kernel_times(fh_plan plan, int64_t *n_groups, double *windows_ms,
                          double *transform_ms);
 
+/* ---- peakmap construction and cleaning ------------------------------------ */
+/* A binned peakmap: offsets (n_fft + 1, int64, a CSR by FFT, offsets[0] = 0) and
+ * the band-relative bin index of every peak (int32, ascending within an FFT);
+ * bin b is frequency (k0 + b) / t_fft.  The optional freq outputs hold exactly
+ * that (binary64), ready for fh_correct_doppler.  All arrays are DEVICE memory
+ * of the current device; each call takes its scratch stream-ordered, runs on
+ * `stream` and synchronises it (the counts come back to the host).  Output
+ * lists hold `capacity` peaks; a larger result writes the first `capacity`,
+ * sets *n_* to the full count and returns FH_ERR_CAPACITY.  Device-side
+ * checks: offsets that are not a CSR of n_peaks, or bins outside the band,
+ * give FH_ERR_INVALID_ARG (the kernels clamp every range, nothing is read out
+ * of bounds). */
+
+/* Peak selection (Sec. "Peakmap", Eq. pm).  s_p, s_ar: n_fft rows of n_bins
+ * binary32 values (periodogram and average-spectrum estimate at the same
+ * resolution), row pitch `pitch` elements.  R = s_p / s_ar, one IEEE binary32
+ * division per bin; bin j of FFT i is a peak when R > theta and R is above
+ * both R(j - 1) and R(j + 1) (so bins 0 and n_bins - 1, with one neighbour, are
+ * never peaks).  Outputs offsets, bins, freq (nullable); *n_peaks (HOST).
+ * n_fft <= 65535. */
+int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_t n_bins,
+                      int64_t pitch, float theta, int64_t k0, double t_fft, int64_t *offsets,
+                      int32_t *bins, double *freq, int64_t capacity, int64_t *n_peaks,
+                      void *stream);
+
+/* Wandering-line veto (Sec. "Removal of spectral wandering lines").  The gross
+ * histogram hist (DEVICE, n_th x n_fh int32, written) counts the peaks per
+ * cell: time cell floor((t[i] - t0_h) / dt_h) of the FFT's start time,
+ * frequency cell floor(((k0 + b) / t_fft - f0_h) / df_h) (binary64 operations
+ * in this order); peaks off the grid are not counted.  Every peak of a cell
+ * holding more than `threshold` peaks is removed; the others are written, in
+ * order, to offsets_out / bins_out / freq_out (nullable); *n_out (HOST). */
+int fh_peakmap_gross_veto(const double *t, const int64_t *offsets, const int32_t *bins,
+                          int32_t n_fft, int64_t n_peaks, int64_t k0, double t_fft, double t0_h,
+                          double dt_h, int32_t n_th, double f0_h, double df_h, int32_t n_fh,
+                          int32_t threshold, int32_t *hist, int64_t *offsets_out,
+                          int32_t *bins_out, double *freq_out, int64_t capacity, int64_t *n_out,
+                          void *stream);
+
+/* Constant-line veto by persistency (Sec. "Removal of spectral lines of
+ * constant frequency"; App. "Robust statistic").  hist (DEVICE, n_bins int32,
+ * written): the number of peaks in each bin over all FFTs.  stats (HOST, 3
+ * doubles, written): m1 = median(hist) (the mean of the two middle values for
+ * an even n_bins), m2 = median(|hist - m1|) / 0.6745, thr = m1 + k_sigma m2.
+ * Every peak of a bin with hist > thr is removed; the rest is written as for
+ * the gross veto. */
+int fh_peakmap_persistency_veto(const int64_t *offsets, const int32_t *bins, int32_t n_fft,
+                                int64_t n_peaks, int32_t n_bins, double k_sigma, int64_t k0,
+                                double t_fft, int32_t *hist, double *stats,
+                                int64_t *offsets_out, int32_t *bins_out, double *freq_out,
+                                int64_t capacity, int64_t *n_out, void *stream);
+
 /* ---- refined grid around coarse candidates -------------------------------- */
 
 /* Refined-grid search (Sec. "Refined Grid in the parameter space"): one

@@ -94,6 +94,12 @@ _SIGS = {
     "fh_autotune": ([_P, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P], ctypes.c_int),
     "fh_plan_launches": ([_P], _i64),
     "fh_set_weights": ([_P, _P, _i32, _i32, _P], ctypes.c_int),
+    "fh_peakmap_select": ([_P, _P, _i32, _i32, _i64, ctypes.c_float, _i64, _f64, _P, _P, _P,
+                           _i64, _P, _P], ctypes.c_int),
+    "fh_peakmap_gross_veto": ([_P, _P, _P, _i32, _i64, _i64, _f64, _f64, _f64, _i32, _f64, _f64,
+                               _i32, _i32, _P, _P, _P, _P, _i64, _P, _P], ctypes.c_int),
+    "fh_peakmap_persistency_veto": ([_P, _P, _i32, _i64, _i32, _f64, _i64, _f64, _P, _P, _P, _P,
+                                     _P, _i64, _P, _P], ctypes.c_int),
     "fh_refine": ([_P, ctypes.POINTER(fh_peakmap), _P, _P, _P, _i32, _P, _i32, _i32, _P, _i64, _P],
                   ctypes.c_int),
     "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
@@ -281,6 +287,81 @@ def fh_autotune(plan, dir_begin: int, n_dir: int, stream=None) -> tuple:
 
 def fh_plan_launches(plan) -> int:
     return int(load().fh_plan_launches(plan))
+
+
+def _dev_ptr(x):
+    return None if x is None else ctypes.c_void_p(x.data_ptr())
+
+
+def fh_peakmap_select(s_p, s_ar, theta: float, k0: int, t_fft: float, capacity: int = None,
+                      want_freq: bool = True, stream=None):
+    """Peaks of device spectra (torch float32, (n_fft, n_bins), rows contiguous).
+    Returns (offsets int64, bins int32, freq float64 or None) on the device."""
+    import torch
+    n_fft, n_bins = int(s_p.shape[0]), int(s_p.shape[1])
+    if s_p.stride(1) != 1 or s_ar.stride(1) != 1 or s_p.stride(0) != s_ar.stride(0):
+        raise ValueError("s_p and s_ar need unit-stride rows of the same pitch")
+    cap = int(capacity) if capacity is not None else max(1, n_fft * max(0, n_bins - 1) // 2)
+    dev = s_p.device
+    offsets = torch.empty(n_fft + 1, dtype=torch.int64, device=dev)
+    bins = torch.empty(cap, dtype=torch.int32, device=dev)
+    freq = torch.empty(cap, dtype=torch.float64, device=dev) if want_freq else None
+    n = ctypes.c_int64(0)
+    _check(load().fh_peakmap_select(_dev_ptr(s_p), _dev_ptr(s_ar), n_fft, n_bins,
+                                    int(s_p.stride(0)), float(theta), int(k0), float(t_fft),
+                                    _dev_ptr(offsets), _dev_ptr(bins), _dev_ptr(freq), cap,
+                                    ctypes.byref(n), _stream(stream)), "fh_peakmap_select")
+    k = n.value
+    return offsets, bins[:k], (freq[:k] if freq is not None else None)
+
+
+def fh_peakmap_gross_veto(t, offsets, bins, k0: int, t_fft: float, t0_h: float, dt_h: float,
+                          n_th: int, f0_h: float, df_h: float, n_fh: int, threshold: int,
+                          want_freq: bool = True, stream=None):
+    """Wandering-line veto of a device peakmap.  Returns (offsets, bins, freq,
+    hist (n_th, n_fh) int32) on the device."""
+    import torch
+    dev = offsets.device
+    n_fft = int(offsets.shape[0]) - 1
+    n_peaks = int(bins.shape[0])
+    hist = torch.empty((int(n_th), int(n_fh)), dtype=torch.int32, device=dev)
+    o2 = torch.empty(n_fft + 1, dtype=torch.int64, device=dev)
+    cap = max(1, n_peaks)
+    b2 = torch.empty(cap, dtype=torch.int32, device=dev)
+    f2 = torch.empty(cap, dtype=torch.float64, device=dev) if want_freq else None
+    n = ctypes.c_int64(0)
+    _check(load().fh_peakmap_gross_veto(_dev_ptr(t), _dev_ptr(offsets), _dev_ptr(bins), n_fft,
+                                        n_peaks, int(k0), float(t_fft), float(t0_h), float(dt_h),
+                                        int(n_th), float(f0_h), float(df_h), int(n_fh),
+                                        int(threshold), _dev_ptr(hist), _dev_ptr(o2),
+                                        _dev_ptr(b2), _dev_ptr(f2), cap, ctypes.byref(n),
+                                        _stream(stream)), "fh_peakmap_gross_veto")
+    k = n.value
+    return o2, b2[:k], (f2[:k] if f2 is not None else None), hist
+
+
+def fh_peakmap_persistency_veto(offsets, bins, n_bins: int, k_sigma: float, k0: int,
+                                t_fft: float, want_freq: bool = True, stream=None):
+    """Constant-line veto of a device peakmap.  Returns (offsets, bins, freq,
+    hist (n_bins) int32, (m1, m2, thr))."""
+    import torch
+    dev = offsets.device
+    n_fft = int(offsets.shape[0]) - 1
+    n_peaks = int(bins.shape[0])
+    hist = torch.empty(int(n_bins), dtype=torch.int32, device=dev)
+    o2 = torch.empty(n_fft + 1, dtype=torch.int64, device=dev)
+    cap = max(1, n_peaks)
+    b2 = torch.empty(cap, dtype=torch.int32, device=dev)
+    f2 = torch.empty(cap, dtype=torch.float64, device=dev) if want_freq else None
+    stats = (ctypes.c_double * 3)()
+    n = ctypes.c_int64(0)
+    _check(load().fh_peakmap_persistency_veto(_dev_ptr(offsets), _dev_ptr(bins), n_fft, n_peaks,
+                                              int(n_bins), float(k_sigma), int(k0), float(t_fft),
+                                              _dev_ptr(hist), ctypes.cast(stats, _P), _dev_ptr(o2), _dev_ptr(b2),
+                                              _dev_ptr(f2), cap, ctypes.byref(n),
+                                              _stream(stream)), "fh_peakmap_persistency_veto")
+    k = n.value
+    return o2, b2[:k], (f2[:k] if f2 is not None else None), hist, tuple(stats)
 
 
 def fh_refine(plan, t, offsets, freq, v_over_c, cells, rows, sky_ref, k_fdot: int,

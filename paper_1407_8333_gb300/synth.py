@@ -574,3 +574,23 @@ def spectra_case(seed: int, n_fft: int, n_bins: int, t_fft: float = 8192.0,
     return Spectra(s_p=np.ascontiguousarray(s_p32), s_ar=np.ascontiguousarray(s_ar32), t=t,
                    k0=k0, t_fft=float(t_fft), wander_bins=wand, const_bins=cb,
                    signal_bins=sig)
+
+
+# The peakmap workload: 150 days of FFTs of 8192 s overlapping by half (3164),
+# a 1 Hz band at 50 Hz (8192 bins), threshold theta = 2.5 (p0 = 0.0755), a
+# gross grid of 12 h x 0.01 Hz with the veto at E_H + 4.5 sigma_H (65 + 35),
+# persistency veto at m1 + 5 m2.
+PEAKMAP_PARAMS = dict(n_fft=3164, n_bins=8192, t_fft=8192.0, f_lo=50.0, theta=2.5,
+                      dt_h=43200.0, n_th=300, df_h=0.01, f0_h=50.0, n_fh=100, gross_thr=100,
+                      k_sigma=5.0)
+
+
+def peakmap_workload(seed: int = 41) -> Spectra:
+    """Spectra of the peakmap workload: noise, a signal track (lambda = 3,
+    50.3 Hz, -1e-9 Hz/s), a wandering line 15 bins wide drifting from 50.55 to
+    50.75 Hz, constant lines at 50.123 and 50.877 Hz in 80 % of the FFTs."""
+    p = PEAKMAP_PARAMS
+    return spectra_case(seed, p["n_fft"], p["n_bins"], t_fft=p["t_fft"], f_lo=p["f_lo"],
+                        signal_lambda=3.0, signal_f0=50.3, signal_fdot=-1e-9,
+                        wander_amp=40.0, wander_f=(50.55, 50.75), wander_width=15,
+                        const_lines=(50.123, 50.877), const_amp=40.0, const_frac=0.8)
