@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu legs")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--legs", default="adaptive,batched,serving,refine,peakmap,cpu",
+                    help="extra legs to run after the timed step (comma list)")
     return ap.parse_args()
 
 
@@ -159,7 +161,7 @@ def peaks_path():
     return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None):
+def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None):
     """The oracle as it stands, whole path a1-a6 on the same workload (and, given
     refine_args = (cells, rows, sky_ref, k_fdot), its refined-grid search on a
     few of the workload's candidates)."""
@@ -189,6 +191,14 @@ def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None):
                      "1 direction, best of %d runs (%.2f s each)" % (len(times), best)}
     if ref is not None:
         out["refine"] = ref
+    if peakmap is not None:
+        t0 = time.perf_counter()
+        oracle.peakmap.select_peaks(peakmap.s_p, peakmap.s_ar, 2.5)
+        dt = time.perf_counter() - t0
+        n = peakmap.s_p.size
+        out["peakmap"] = {"bins_per_s": n / dt, "cores": 1,
+                          "sample": "peak selection of the whole peakmap workload (%d bins), "
+                                    "numpy, one run (%.2f s)" % (n, dt)}
     return out
 
 
@@ -336,19 +346,32 @@ def run_ours(args):
                   "ms_per_step": statistics.mean(e2e_ms)}
     fh.fh_destroy_plan(plan)
 
+    legs = set(args.legs.split(","))
     if rank == 0 and world == 1 and not args.no_extras:
-        out["adaptive"] = adaptive_leg(fh, inp, pp, dev, cand, flush, torch, args.steps)
-        out["batched_vs_plain"] = batched_vs_plain(fh, synth, torch)
-        try:
-            out["serving"] = serving_leg(fh, synth, torch, args.serve_seconds)
-        except Exception as e:  # report, do not hide
-            out["serving"] = {"error": str(e)[:300]}
+        if "adaptive" in legs:
+            out["adaptive"] = adaptive_leg(fh, inp, pp, dev, cand, flush, torch, args.steps)
+        if "batched" in legs:
+            out["batched_vs_plain"] = batched_vs_plain(fh, synth, torch)
+        if "serving" in legs:
+            try:
+                out["serving"] = serving_leg(fh, synth, torch, args.serve_seconds)
+            except Exception as e:  # report, do not hide
+                out["serving"] = {"error": str(e)[:300]}
         ref_args = None
-        try:
-            out["refine"], ref_args = refine_leg(fh, synth, w, inp, pp, host_out, args.steps)
-        except Exception as e:  # report, do not hide
-            out["refine"] = {"error": str(e)[:300]}
-        out["cpu_baseline"] = cpu_baseline_leg(inp, pp, refine_args=ref_args)
+        if "refine" in legs:
+            try:
+                out["refine"], ref_args = refine_leg(fh, synth, w, inp, pp, host_out, args.steps)
+            except Exception as e:  # report, do not hide
+                out["refine"] = {"error": str(e)[:300]}
+        if "peakmap" in legs:
+            try:
+                out["peakmap"] = peakmap_leg(fh, synth, torch, args.steps)
+            except Exception as e:  # report, do not hide
+                out["peakmap"] = {"error": str(e)[:300]}
+        if "cpu" in legs:
+            out["cpu_baseline"] = cpu_baseline_leg(
+                inp, pp, refine_args=ref_args,
+                peakmap=synth.peakmap_workload() if "peakmap" in legs else None)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -423,6 +446,69 @@ def refine_leg(fh, synth, w, inp, pp, host_out, steps):
            "inputs": "host (pageable) peakmap, copied every call"}
     sel = slice(0, min(3, cand.shape[0]))
     return res, (cells[sel], rows[sel], sky[sel], k_fdot)
+
+
+def peakmap_leg(fh, synth, torch, steps):
+    """Peakmap construction (Eq. pm) and cleaning on the 150-day, 1 Hz workload
+    (3164 FFTs x 8192 bins, 207 MB of binary32 spectra, more than L2): the
+    selection timed on the device around its asynchronous call (three kernels);
+    the two vetoes as host calls (each synchronises)."""
+    p = synth.PEAKMAP_PARAMS
+    s = synth.peakmap_workload()
+    sp = torch.from_numpy(s.s_p).cuda()
+    sa = torch.from_numpy(s.s_ar).cuda()
+    t = torch.from_numpy(s.t).cuda()
+    n_fft, n_bins = s.s_p.shape
+    cap = n_fft * n_bins // 4
+    out = (torch.empty(n_fft + 1, dtype=torch.int64, device="cuda"),
+           torch.empty(cap, dtype=torch.int32, device="cuda"),
+           torch.empty(cap, dtype=torch.float64, device="cuda"))
+    ws = torch.empty(fh.fh_peakmap_select_workspace(n_fft, n_bins), dtype=torch.uint8,
+                     device="cuda")
+    ms = []
+    for k in range(3 + steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fh.fh_peakmap_select(sp, sa, p["theta"], s.k0, s.t_fft, out=out, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            ms.append(e0.elapsed_time(e1))
+    n_peaks = int(out[0][-1].item())
+    o, b = out[0], out[1][:n_peaks]
+    grid = (0.0, p["dt_h"], p["n_th"], p["f0_h"], p["df_h"], p["n_fh"])
+    g_ms, c_ms = [], []
+    for k in range(2 + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        go, gb, _, gh = fh.fh_peakmap_gross_veto(t, o, b, s.k0, s.t_fft, *grid, p["gross_thr"])
+        t1 = time.perf_counter()
+        po, pb, _, ph, st = fh.fh_peakmap_persistency_veto(go, gb, n_bins, p["k_sigma"], s.k0,
+                                                           s.t_fft)
+        t2 = time.perf_counter()
+        if k >= 2:
+            g_ms.append((t1 - t0) * 1e3)
+            c_ms.append((t2 - t1) * 1e3)
+    sel = statistics.median(ms)
+    alg = 8 * n_fft * n_bins + 12 * n_peaks
+    peaks, src = peaks_path()
+    gbs = alg / (sel * 1e-3) / 1e9
+    return {"workload": "peakmap_T8192_150d_1Hz: 3164 FFTs x 8192 bins, theta 2.5, "
+                        "gross 12 h x 0.01 Hz (threshold 100), persistency k = 5",
+            "select_ms": sel, "bins_per_s": n_fft * n_bins / (sel * 1e-3),
+            "n_peaks": n_peaks, "after_gross": int(gb.shape[0]),
+            "after_persistency": int(pb.shape[0]),
+            "gross_veto_ms": statistics.median(g_ms),
+            "persistency_veto_ms": statistics.median(c_ms),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
+                         "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs"),
+                         "algorithmic": "8 B per bin (two binary32 spectra) + 12 B per peak "
+                                        "(bin, frequency) per selection",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % src,
+                         "duration_note": "CUDA events around the asynchronous "
+                                          "fh_peakmap_select with a workspace (mask, scan "
+                                          "and expand kernels)"}}
 
 
 def batched_vs_plain(fh, synth, torch):

@@ -281,11 +281,21 @@ int fh_plan_kernel_times(fh_plan plan, int64_t *n_groups, double *windows_ms,
  * division per bin; bin j of FFT i is a peak when R > theta and R is above
  * both R(j - 1) and R(j + 1) (so bins 0 and n_bins - 1, with one neighbour, are
  * never peaks).  Outputs offsets, bins, freq (nullable); *n_peaks (HOST).
- * n_fft <= 65535. */
+ * n_fft <= 65535.  workspace: NULL (the call takes its scratch stream-ordered)
+ * or DEVICE memory of at least fh_peakmap_select_workspace(n_fft, n_bins)
+ * bytes, 256-byte aligned, not used by anything else until the call's work on
+ * `stream` is done.  With n_peaks NULL the call is asynchronous (no
+ * synchronisation; with a workspace nothing is allocated, so it can be
+ * captured in a CUDA graph): the total is offsets[n_fft] on the device, and
+ * peaks beyond `capacity` are counted there but not written. */
 int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_t n_bins,
                       int64_t pitch, float theta, int64_t k0, double t_fft, int64_t *offsets,
                       int32_t *bins, double *freq, int64_t capacity, int64_t *n_peaks,
-                      void *stream);
+                      void *workspace, int64_t workspace_bytes, void *stream);
+
+/* Bytes of the selection's workspace (a bit per bin and a count per 4096-bin
+ * segment); -1 for negative sizes. */
+int64_t fh_peakmap_select_workspace(int32_t n_fft, int32_t n_bins);
 
 /* Wandering-line veto (Sec. "Removal of spectral wandering lines").  The gross
  * histogram hist (DEVICE, n_th x n_fh int32, written) counts the peaks per

@@ -33,10 +33,36 @@ namespace fh {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSegBins = 4096;     // bins of one FFT per selection block
-constexpr int kSegThreads = 1024;  // 4 bins per thread
+constexpr int kSegBins = 4096;    // bins of one FFT per selection block
+constexpr int kSegThreads = 256;  // 16 bins per thread
 constexpr int kSegWords = kSegBins / 32;
 constexpr int kScanThreads = 1024;
+
+// (k0 + b) / t_fft, the IEEE quotient.  When t_fft is a power of two the
+// quotient is the exact product with inv = 1 / t_fft (also exact), and a
+// binary64 multiply replaces the much slower division.
+struct FreqOf {
+    int64_t k0;
+    double t_fft, inv;
+    bool pow2;
+    __device__ __forceinline__ double operator()(int32_t b) const
+    {
+        const double x = (double)(k0 + b);
+        return pow2 ? __dmul_rn(x, inv) : __ddiv_rn(x, t_fft);
+    }
+};
+
+FreqOf make_freq_of(int64_t k0, double t_fft)
+{
+    int ex = 0;
+    const double m = std::frexp(t_fft, &ex);
+    FreqOf f;
+    f.k0 = k0;
+    f.t_fft = t_fft;
+    f.pow2 = m == 0.5 && ex > -1000 && ex < 1000;
+    f.inv = f.pow2 ? std::ldexp(1.0, 1 - ex) : 0.0;
+    return f;
+}
 
 // ---------------------------------------------------------------- selection
 struct SelArgs {
@@ -55,6 +81,12 @@ __device__ __forceinline__ float ratio_at(const float *sp, const float *sa, int 
     return (j >= 0 && j < n_bins) ? __fdiv_rn(__ldg(sp + j), __ldg(sa + j)) : 0.0f;
 }
 
+// A block takes 4096 bins of one FFT.  Loads: 16 bins per thread, as four
+// float4 per spectrum when the rows are 16-byte aligned (VEC), so that each
+// SM keeps ~256 KB of loads in flight; the ratios go to shared memory with one
+// halo bin on each side.  Flags: warp w takes words w, w + 8, ... (32 bins
+// each), one ballot per word.
+template <bool VEC>
 __global__ void __launch_bounds__(kSegThreads) select_mask_kernel(const SelArgs a)
 {
     __shared__ float r_s[kSegBins + 2];  // r_s[1 + k] = R(j0 + k); halos at 0 and kSegBins + 1
@@ -64,31 +96,58 @@ __global__ void __launch_bounds__(kSegThreads) select_mask_kernel(const SelArgs 
     const int j0 = seg * kSegBins;
     const float *sp = a.s_p + (int64_t)row * a.pitch;
     const float *sa = a.s_ar + (int64_t)row * a.pitch;
+    if (VEC) {
+        float4 p[4], q[4];
 #pragma unroll
-    for (int k = 0; k < kSegBins / kSegThreads; ++k) {
-        const int j = j0 + k * kSegThreads + tid;
-        r_s[1 + k * kSegThreads + tid] = ratio_at(sp, sa, j, a.n_bins);
+        for (int k = 0; k < 4; ++k) {
+            const int j = j0 + 4 * (k * kSegThreads + tid);
+            if (j + 3 < a.n_bins) {
+                p[k] = __ldg(reinterpret_cast<const float4 *>(sp + j));
+                q[k] = __ldg(reinterpret_cast<const float4 *>(sa + j));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int loc = 4 * (k * kSegThreads + tid);
+            const int j = j0 + loc;
+            if (j + 3 < a.n_bins) {
+                r_s[1 + loc] = __fdiv_rn(p[k].x, q[k].x);
+                r_s[2 + loc] = __fdiv_rn(p[k].y, q[k].y);
+                r_s[3 + loc] = __fdiv_rn(p[k].z, q[k].z);
+                r_s[4 + loc] = __fdiv_rn(p[k].w, q[k].w);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) r_s[1 + loc + e] = ratio_at(sp, sa, j + e, a.n_bins);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kSegBins / kSegThreads; ++k) {
+            const int loc = k * kSegThreads + tid;
+            r_s[1 + loc] = ratio_at(sp, sa, j0 + loc, a.n_bins);
+        }
     }
     if (tid == 0) r_s[0] = ratio_at(sp, sa, j0 - 1, a.n_bins);
     if (tid == 1) r_s[kSegBins + 1] = ratio_at(sp, sa, j0 + kSegBins, a.n_bins);
     __syncthreads();
     int cnt = 0;
 #pragma unroll
-    for (int k = 0; k < kSegBins / kSegThreads; ++k) {
-        const int loc = k * kSegThreads + tid;
+    for (int k = 0; k < kSegWords / (kSegThreads / 32); ++k) {
+        const int wl = k * (kSegThreads / 32) + warp;  // word of the segment
+        const int loc = wl * 32 + lane;
         const int j = j0 + loc;
         const float r = r_s[1 + loc];
         const bool f = j >= 1 && j <= a.n_bins - 2 && r > a.theta && r > r_s[loc] &&
                        r > r_s[loc + 2];
         const unsigned word = __ballot_sync(kFull, f);
-        const int w = (j0 + k * kSegThreads + warp * 32) >> 5;
+        const int w = seg * kSegWords + wl;
         if (lane == 0 && w < a.n_words) a.mask[(int64_t)row * a.n_words + w] = word;
         cnt += __popc(word);
     }
     if (lane == 0) warp_cnt[warp] = cnt;
     __syncthreads();
     if (warp == 0) {
-        int c = warp_cnt[lane];
+        int c = lane < kSegThreads / 32 ? warp_cnt[lane] : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
         if (lane == 0) a.seg_count[(int64_t)row * a.n_seg + seg] = c;
@@ -99,8 +158,8 @@ struct ExpandArgs {
     const uint32_t *mask;
     const int64_t *seg_base;  // [fft][seg] first output slot of the segment
     int32_t n_seg, n_words;
-    int64_t k0, capacity;
-    double t_fft;
+    int64_t capacity;
+    FreqOf fq;
     int32_t *bins;
     double *freq;
 };
@@ -132,7 +191,7 @@ __global__ void __launch_bounds__(kSegWords) select_expand_kernel(const ExpandAr
         if (pos < a.capacity) {
             const int b = w * 32 + bit;
             a.bins[pos] = b;
-            if (a.freq) a.freq[pos] = __ddiv_rn((double)(a.k0 + b), a.t_fft);
+            if (a.freq) a.freq[pos] = a.fq(b);
         }
         ++pos;
     }
@@ -192,29 +251,43 @@ __global__ void check_csr_kernel(const int64_t *o, int32_t n_fft, int64_t n_peak
     }
 }
 
+// floor(num / den) of the IEEE quotient: the product with inv = RN(1 / den)
+// differs from the quotient by a few units of 2^-53 relative, so when it lies
+// more than 1e-9 (relative, at least absolute) from an integer both have the
+// same floor; otherwise the division decides.
+__device__ __forceinline__ double floor_quot(double num, double den, double inv)
+{
+    const double q = __dmul_rn(num, inv);
+    const double fq = floor(q);
+    const double margin = 1e-9 * fmax(1.0, fabs(q));
+    if (q - fq > margin && fq + 1.0 - q > margin) return fq;
+    return floor(__ddiv_rn(num, den));
+}
+
 struct GrossCell {
     const double *t;
-    int64_t k0;
-    double t_fft, t0_h, dt_h, f0_h, df_h;
+    FreqOf fq;
+    double t0_h, dt_h, f0_h, df_h, inv_df;
     int32_t n_th, n_fh;
-    // the gross cell of a peak of bin b in FFT i, or -1 off the grid
+    // time cell of FFT i, or -1 off the grid
     __device__ __forceinline__ int64_t it_of(int i) const
     {
         const double x = floor(__ddiv_rn(__dsub_rn(__ldg(t + i), t0_h), dt_h));
         return (x >= 0.0 && x < (double)n_th) ? (int64_t)x : -1;
     }
-    __device__ __forceinline__ int64_t cell(int64_t it, int32_t b) const
+    // gross cell of a peak of bin b in time cell it, or -1 off the grid
+    __device__ __forceinline__ int32_t cell(int64_t it, int32_t b) const
     {
         if (it < 0) return -1;
-        const double f = __ddiv_rn((double)(k0 + b), t_fft);
-        const double y = floor(__ddiv_rn(__dsub_rn(f, f0_h), df_h));
-        return (y >= 0.0 && y < (double)n_fh) ? it * n_fh + (int64_t)y : -1;
+        const double y = floor_quot(__dsub_rn(fq(b), f0_h), df_h, inv_df);
+        return (y >= 0.0 && y < (double)n_fh) ? (int32_t)(it * n_fh + (int64_t)y) : -1;
     }
 };
 
-// warp per FFT: every peak on the grid adds one to its gross cell
+// warp per FFT: the gross cell of every peak (kept for the veto pass) and the
+// histogram (warp-aggregated atomics)
 __global__ void gross_hist_kernel(const int64_t *o, const int32_t *bins, int32_t n_fft,
-                                  int64_t n_peaks, GrossCell g, int32_t *hist)
+                                  int64_t n_peaks, GrossCell g, int32_t *cell, int32_t *hist)
 {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -222,10 +295,14 @@ __global__ void gross_hist_kernel(const int64_t *o, const int32_t *bins, int32_t
         int64_t lo, hi;
         peak_range(o, i, n_peaks, lo, hi);
         const int64_t it = g.it_of(i);
-        if (it < 0) continue;
-        for (int64_t q = lo + lane; q < hi; q += 32) {
-            const int64_t c = g.cell(it, __ldg(bins + q));
-            if (c >= 0) atomicAdd(hist + c, 1);
+        for (int64_t q0 = lo; q0 < hi; q0 += 32) {
+            const int64_t q = q0 + lane;
+            const int32_t c = q < hi ? g.cell(it, __ldg(bins + q)) : -1;
+            if (q < hi) cell[q] = c;
+            // neighbouring peaks of an FFT mostly share a cell: one atomic per
+            // distinct cell of the warp, adding its number of lanes
+            const unsigned same = __match_any_sync(kFull, c);
+            if (c >= 0 && lane == __ffs(same) - 1) atomicAdd(hist + c, __popc(same));
         }
     }
 }
@@ -340,12 +417,11 @@ robust_stats_kernel(const int32_t *hc, int32_t vmax, int64_t n_bins, int32_t *hd
 
 // which peaks stay: the gross cell holds at most `thr` peaks (or is off the grid)
 struct KeepGross {
-    GrossCell g;
-    const int32_t *hist;
+    const int32_t *cell, *hist;
     int32_t thr;
-    __device__ __forceinline__ bool operator()(int i, int64_t, int32_t b) const
+    __device__ __forceinline__ bool operator()(int, int64_t q, int32_t) const
     {
-        const int64_t c = g.cell(g.it_of(i), b);
+        const int32_t c = cell[q];
         return c < 0 || hist[c] <= thr;
     }
 };
@@ -384,7 +460,7 @@ __global__ void filter_count_kernel(const int64_t *o, const int32_t *bins, int32
 template <class Keep>
 __global__ void filter_write_kernel(const int64_t *o, const int32_t *bins, int32_t n_fft,
                                     int64_t n_peaks, Keep keep, const int64_t *o_out,
-                                    int64_t capacity, int64_t k0, double t_fft, int32_t *bins_out,
+                                    int64_t capacity, FreqOf fq, int32_t *bins_out,
                                     double *freq_out)
 {
     const int lane = threadIdx.x & 31;
@@ -402,7 +478,7 @@ __global__ void filter_write_kernel(const int64_t *o, const int32_t *bins, int32
             const int64_t at = pos + __popc(m & lt);
             if (k && at < capacity) {
                 bins_out[at] = b;
-                if (freq_out) freq_out[at] = __ddiv_rn((double)(k0 + b), t_fft);
+                if (freq_out) freq_out[at] = fq(b);
             }
             pos += __popc(m);
         }
@@ -454,7 +530,7 @@ int run_filter(const int64_t *o, const int32_t *bins, int32_t n_fft, int64_t n_p
     }
     if (e == cudaSuccess && n_fft > 0) {
         filter_write_kernel<<<grid, 256, 0, s>>>(o, bins, n_fft, n_peaks, keep, o_out, capacity,
-                                                 k0, t_fft, bins_out, freq_out);
+                                                 make_freq_of(k0, t_fft), bins_out, freq_out);
         e = cudaGetLastError();
     }
     int64_t total = 0;
@@ -492,13 +568,21 @@ using namespace fh;
 
 extern "C" {
 
+int64_t fh_peakmap_select_workspace(int32_t n_fft, int32_t n_bins)
+{
+    if (n_fft < 0 || n_bins < 0) return -1;
+    const int64_t n_seg = (n_bins + kSegBins - 1) / kSegBins;
+    const int64_t n_words = (n_bins + 31) / 32;
+    auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+    return up(4 * n_fft * n_words) + up(4 * n_fft * n_seg) + up(8 * (n_fft * n_seg + 1));
+}
+
 int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_t n_bins,
                       int64_t pitch, float theta, int64_t k0, double t_fft, int64_t *offsets,
                       int32_t *bins, double *freq, int64_t capacity, int64_t *n_peaks,
-                      void *stream)
+                      void *workspace, int64_t workspace_bytes, void *stream)
 {
-    if (!offsets || !n_peaks || (n_fft > 0 && n_bins > 0 && (!s_p || !s_ar)) ||
-        (capacity > 0 && !bins))
+    if (!offsets || (n_fft > 0 && n_bins > 0 && (!s_p || !s_ar)) || (capacity > 0 && !bins))
         return set_error(FH_ERR_INVALID_ARG, "null spectrum, offsets, bins or n_peaks");
     if (n_fft < 0 || n_fft > 65535 * 1024 || n_bins < 0 || pitch < n_bins || capacity < 0)
         return set_error(FH_ERR_INVALID_ARG, "need n_fft >= 0, n_bins >= 0, pitch >= n_bins, "
@@ -511,10 +595,10 @@ int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_
     const int32_t n_seg = (n_bins + kSegBins - 1) / kSegBins;
     const int32_t n_words = (n_bins + 31) / 32;
     if (n_fft == 0 || n_seg == 0) {
-        const cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(int64_t) * (n_fft + 1), s);
-        if (e == cudaSuccess) cudaStreamSynchronize(s);
+        cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(int64_t) * (n_fft + 1), s);
+        if (e == cudaSuccess && n_peaks) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync (peakmap)");
-        *n_peaks = 0;
+        if (n_peaks) *n_peaks = 0;
         return FH_OK;
     }
     if (n_fft > 65535) return set_error(FH_ERR_INVALID_ARG, "at most 65535 FFTs per call");
@@ -522,12 +606,31 @@ int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_
     uint32_t *mask = nullptr;
     int32_t *seg_count = nullptr;
     int64_t *seg_base = nullptr;
-    cudaError_t e = sc.get(&mask, (size_t)n_fft * n_words);
-    if (e == cudaSuccess) e = sc.get(&seg_count, (size_t)n_fft * n_seg);
-    if (e == cudaSuccess) e = sc.get(&seg_base, (size_t)n_fft * n_seg + 1);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync (peakmap)");
+    cudaError_t e = cudaSuccess;
+    const int64_t need = fh_peakmap_select_workspace(n_fft, n_bins);
+    if (workspace) {
+        if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+            return set_error(FH_ERR_INVALID_ARG, "workspace of %lld bytes (256-byte aligned) "
+                                                 "needed", (long long)need);
+        char *w = static_cast<char *>(workspace);
+        auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+        mask = reinterpret_cast<uint32_t *>(w);
+        seg_count = reinterpret_cast<int32_t *>(w + up(4 * (int64_t)n_fft * n_words));
+        seg_base = reinterpret_cast<int64_t *>(w + up(4 * (int64_t)n_fft * n_words) +
+                                               up(4 * (int64_t)n_fft * n_seg));
+    } else {
+        e = sc.get(&mask, (size_t)n_fft * n_words);
+        if (e == cudaSuccess) e = sc.get(&seg_count, (size_t)n_fft * n_seg);
+        if (e == cudaSuccess) e = sc.get(&seg_base, (size_t)n_fft * n_seg + 1);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync (peakmap)");
+    }
     SelArgs a{s_p, s_ar, pitch, n_fft, n_bins, n_seg, n_words, theta, mask, seg_count};
-    select_mask_kernel<<<dim3(n_seg, n_fft), kSegThreads, 0, s>>>(a);
+    const bool vec = ((reinterpret_cast<uintptr_t>(s_p) | reinterpret_cast<uintptr_t>(s_ar)) &
+                      15u) == 0 && (pitch & 3) == 0;
+    if (vec)
+        select_mask_kernel<true><<<dim3(n_seg, n_fft), kSegThreads, 0, s>>>(a);
+    else
+        select_mask_kernel<false><<<dim3(n_seg, n_fft), kSegThreads, 0, s>>>(a);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         scan_counts_kernel<<<1, kScanThreads, 0, s>>>(seg_count, (int64_t)n_fft * n_seg,
@@ -535,13 +638,15 @@ int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        ExpandArgs x{mask, seg_base, n_seg, n_words, k0, capacity, t_fft, bins, freq};
+        ExpandArgs x{mask, seg_base, n_seg, n_words, capacity, make_freq_of(k0, t_fft), bins,
+                     freq};
         select_expand_kernel<<<dim3(n_seg, n_fft), kSegWords, 0, s>>>(x);
         e = cudaGetLastError();
     }
+    if (e != cudaSuccess) return cuda_error(e, "peak selection");
+    if (!n_peaks) return FH_OK;  // asynchronous: the total is offsets[n_fft]
     int64_t total = 0;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&total, offsets + n_fft, sizeof(total), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(&total, offsets + n_fft, sizeof(total), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "peak selection");
     *n_peaks = total;
@@ -576,13 +681,16 @@ int fh_peakmap_gross_veto(const double *t, const int64_t *offsets, const int32_t
         check_csr_kernel<<<(n_fft + 256) / 256, 256, 0, s>>>(offsets, n_fft, n_peaks, err);
         e = cudaGetLastError();
     }
-    GrossCell g{t, k0, t_fft, t0_h, dt_h, f0_h, df_h, n_th, n_fh};
+    GrossCell g{t, make_freq_of(k0, t_fft), t0_h, dt_h, f0_h, df_h, 1.0 / df_h, n_th, n_fh};
+    int32_t *cell = nullptr;
+    if (e == cudaSuccess) e = sc.get(&cell, (size_t)n_peaks);
     if (e == cudaSuccess && n_fft > 0) {
-        gross_hist_kernel<<<warp_grid(n_fft), 256, 0, s>>>(offsets, bins, n_fft, n_peaks, g, hist);
+        gross_hist_kernel<<<warp_grid(n_fft), 256, 0, s>>>(offsets, bins, n_fft, n_peaks, g, cell,
+                                                           hist);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_error(e, "gross histogram");
-    return run_filter(offsets, bins, n_fft, n_peaks, KeepGross{g, hist, threshold}, k0, t_fft,
+    return run_filter(offsets, bins, n_fft, n_peaks, KeepGross{cell, hist, threshold}, k0, t_fft,
                       offsets_out, bins_out, freq_out, capacity, n_out, err, sc, s);
 }
 

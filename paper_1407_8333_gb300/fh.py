@@ -95,7 +95,8 @@ _SIGS = {
     "fh_plan_launches": ([_P], _i64),
     "fh_set_weights": ([_P, _P, _i32, _i32, _P], ctypes.c_int),
     "fh_peakmap_select": ([_P, _P, _i32, _i32, _i64, ctypes.c_float, _i64, _f64, _P, _P, _P,
-                           _i64, _P, _P], ctypes.c_int),
+                           _i64, _P, _P, _i64, _P], ctypes.c_int),
+    "fh_peakmap_select_workspace": ([_i32, _i32], _i64),
     "fh_peakmap_gross_veto": ([_P, _P, _P, _i32, _i64, _i64, _f64, _f64, _f64, _i32, _f64, _f64,
                                _i32, _i32, _P, _P, _P, _P, _i64, _P, _P], ctypes.c_int),
     "fh_peakmap_persistency_veto": ([_P, _P, _i32, _i64, _i32, _f64, _i64, _f64, _P, _P, _P, _P,
@@ -293,14 +294,35 @@ def _dev_ptr(x):
     return None if x is None else ctypes.c_void_p(x.data_ptr())
 
 
+def _ws_bytes(w) -> int:
+    return 0 if w is None else int(w.numel() * w.element_size())
+
+
+def fh_peakmap_select_workspace(n_fft: int, n_bins: int) -> int:
+    return int(load().fh_peakmap_select_workspace(int(n_fft), int(n_bins)))
+
+
 def fh_peakmap_select(s_p, s_ar, theta: float, k0: int, t_fft: float, capacity: int = None,
-                      want_freq: bool = True, stream=None):
+                      want_freq: bool = True, stream=None, out=None, workspace=None):
     """Peaks of device spectra (torch float32, (n_fft, n_bins), rows contiguous).
-    Returns (offsets int64, bins int32, freq float64 or None) on the device."""
+    Returns (offsets int64, bins int32, freq float64 or None) on the device.
+    With ``out`` = (offsets, bins, freq) preallocated, the call is asynchronous
+    and returns those buffers whole (the total is offsets[n_fft]); ``workspace``
+    (a device uint8 tensor of fh_peakmap_select_workspace bytes) avoids the
+    call's own scratch allocation."""
     import torch
     n_fft, n_bins = int(s_p.shape[0]), int(s_p.shape[1])
     if s_p.stride(1) != 1 or s_ar.stride(1) != 1 or s_p.stride(0) != s_ar.stride(0):
         raise ValueError("s_p and s_ar need unit-stride rows of the same pitch")
+    if out is not None:
+        offsets, bins, freq = out
+        _check(load().fh_peakmap_select(_dev_ptr(s_p), _dev_ptr(s_ar), n_fft, n_bins,
+                                        int(s_p.stride(0)), float(theta), int(k0), float(t_fft),
+                                        _dev_ptr(offsets), _dev_ptr(bins), _dev_ptr(freq),
+                                        int(bins.shape[0]), None, _dev_ptr(workspace),
+                                        _ws_bytes(workspace), _stream(stream)),
+               "fh_peakmap_select")
+        return offsets, bins, freq
     cap = int(capacity) if capacity is not None else max(1, n_fft * max(0, n_bins - 1) // 2)
     dev = s_p.device
     offsets = torch.empty(n_fft + 1, dtype=torch.int64, device=dev)
@@ -310,7 +332,8 @@ def fh_peakmap_select(s_p, s_ar, theta: float, k0: int, t_fft: float, capacity: 
     _check(load().fh_peakmap_select(_dev_ptr(s_p), _dev_ptr(s_ar), n_fft, n_bins,
                                     int(s_p.stride(0)), float(theta), int(k0), float(t_fft),
                                     _dev_ptr(offsets), _dev_ptr(bins), _dev_ptr(freq), cap,
-                                    ctypes.byref(n), _stream(stream)), "fh_peakmap_select")
+                                    ctypes.byref(n), _dev_ptr(workspace), _ws_bytes(workspace),
+                                    _stream(stream)), "fh_peakmap_select")
     k = n.value
     return offsets, bins[:k], (freq[:k] if freq is not None else None)
 
@@ -357,8 +380,9 @@ def fh_peakmap_persistency_veto(offsets, bins, n_bins: int, k_sigma: float, k0: 
     n = ctypes.c_int64(0)
     _check(load().fh_peakmap_persistency_veto(_dev_ptr(offsets), _dev_ptr(bins), n_fft, n_peaks,
                                               int(n_bins), float(k_sigma), int(k0), float(t_fft),
-                                              _dev_ptr(hist), ctypes.cast(stats, _P), _dev_ptr(o2), _dev_ptr(b2),
-                                              _dev_ptr(f2), cap, ctypes.byref(n),
+                                              _dev_ptr(hist), ctypes.cast(stats, _P),
+                                              _dev_ptr(o2), _dev_ptr(b2), _dev_ptr(f2), cap,
+                                              ctypes.byref(n),
                                               _stream(stream)), "fh_peakmap_persistency_veto")
     k = n.value
     return o2, b2[:k], (f2[:k] if f2 is not None else None), hist, tuple(stats)

@@ -179,3 +179,41 @@ def test_full_size_pipeline_matches_oracle(fh, pm):
     # the disturbances are what the vetoes removed
     assert set(np.nonzero(wh2 > thr)[0]) == set(int(x) for x in s.const_bins)
     assert (wh > p["gross_thr"]).any()
+
+
+def test_select_asynchronous_form(fh, pm):
+    """With preallocated outputs the call does not synchronise; the total is
+    offsets[n_fft] and peaks beyond the capacity are counted, not written;
+    with or without a caller's workspace."""
+    import torch
+    s = synth.spectra_case(34, 23, 5000, wander_amp=30.0, wander_f=(50.05, 50.3), wander_width=7)
+    wo, wb = pm.select_peaks(s.s_p, s.s_ar, 2.5)
+    for cap in (len(wb) + 5, len(wb) // 2):
+        out = (torch.empty(24, dtype=torch.int64, device="cuda"),
+               torch.full((cap,), -1, dtype=torch.int32, device="cuda"),
+               torch.empty(cap, dtype=torch.float64, device="cuda"))
+        ws = torch.empty(fh.fh_peakmap_select_workspace(23, 5000), dtype=torch.uint8,
+                         device="cuda") if cap % 2 else None
+        o, b, f = fh.fh_peakmap_select(dev(s.s_p), dev(s.s_ar), 2.5, s.k0, s.t_fft, out=out,
+                                       workspace=ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(o), wo)
+        k = min(cap, len(wb))
+        assert np.array_equal(host(b)[:k], wb[:k])
+        assert np.all(host(b)[k:] == -1)
+        assert np.array_equal(host(f)[:k], pm.peak_frequencies(wb[:k], s.k0, s.t_fft))
+
+
+def test_frequencies_for_a_t_fft_that_is_not_a_power_of_two(fh, pm):
+    """A power-of-two T_FFT takes an exact multiply, any other the division;
+    both give the IEEE quotient (k0 + b) / T_FFT, bit for bit."""
+    for t_fft in (1800.0, 1024.0, 3.0):
+        s = synth.spectra_case(35, 9, 700, t_fft=t_fft, f_lo=20.0)
+        check_select(fh, pm, s, 2.0)
+        o, b = pm.select_peaks(s.s_p, s.s_ar, 2.0)
+        go, gb, gf, _ = fh.fh_peakmap_gross_veto(dev(s.t), dev(o), dev(b), s.k0, s.t_fft,
+                                                 0.0, 5000.0, 4, 20.0, 0.05, 10, 3)
+        wo, wb, _ = pm.gross_veto(s.t, o, b, s.k0, s.t_fft, 0.0, 5000.0, 4, 20.0, 0.05, 10, 3)
+        assert np.array_equal(host(gb), wb)
+        assert np.array_equal(host(gf).view(np.uint64),
+                              pm.peak_frequencies(wb, s.k0, s.t_fft).view(np.uint64))
