@@ -30,6 +30,7 @@ import threading
 
 import numpy as np
 
+from . import coincidence  # noqa: F401  (candidate clustering and coincidences)
 from . import peakmap  # noqa: F401  (peakmap construction and cleaning)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

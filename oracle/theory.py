@@ -9,6 +9,8 @@ Each function restates one equation of the paper in binary64:
 * ``n_thr_gauss``  count threshold for a false-alarm probability (Eq. nthr_gauss)
 * ``cr_thr``       CR threshold for N_cand of N_tot points (Eq. crthr)
 * ``n_tot``        number of coarse parameter-space points (Eq. Ntot, Sec. VIII)
+* ``n_coinc``      expected number of candidates of set 1 with at least one
+                   coincidence in set 2 (App. "Theory of coincidences")
 * ``gross_points`` points N of one gross-histogram cell and its noise mean and
                    standard deviation E_H = N p0, sigma_H = sqrt(N p0 (1 - p0))
                    (Sec. "Removal of spectral wandering lines")
@@ -72,3 +74,12 @@ def gross_points(dt_h: float, df_h: float, t_fft: float, interlaced: bool = True
 def gross_noise(n_points: float, p: float) -> tuple:
     """(E_H, sigma_H) = (N p0, sqrt(N p0 (1 - p0))) of a noise-only gross cell."""
     return n_points * p, math.sqrt(n_points * p * (1.0 - p))
+
+
+def n_coinc(n1: int, n2: int, w, m) -> float:
+    """App. "Theory of coincidences": N_coinc,1 = N1 (1 - exp(-N2 prod_j w_j / m_j)),
+    w_j the total coincidence window and m_j the cells of parameter j."""
+    prod = 1.0
+    for wj, mj in zip(w, m):
+        prod *= wj / mj
+    return n1 * (1.0 - math.exp(-n2 * prod))

@@ -594,3 +594,90 @@ def peakmap_workload(seed: int = 41) -> Spectra:
                         signal_lambda=3.0, signal_f0=50.3, signal_fdot=-1e-9,
                         wander_amp=40.0, wander_f=(50.55, 50.75), wander_width=15,
                         const_lines=(50.123, 50.877), const_amp=40.0, const_frac=0.8)
+
+
+# --------------------------------------------------------------------------
+# Candidate sets (clustering and coincidences)
+# --------------------------------------------------------------------------
+_S_CAND = 12
+CAND_FIELDS = ("lam", "beta", "f", "fdot", "dlam", "dbeta", "df", "dfdot")
+
+
+def candidates_on_grid(seed: int, stream: int, n: int, m) -> np.ndarray:
+    """n candidates drawn uniformly on a grid of m = (m_lam, m_beta, m_f,
+    m_fdot) cells, as (n, 8) float64 rows in CAND_FIELDS order: every width is
+    one cell; longitude cells cover the circle (value = cell 2 pi / m_lam), the
+    other values are the cell indices."""
+    u = uniform(seed, 100 + stream, np.arange(4 * n)).reshape(4, n)
+    cells = [np.floor(u[q] * m[q]) for q in range(4)]
+    out = np.empty((n, 8))
+    out[:, 0] = cells[0] * (2.0 * math.pi / m[0])
+    out[:, 1], out[:, 2], out[:, 3] = cells[1], cells[2], cells[3]
+    out[:, 4] = 2.0 * math.pi / m[0]
+    out[:, 5:8] = 1.0
+    return out
+
+
+def candidate_set(seed: int, stream: int, n: int, f_lo: float = 100.0, band: float = 1.0,
+                  t_fft: float = 1024.0, n_d: float = None, fdot_step: float = None,
+                  fdot_rows: int = 100, clusters: int = 0, cluster_size: int = 8,
+                  signals: np.ndarray = None, jitter: float = 0.5) -> np.ndarray:
+    """A set of n candidates in the shape of the search's output, (n, 8) rows
+    in CAND_FIELDS order: sky directions uniform on the sphere with the coarse
+    widths of the App. A2 grid at Doppler number n_d (beta: 1 / (N_D |sin beta|),
+    at most pi / 8; lambda: 2 pi / ceil(2 pi N_D cos beta)); f uniform in the
+    band, width 1 / T_FFT; fdot on fdot_rows rows of fdot_step below zero.
+    ``clusters`` groups of ``cluster_size`` candidates within about a bin of a
+    seed candidate, and ``signals`` (rows of lam, beta, f, fdot) repeated with
+    up to ``jitter`` bins of noise, replace the first rows."""
+    if n_d is None:
+        n_d = doppler_number(f_lo + band, t_fft)
+    if fdot_step is None:
+        fdot_step = 1.0 / (t_fft * 3.15e7)
+    u = uniform(seed, _S_CAND + stream, np.arange(6 * n)).reshape(6, n)
+    lam = u[0] * 2.0 * math.pi
+    beta = np.arcsin(u[1] * 2.0 - 1.0)
+    f = f_lo + u[2] * band
+    fdot = -np.floor(u[3] * fdot_rows) * fdot_step
+
+    def widths(b):
+        db = np.minimum(1.0 / (n_d * np.maximum(np.abs(np.sin(b)), 1e-3)), math.pi / 8)
+        dl = 2.0 * math.pi / np.maximum(1.0, np.ceil(2.0 * math.pi * n_d * np.cos(b) - 1e-12))
+        return dl, db
+
+    rows = []
+    k = 0
+    sig = np.zeros((0, 4)) if signals is None else np.asarray(signals, np.float64).reshape(-1, 4)
+    for s in sig:
+        rows.append(s)
+    for c in range(clusters):
+        rows.append(np.array([lam[c], beta[c], f[c], fdot[c]]))
+        for q in range(cluster_size - 1):
+            rows.append(None)   # filled below, near the seed
+    out = np.empty((n, 8))
+    out[:, 0], out[:, 1], out[:, 2], out[:, 3] = lam, beta, f, fdot
+    j = uniform(seed, _S_CAND + 50 + stream, np.arange(4 * n)).reshape(4, n) * 2.0 - 1.0
+    seed_row = None
+    for r, v in enumerate(rows[:n]):
+        if v is not None:
+            out[r, :4] = v
+            seed_row = out[r, :4].copy()
+            if r < len(sig):
+                seed_row = None
+        elif seed_row is not None:
+            dl, db = widths(seed_row[1])
+            out[r, 0] = np.mod(seed_row[0] + j[0, r] * dl, 2.0 * math.pi)
+            out[r, 1] = np.clip(seed_row[1] + j[1, r] * db, -math.pi / 2, math.pi / 2)
+            out[r, 2] = seed_row[2] + j[2, r] / t_fft
+            out[r, 3] = seed_row[3] + np.round(j[3, r]) * fdot_step
+    dl, db = widths(out[:, 1])
+    for r in range(min(len(sig), n)):
+        out[r, 0] = np.mod(out[r, 0] + jitter * j[0, r] * dl[r], 2.0 * math.pi)
+        out[r, 1] = np.clip(out[r, 1] + jitter * j[1, r] * db[r], -math.pi / 2, math.pi / 2)
+        out[r, 2] += jitter * j[2, r] / t_fft
+        out[r, 3] += np.round(jitter * j[3, r]) * fdot_step
+    dl, db = widths(out[:, 1])
+    out[:, 4], out[:, 5] = dl, db
+    out[:, 6] = 1.0 / t_fft
+    out[:, 7] = fdot_step
+    return out
