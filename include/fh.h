@@ -324,6 +324,41 @@ int fh_peakmap_persistency_veto(const int64_t *offsets, const int32_t *bins, int
                                 int64_t *offsets_out, int32_t *bins_out, double *freq_out,
                                 int64_t capacity, int64_t *n_out, void *stream);
 
+/* ---- candidate clustering and coincidences --------------------------------- */
+/* A candidate's parameters (sky position in ecliptic longitude and latitude,
+ * radians; frequency, Hz; spin-down, Hz/s) and the widths of its coarse bins
+ * in each (the longitude width depends on the latitude).  64 bytes. */
+typedef struct fh_cand_params {
+    double lam, beta, f, fdot;
+    double dlam, dbeta, df, dfdot;
+} fh_cand_params;
+
+/* Clusters of one candidate set (Sec. "Candidate clustering and
+ * coincidences", Eq. norm).  The distance of two candidates is
+ * d = sqrt(((k_lam^2 + k_beta^2) + k_f^2) + k_fdot^2), k_x = |x2 - x1| /
+ * ((dx1 + dx2) * 0.5) (binary64, in this order; a longitude difference above
+ * pi is taken as 2 pi - it).  Candidates linked by chains of d <= d_max form a
+ * cluster; label[i] (DEVICE, n int32, written) is the smallest index of i's
+ * cluster; *n_clusters (HOST).  cands: DEVICE, n records, values finite and
+ * widths > 0 (else FH_ERR_INVALID_ARG).  Synchronises the stream. */
+int fh_cluster(const fh_cand_params *cands, int32_t n, double d_max, int32_t *label,
+               int32_t *n_clusters, void *stream);
+
+/* Coincident pairs of two candidate sets (Sec. "Candidate clustering and
+ * coincidences"; App. "Theory of coincidences").  Frequencies are referred to
+ * the common time t_c first, f + fdot (t_c - t_ref) (the set's own reference
+ * time); candidate i of set 1 and j of set 2 coincide when k_lam <= win[0],
+ * k_beta <= win[1], k_f <= win[2] and k_fdot <= win[3] (k as for fh_cluster;
+ * win HOST, 4 windows in bins, the sum of the two sets' half-windows).
+ * pairs (DEVICE, 2 x capacity int32, written): (i, j) in (i, j) order;
+ * *n_pairs (HOST) the count (more than capacity: FH_ERR_CAPACITY, the list is
+ * then incomplete); n_match1 / n_match2 (DEVICE, nullable) the number of
+ * partners of each candidate.  Synchronises the stream. */
+int fh_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
+                    const fh_cand_params *c2, int32_t n2, double t_ref2, double t_c,
+                    const double *win, int32_t *pairs, int64_t capacity, int64_t *n_pairs,
+                    int32_t *n_match1, int32_t *n_match2, void *stream);
+
 /* ---- refined grid around coarse candidates -------------------------------- */
 
 /* Refined-grid search (Sec. "Refined Grid in the parameter space"): one

@@ -1,0 +1,505 @@
+// Candidate clustering and coincidences on the GPU (Sec. "Candidate clustering
+// and coincidences", Eq. norm; App. "Theory of coincidences").
+//
+//   fh_cluster       single-linkage clusters of one candidate set: candidates
+//                    whose distance (Eq. norm, in mean coarse-bin widths) is at
+//                    most d_max are linked; every cluster is labelled by its
+//                    smallest member
+//   fh_coincidences  the coincident pairs of two sets: frequencies referred to a
+//                    common time, every parameter within its window in bins
+//
+// Both bucket candidates by frequency: a bucket is at least as wide as the
+// largest frequency difference a link (or a coincidence) allows, d_max
+// max(df) (w_f max(df)), so a candidate's partners lie in its own bucket and
+// the two beside it.  Buckets are built by a count, the shared exclusive scan
+// and a scatter.
+//
+// Clustering links each candidate to the larger-index candidates of those
+// buckets through a lock-free union-find: a root is only ever hung below a
+// smaller root (one compare-and-swap), so the root of every cluster is its
+// smallest member and the labels do not depend on the order of the links.
+// Coincidences count each set-1 candidate's partners, scan the counts into
+// output offsets, then write the partners and sort each candidate's short list
+// by index, so the pairs come out in (i, j) order.
+//
+// Arithmetic: every k and the distance are the binary64 operations of the
+// definition in the order written (|x2 - x1|, 2 pi - that above pi for
+// longitudes, divided by (w1 + w2) * 0.5; ((k_l^2 + k_b^2) + k_f^2) + k_fd^2 and
+// its square root), so every link and every coincidence is decided exactly as
+// the definition decides it.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "fh_internal.h"
+
+namespace fh {
+namespace {
+
+constexpr double kPi = 3.141592653589793;
+constexpr double kTwoPi = 6.283185307179586;
+constexpr int kMaxBuckets = 1 << 22;
+constexpr int kUnionLimit = 1 << 20;  // retries of one union (each follows another's progress)
+
+__device__ __forceinline__ double bins_apart(double x1, double x2, double w1, double w2,
+                                             bool wrap)
+{
+    double a = fabs(__dsub_rn(x2, x1));
+    if (wrap && a > kPi) a = __dsub_rn(kTwoPi, a);
+    return __ddiv_rn(a, __dmul_rn(__dadd_rn(w1, w2), 0.5));
+}
+
+__device__ __forceinline__ double norm_distance(const fh_cand_params &a, const fh_cand_params &b,
+                                                double fa, double fb)
+{
+    const double kl = bins_apart(a.lam, b.lam, a.dlam, b.dlam, true);
+    const double kb = bins_apart(a.beta, b.beta, a.dbeta, b.dbeta, false);
+    const double kf = bins_apart(fa, fb, a.df, b.df, false);
+    const double kd = bins_apart(a.fdot, b.fdot, a.dfdot, b.dfdot, false);
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(kl, kl), __dmul_rn(kb, kb)),
+                                          __dmul_rn(kf, kf)),
+                                __dmul_rn(kd, kd)));
+}
+
+// order-preserving map of doubles to unsigned 64-bit keys (for atomic min / max)
+__device__ __forceinline__ unsigned long long okey(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__host__ __device__ __forceinline__ double from_okey(unsigned long long k)
+{
+    const unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+#endif
+}
+
+__device__ __forceinline__ bool cand_ok(const fh_cand_params &c)
+{
+    return isfinite(c.lam) && isfinite(c.beta) && isfinite(c.f) && isfinite(c.fdot) &&
+           c.dlam > 0.0 && c.dbeta > 0.0 && c.df > 0.0 && c.dfdot > 0.0 && isfinite(c.dlam) &&
+           isfinite(c.dbeta) && isfinite(c.df) && isfinite(c.dfdot);
+}
+
+// Range of the (shifted) frequencies and the largest frequency width.  rng:
+// [0] okey(min f), [1] okey(max f), [2] okey(max df).  Non-finite values or
+// widths <= 0 are flagged.
+__global__ void range_kernel(const fh_cand_params *c, const double *fs, int32_t n,
+                             unsigned long long *rng, int32_t *err, bool widths_only)
+{
+    unsigned long long lo = ~0ull, hi = 0ull, wd = 0ull;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const fh_cand_params x = c[i];
+        bad = bad || !cand_ok(x);
+        const double f = fs ? fs[i] : x.f;
+        if (!widths_only) {
+            lo = min(lo, okey(f));
+            hi = max(hi, okey(f));
+        }
+        wd = max(wd, okey(x.df));
+    }
+    if (!widths_only) {
+        atomicMin(rng + 0, lo);
+        atomicMax(rng + 1, hi);
+    }
+    atomicMax(rng + 2, wd);
+    if (bad) atomicOr(err, kErrInvalid);
+}
+
+// bucket width: at least `reach` x max(df) (the largest frequency difference a
+// link or a coincidence allows) and wide enough for nb buckets to span the
+// range; 1e-6 wider so that two frequencies one width apart never land two
+// buckets apart after rounding
+struct Buckets {
+    double f0, w;
+    int32_t nb;
+    __device__ __forceinline__ long long raw(double f) const
+    {
+        const double x = floor(__ddiv_rn(__dsub_rn(f, f0), w));
+        return x < -1.0 ? -2 : (x > (double)nb ? (long long)nb + 1 : (long long)x);
+    }
+};
+
+__global__ void bucket_setup_kernel(const unsigned long long *rng, int32_t nb, double reach,
+                                    const unsigned long long *rng_w, Buckets *out)
+{
+    const double lo = from_okey(rng[0]), hi = from_okey(rng[1]);
+    const double wd = from_okey(rng_w[2]);
+    // an infinite width (an enormous window) puts everything in one bucket,
+    // which is right; zero or NaN (no candidates, degenerate input) takes 1
+    double w = fmax(reach * wd, (hi - lo) / (double)nb);
+    if (!(w > 0.0)) w = 1.0;
+    Buckets b;
+    b.f0 = isfinite(lo) ? lo : 0.0;
+    b.w = w * (1.0 + 1e-6);
+    b.nb = nb;
+    *out = b;
+}
+
+__global__ void bucket_count_kernel(const double *fs, int32_t n, const Buckets *bk, int32_t *bkt,
+                                    int32_t *cnt)
+{
+    const Buckets b = *bk;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const long long r = b.raw(fs[i]);
+        const int32_t q = (int32_t)min(max(r, 0ll), (long long)b.nb - 1);
+        bkt[i] = q;
+        atomicAdd(cnt + q, 1);
+    }
+}
+
+__global__ void bucket_scatter_kernel(const int32_t *bkt, int32_t n, const int64_t *start,
+                                      int32_t *cursor, int32_t *order)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t q = bkt[i];
+        order[start[q] + atomicAdd(cursor + q, 1)] = i;
+    }
+}
+
+// ---------------------------------------------------------------- clustering
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, int32_t *err)
+{
+    for (int it = 0; it < kUnionLimit; ++it) {
+        const int32_t p = ((volatile int32_t *)parent)[x];
+        if (p == x) return x;
+        const int32_t gp = ((volatile int32_t *)parent)[p];
+        if (gp != p) atomicCAS(parent + x, p, gp);  // path halving: point to an ancestor
+        x = gp;
+    }
+    atomicOr(err, kErrRange);
+    return x;
+}
+
+__device__ __forceinline__ void uf_union(int32_t *parent, int32_t a, int32_t b, int32_t *err)
+{
+    for (int it = 0; it < kUnionLimit; ++it) {
+        const int32_t ra = uf_find(parent, a, err), rb = uf_find(parent, b, err);
+        if (ra == rb) return;
+        const int32_t lo = min(ra, rb), hi = max(ra, rb);
+        // hang the larger root below the smaller one, unless it stopped being a root
+        if (atomicCAS(parent + hi, hi, lo) == hi) return;
+        a = lo;
+        b = hi;
+    }
+    atomicOr(err, kErrRange);
+}
+
+__global__ void link_kernel(const fh_cand_params *c, int32_t n, double d_max, const int32_t *bkt,
+                            const int64_t *start, const int32_t *order, int32_t nb,
+                            int32_t *parent, int32_t *err)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const fh_cand_params a = c[i];
+        const int32_t q = bkt[i];
+        for (int32_t qq = max(q - 1, 0); qq <= min(q + 1, nb - 1); ++qq) {
+            for (int64_t p = start[qq]; p < start[qq + 1]; ++p) {
+                const int32_t j = order[p];
+                if (j <= i) continue;
+                const fh_cand_params b = c[j];
+                if (norm_distance(a, b, a.f, b.f) <= d_max) uf_union(parent, i, j, err);
+            }
+        }
+    }
+}
+
+__global__ void init_parent_kernel(int32_t *parent, int32_t n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        parent[i] = i;
+}
+
+__global__ void finish_labels_kernel(int32_t *parent, int32_t n, int32_t *label,
+                                     int32_t *n_roots, int32_t *err)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t r = uf_find(parent, i, err);
+        label[i] = r;
+        if (r == i) atomicAdd(n_roots, 1);
+    }
+}
+
+// ---------------------------------------------------------------- coincidences
+__global__ void shift_kernel(const fh_cand_params *c, int32_t n, double dt, double *fs)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        fs[i] = __dadd_rn(c[i].f, __dmul_rn(c[i].fdot, dt));
+}
+
+struct CoinArgs {
+    const fh_cand_params *c1, *c2;
+    const double *f1, *f2;
+    int32_t n1, n2;
+    double w_lam, w_beta, w_f, w_fdot;
+    const Buckets *bk;
+    const int64_t *start;
+    const int32_t *order;
+};
+
+__device__ __forceinline__ bool coincide(const CoinArgs &a, const fh_cand_params &x, double fx,
+                                         int32_t j)
+{
+    const fh_cand_params y = a.c2[j];
+    return bins_apart(x.lam, y.lam, x.dlam, y.dlam, true) <= a.w_lam &&
+           bins_apart(x.beta, y.beta, x.dbeta, y.dbeta, false) <= a.w_beta &&
+           bins_apart(fx, a.f2[j], x.df, y.df, false) <= a.w_f &&
+           bins_apart(x.fdot, y.fdot, x.dfdot, y.dfdot, false) <= a.w_fdot;
+}
+
+__global__ void coin_count_kernel(const CoinArgs a, int32_t *cnt1, int32_t *cnt2)
+{
+    const Buckets b = *a.bk;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n1; i += gridDim.x * blockDim.x) {
+        const fh_cand_params x = a.c1[i];
+        const double fx = a.f1[i];
+        const long long r = b.raw(fx);
+        int c = 0;
+        for (long long qq = max(r - 1, 0ll); qq <= min(r + 1, (long long)b.nb - 1); ++qq)
+            for (int64_t p = a.start[qq]; p < a.start[qq + 1]; ++p) {
+                const int32_t j = a.order[p];
+                if (coincide(a, x, fx, j)) {
+                    ++c;
+                    if (cnt2) atomicAdd(cnt2 + j, 1);
+                }
+            }
+        cnt1[i] = c;
+    }
+}
+
+__global__ void coin_write_kernel(const CoinArgs a, const int64_t *off, int64_t capacity,
+                                  int32_t *pairs)
+{
+    const Buckets b = *a.bk;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n1; i += gridDim.x * blockDim.x) {
+        const fh_cand_params x = a.c1[i];
+        const double fx = a.f1[i];
+        const long long r = b.raw(fx);
+        const int64_t o0 = off[i];
+        int64_t o = o0;
+        for (long long qq = max(r - 1, 0ll); qq <= min(r + 1, (long long)b.nb - 1); ++qq)
+            for (int64_t p = a.start[qq]; p < a.start[qq + 1]; ++p) {
+                const int32_t j = a.order[p];
+                if (coincide(a, x, fx, j)) {
+                    if (o < capacity) {
+                        // insertion into the candidate's list, kept sorted by j
+                        int64_t q = o;
+                        while (q > o0 && pairs[2 * (q - 1) + 1] > j) {
+                            pairs[2 * q] = i;
+                            pairs[2 * q + 1] = pairs[2 * (q - 1) + 1];
+                            --q;
+                        }
+                        pairs[2 * q] = i;
+                        pairs[2 * q + 1] = j;
+                    }
+                    ++o;
+                }
+            }
+    }
+}
+
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> bufs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    cudaError_t get(T **p, size_t n)
+    {
+        void *q = nullptr;
+        const cudaError_t e = cudaMallocAsync(&q, (n ? n : 1) * sizeof(T), s);
+        if (e == cudaSuccess) bufs.push_back(q);
+        *p = static_cast<T *>(q);
+        return e;
+    }
+    ~Scratch()
+    {
+        for (void *b : bufs) cudaFreeAsync(b, s);
+    }
+};
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
+
+// buckets of n candidates by the frequencies fs: bkt, start (nb + 1), order
+cudaError_t build_buckets(const double *fs, int32_t n, int32_t nb, const Buckets *bk,
+                          int32_t *bkt, int64_t *start, int32_t *order, Scratch &sc,
+                          cudaStream_t s)
+{
+    int32_t *cnt = nullptr, *cursor = nullptr;
+    cudaError_t e = sc.get(&cnt, (size_t)nb);
+    if (e == cudaSuccess) e = sc.get(&cursor, (size_t)nb);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * (size_t)nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, 4 * (size_t)nb, s);
+    if (e == cudaSuccess && n > 0) {
+        bucket_count_kernel<<<grid_for(n), 256, 0, s>>>(fs, n, bk, bkt, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_exclusive_scan(cnt, nb, start, 1, nullptr, s);
+    if (e == cudaSuccess && n > 0) {
+        bucket_scatter_kernel<<<grid_for(n), 256, 0, s>>>(bkt, n, start, cursor, order);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+int report(int32_t h_err)
+{
+    if (h_err & kErrInvalid)
+        return set_error(FH_ERR_INVALID_ARG, "a candidate value is not finite or a width <= 0");
+    if (h_err & kErrRange) return set_error(FH_ERR_TIMEOUT, "union-find retry limit reached");
+    return FH_OK;
+}
+
+}  // namespace
+}  // namespace fh
+
+using namespace fh;
+
+extern "C" {
+
+int fh_cluster(const fh_cand_params *cands, int32_t n, double d_max, int32_t *label,
+               int32_t *n_clusters, void *stream)
+{
+    if ((n > 0 && (!cands || !label)) || !n_clusters || n < 0 || n > (1 << 30) ||
+        !(d_max >= 0.0) || !std::isfinite(d_max))
+        return set_error(FH_ERR_INVALID_ARG, "need cands, label, n in [0, 2^30], finite d_max >= 0");
+    *n_clusters = 0;
+    if (n == 0) return FH_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch sc(s);
+    const int32_t nb = std::min(n, kMaxBuckets);
+    unsigned long long *rng = nullptr;
+    Buckets *bk = nullptr;
+    double *fs = nullptr;
+    int32_t *bkt = nullptr, *order = nullptr, *parent = nullptr, *err = nullptr, *roots = nullptr;
+    int64_t *start = nullptr;
+    cudaError_t e = sc.get(&rng, 3);
+    if (e == cudaSuccess) e = sc.get(&bk, 1);
+    if (e == cudaSuccess) e = sc.get(&fs, (size_t)n);
+    if (e == cudaSuccess) e = sc.get(&bkt, (size_t)n);
+    if (e == cudaSuccess) e = sc.get(&order, (size_t)n);
+    if (e == cudaSuccess) e = sc.get(&parent, (size_t)n);
+    if (e == cudaSuccess) e = sc.get(&err, 2);
+    if (e == cudaSuccess) e = sc.get(&start, (size_t)nb + 1);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync (cluster)");
+    roots = err + 1;
+    const unsigned long long init[3] = {~0ull, 0ull, 0ull};
+    e = cudaMemcpyAsync(rng, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 8, s);
+    if (e == cudaSuccess) {
+        range_kernel<<<grid_for(n), 256, 0, s>>>(cands, nullptr, n, rng, err, false);
+        shift_kernel<<<grid_for(n), 256, 0, s>>>(cands, n, 0.0, fs);  // f itself (f + fdot 0)
+        bucket_setup_kernel<<<1, 1, 0, s>>>(rng, nb, d_max, rng, bk);
+        init_parent_kernel<<<grid_for(n), 256, 0, s>>>(parent, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = build_buckets(fs, n, nb, bk, bkt, start, order, sc, s);
+    if (e == cudaSuccess) {
+        link_kernel<<<grid_for(n), 256, 0, s>>>(cands, n, d_max, bkt, start, order, nb, parent,
+                                                 err);
+        finish_labels_kernel<<<grid_for(n), 256, 0, s>>>(parent, n, label, roots, err);
+        e = cudaGetLastError();
+    }
+    int32_t h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, err, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "cluster");
+    *n_clusters = h[1];
+    return report(h[0]);
+}
+
+int fh_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
+                    const fh_cand_params *c2, int32_t n2, double t_ref2, double t_c,
+                    const double *win, int32_t *pairs, int64_t capacity, int64_t *n_pairs,
+                    int32_t *n_match1, int32_t *n_match2, void *stream)
+{
+    if ((n1 > 0 && !c1) || (n2 > 0 && !c2) || !win || !n_pairs || (capacity > 0 && !pairs) ||
+        n1 < 0 || n2 < 0 || n1 > (1 << 30) || n2 > (1 << 30) || capacity < 0)
+        return set_error(FH_ERR_INVALID_ARG, "bad candidate sets or outputs");
+    for (int q = 0; q < 4; ++q)
+        if (!(win[q] >= 0.0) || !std::isfinite(win[q]))
+            return set_error(FH_ERR_INVALID_ARG, "windows must be finite and >= 0");
+    if (!std::isfinite(t_ref1) || !std::isfinite(t_ref2) || !std::isfinite(t_c))
+        return set_error(FH_ERR_INVALID_ARG, "reference times must be finite");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    *n_pairs = 0;
+    cudaError_t e = cudaSuccess;
+    if (n_match2 && n2 > 0) e = cudaMemsetAsync(n_match2, 0, 4 * (size_t)n2, s);
+    if (e == cudaSuccess && n_match1 && n1 > 0 && n2 == 0)
+        e = cudaMemsetAsync(n_match1, 0, 4 * (size_t)n1, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync (coincidences)");
+    if (n1 == 0 || n2 == 0) {
+        e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? FH_OK : cuda_error(e, "coincidences");
+    }
+    Scratch sc(s);
+    const int32_t nb = std::min(n2, kMaxBuckets);
+    unsigned long long *rng = nullptr, *rngw = nullptr;
+    Buckets *bk = nullptr;
+    double *f1 = nullptr, *f2 = nullptr;
+    int32_t *bkt = nullptr, *order = nullptr, *err = nullptr, *cnt1 = nullptr;
+    int64_t *start = nullptr, *off = nullptr;
+    e = sc.get(&rng, 3);
+    if (e == cudaSuccess) e = sc.get(&rngw, 3);
+    if (e == cudaSuccess) e = sc.get(&bk, 1);
+    if (e == cudaSuccess) e = sc.get(&f1, (size_t)n1);
+    if (e == cudaSuccess) e = sc.get(&f2, (size_t)n2);
+    if (e == cudaSuccess) e = sc.get(&bkt, (size_t)n2);
+    if (e == cudaSuccess) e = sc.get(&order, (size_t)n2);
+    if (e == cudaSuccess) e = sc.get(&err, 1);
+    if (e == cudaSuccess) e = sc.get(&start, (size_t)nb + 1);
+    if (e == cudaSuccess) e = sc.get(&off, (size_t)n1 + 1);
+    if (e == cudaSuccess) {
+        if (n_match1)
+            cnt1 = n_match1;
+        else
+            e = sc.get(&cnt1, (size_t)n1);
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync (coincidences)");
+    const unsigned long long init[3] = {~0ull, 0ull, 0ull};
+    e = cudaMemcpyAsync(rng, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rngw, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, s);
+    if (e == cudaSuccess) {
+        // frequencies at the common time: f + fdot (t_c - t_ref)
+        shift_kernel<<<grid_for(n1), 256, 0, s>>>(c1, n1, t_c - t_ref1, f1);
+        shift_kernel<<<grid_for(n2), 256, 0, s>>>(c2, n2, t_c - t_ref2, f2);
+        range_kernel<<<grid_for(n2), 256, 0, s>>>(c2, f2, n2, rng, err, false);
+        range_kernel<<<grid_for(n1), 256, 0, s>>>(c1, f1, n1, rngw, err, true);
+        range_kernel<<<grid_for(n2), 256, 0, s>>>(c2, f2, n2, rngw, err, true);
+        bucket_setup_kernel<<<1, 1, 0, s>>>(rng, nb, win[2], rngw, bk);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = build_buckets(f2, n2, nb, bk, bkt, start, order, sc, s);
+    CoinArgs a{c1, c2, f1, f2, n1, n2, win[0], win[1], win[2], win[3], bk, start, order};
+    if (e == cudaSuccess) {
+        coin_count_kernel<<<grid_for(n1), 256, 0, s>>>(a, cnt1, n_match2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_exclusive_scan(cnt1, n1, off, 1, nullptr, s);
+    if (e == cudaSuccess && capacity > 0) {
+        coin_write_kernel<<<grid_for(n1), 256, 0, s>>>(a, off, capacity, pairs);
+        e = cudaGetLastError();
+    }
+    int64_t total = 0;
+    int32_t h_err = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, off + n1, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "coincidences");
+    const int rc = report(h_err);
+    if (rc) return rc;
+    *n_pairs = total;
+    if (total > capacity)
+        return set_error(FH_ERR_CAPACITY, "%lld coincident pairs, capacity %lld",
+                         (long long)total, (long long)capacity);
+    return FH_OK;
+}
+
+}  // extern "C"

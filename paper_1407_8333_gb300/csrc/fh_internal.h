@@ -122,6 +122,11 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t s);
 cudaError_t launch_smem_atomic_bench(int32_t variant, int32_t iters, int32_t grid,
                                      unsigned long long *sink, cudaStream_t s);
 
+// Exclusive scan of n int32 counts into int64 (one block): pref[0 .. n] (may be
+// null) and strided[r] = pref[r * stride] for r = 0 .. n / stride (may be null).
+cudaError_t launch_exclusive_scan(const int32_t *cnt, int64_t n, int64_t *pref, int32_t stride,
+                                  int64_t *strided, cudaStream_t s);
+
 // ---- host helpers (fh_api.cu) ----
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);

@@ -505,6 +505,17 @@ struct Scratch {
     }
 };
 
+}  // namespace
+
+cudaError_t launch_exclusive_scan(const int32_t *cnt, int64_t n, int64_t *pref, int32_t stride,
+                                  int64_t *strided, cudaStream_t s)
+{
+    scan_counts_kernel<<<1, kScanThreads, 0, s>>>(cnt, n, pref, stride, strided);
+    return cudaGetLastError();
+}
+
+namespace {
+
 int warp_grid(int32_t n_fft)
 {
     const int per_block = 8;  // warps of a 256-thread block

@@ -101,6 +101,9 @@ _SIGS = {
                                _i32, _i32, _P, _P, _P, _P, _i64, _P, _P], ctypes.c_int),
     "fh_peakmap_persistency_veto": ([_P, _P, _i32, _i64, _i32, _f64, _i64, _f64, _P, _P, _P, _P,
                                      _P, _i64, _P, _P], ctypes.c_int),
+    "fh_cluster": ([_P, _i32, _f64, _P, _P, _P], ctypes.c_int),
+    "fh_coincidences": ([_P, _i32, _f64, _P, _i32, _f64, _f64, _P, _P, _i64, _P, _P, _P, _P],
+                        ctypes.c_int),
     "fh_refine": ([_P, ctypes.POINTER(fh_peakmap), _P, _P, _P, _i32, _P, _i32, _i32, _P, _i64, _P],
                   ctypes.c_int),
     "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
@@ -386,6 +389,57 @@ def fh_peakmap_persistency_veto(offsets, bins, n_bins: int, k_sigma: float, k0: 
                                               _stream(stream)), "fh_peakmap_persistency_veto")
     k = n.value
     return o2, b2[:k], (f2[:k] if f2 is not None else None), hist, tuple(stats)
+
+
+def _cands(c):
+    """A device tensor of candidate records: (n, 8) float64, rows in the order
+    lam, beta, f, fdot, dlam, dbeta, df, dfdot."""
+    if c.dtype != _torch().float64 or c.dim() != 2 or c.shape[1] != 8 or not c.is_contiguous():
+        raise ValueError("candidates: a contiguous (n, 8) float64 device tensor")
+    return c
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def fh_cluster(cands, d_max: float, stream=None):
+    """Cluster labels (device int32, the smallest index of each cluster) and the
+    number of clusters."""
+    torch = _torch()
+    c = _cands(cands)
+    n = int(c.shape[0])
+    label = torch.empty(max(1, n), dtype=torch.int32, device=c.device)
+    nc = ctypes.c_int32(0)
+    _check(load().fh_cluster(_dev_ptr(c), n, float(d_max), _dev_ptr(label), ctypes.byref(nc),
+                             _stream(stream)), "fh_cluster")
+    return label[:n], int(nc.value)
+
+
+def fh_coincidences(c1, c2, t_ref1: float, t_ref2: float, t_c: float, win, capacity: int = None,
+                    stream=None):
+    """Coincident pairs ((k, 2) device int32, (i, j) order) and the partner
+    counts of both sets."""
+    torch = _torch()
+    a, b = _cands(c1), _cands(c2)
+    n1, n2 = int(a.shape[0]), int(b.shape[0])
+    w = (ctypes.c_double * 4)(*[float(x) for x in win])
+    cap = int(capacity) if capacity is not None else max(1, 4 * (n1 + n2))
+    while True:
+        pairs = torch.empty((cap, 2), dtype=torch.int32, device=a.device)
+        m1 = torch.empty(max(1, n1), dtype=torch.int32, device=a.device)
+        m2 = torch.empty(max(1, n2), dtype=torch.int32, device=a.device)
+        n = ctypes.c_int64(0)
+        rc = load().fh_coincidences(_dev_ptr(a), n1, float(t_ref1), _dev_ptr(b), n2,
+                                    float(t_ref2), float(t_c), ctypes.cast(w, _P),
+                                    _dev_ptr(pairs), cap, ctypes.byref(n), _dev_ptr(m1),
+                                    _dev_ptr(m2), _stream(stream))
+        if rc == FH_ERR_CAPACITY and capacity is None:
+            cap = int(n.value)
+            continue
+        _check(rc, "fh_coincidences")
+        return pairs[:n.value], m1[:n1], m2[:n2]
 
 
 def fh_refine(plan, t, offsets, freq, v_over_c, cells, rows, sky_ref, k_fdot: int,
