@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu legs")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--legs", default="adaptive,batched,serving,refine,peakmap,cpu",
+    ap.add_argument("--legs", default="adaptive,batched,serving,refine,peakmap,coincidences,cpu",
                     help="extra legs to run after the timed step (comma list)")
     return ap.parse_args()
 
@@ -161,7 +161,7 @@ def peaks_path():
     return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None):
+def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None, coinc=None):
     """The oracle as it stands, whole path a1-a6 on the same workload (and, given
     refine_args = (cells, rows, sky_ref, k_fdot), its refined-grid search on a
     few of the workload's candidates)."""
@@ -191,6 +191,18 @@ def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None):
                      "1 direction, best of %d runs (%.2f s each)" % (len(times), best)}
     if ref is not None:
         out["refine"] = ref
+    if coinc is not None:
+        a, b = coinc
+        t0 = time.perf_counter()
+        oracle.coincidence.cluster(a, 4.0)
+        t1 = time.perf_counter()
+        oracle.coincidence.coincidences(a, b, 1.0e6, 2.0e6, 1.5e6, (2, 2, 2, 2))
+        t2 = time.perf_counter()
+        out["coincidences"] = {"cluster_candidates_per_s": len(a) / (t1 - t0),
+                               "coincidence_candidates_per_s": 2 * len(a) / (t2 - t1),
+                               "cores": 1,
+                               "sample": "%d candidates per set (numpy), one run each "
+                                         "(%.2f s, %.2f s)" % (len(a), t1 - t0, t2 - t1)}
     if peakmap is not None:
         t0 = time.perf_counter()
         oracle.peakmap.select_peaks(peakmap.s_p, peakmap.s_ar, 2.5)
@@ -368,10 +380,16 @@ def run_ours(args):
                 out["peakmap"] = peakmap_leg(fh, synth, torch, args.steps)
             except Exception as e:  # report, do not hide
                 out["peakmap"] = {"error": str(e)[:300]}
+        if "coincidences" in legs:
+            try:
+                out["coincidences"] = coincidence_leg(fh, synth, torch, args.steps)
+            except Exception as e:  # report, do not hide
+                out["coincidences"] = {"error": str(e)[:300]}
         if "cpu" in legs:
             out["cpu_baseline"] = cpu_baseline_leg(
                 inp, pp, refine_args=ref_args,
-                peakmap=synth.peakmap_workload() if "peakmap" in legs else None)
+                peakmap=synth.peakmap_workload() if "peakmap" in legs else None,
+                coinc=coincidence_sets(synth, 5000, 1) if "coincidences" in legs else None)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -509,6 +527,53 @@ def peakmap_leg(fh, synth, torch, steps):
                          "duration_note": "CUDA events around the asynchronous "
                                           "fh_peakmap_select with a workspace (mask, scan "
                                           "and expand kernels)"}}
+
+
+def coincidence_sets(synth, n, bands, seed=51):
+    """Two candidate sets of n each over `bands` 1 Hz bands at 100 Hz (T_FFT
+    1024 s, sky uniform, 100 spin-down rows), n / 100 sources present in both
+    (the second set at its own reference time, 1e6 s later), n / 50 clusters
+    of 6 per set."""
+    import numpy as np
+    seeds = synth.candidate_set(seed, 0, n // 100, band=float(bands))[:, :4]
+    later = seeds.copy()
+    later[:, 2] += later[:, 3] * 1.0e6
+    a = synth.candidate_set(seed, 1, n, band=float(bands), signals=seeds, clusters=n // 50,
+                            cluster_size=6)
+    b = synth.candidate_set(seed, 2, n, band=float(bands), signals=later, clusters=n // 50,
+                            cluster_size=6)
+    return np.ascontiguousarray(a), np.ascontiguousarray(b)
+
+
+def coincidence_leg(fh, synth, torch, steps):
+    """Clustering (d <= 4, Eq. norm) and coincidences (windows of 2 bins in
+    every parameter, frequencies at the common time) through the host API
+    (device candidates; each call synchronises)."""
+    res = {}
+    for n, bands in ((100000, 1), (1000000, 10)):
+        a, b = coincidence_sets(synth, n, bands)
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        c_ms, k_ms = [], []
+        for k in range(2 + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lab, ncl = fh.fh_cluster(da, 4.0)
+            t1 = time.perf_counter()
+            pairs, m1, m2 = fh.fh_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, (2, 2, 2, 2))
+            t2 = time.perf_counter()
+            if k >= 2:
+                c_ms.append((t1 - t0) * 1e3)
+                k_ms.append((t2 - t1) * 1e3)
+        cm, km = statistics.median(c_ms), statistics.median(k_ms)
+        res["%dk_x_%dHz" % (n // 1000, bands)] = {
+            "n_per_set": n, "clusters": ncl, "pairs": int(pairs.shape[0]),
+            "coincident_in_set1": int((m1 > 0).sum().item()),
+            "cluster_ms": cm, "coincidence_ms": km,
+            "cluster_candidates_per_s": n / (cm * 1e-3),
+            "coincidence_candidates_per_s": 2 * n / (km * 1e-3)}
+    res["workload"] = ("two sets per size, sky uniform, f in 1 Hz bands at 100 Hz "
+                       "(T_FFT 1024 s), 1 % common sources, 2 % clusters of 6")
+    return res
 
 
 def batched_vs_plain(fh, synth, torch):

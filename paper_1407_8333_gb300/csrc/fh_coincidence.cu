@@ -62,6 +62,40 @@ __device__ __forceinline__ double norm_distance(const fh_cand_params &a, const f
                                 __dmul_rn(kd, kd)));
 }
 
+// A pair farther apart in one parameter than `reach` bins cannot link or
+// coincide: that k exceeds reach, and the distance is at least each k to a unit
+// in the last place.  These tests multiply instead of dividing and keep a
+// margin of 1e-12, so they only reject pairs the exact test rejects too; they
+// run in the order that rejects most pairs first (frequency, spin-down,
+// latitude, longitude), and the divisions and the square root are left to
+// the few pairs that pass all four.
+__device__ __forceinline__ bool out_of_reach(double xa, double xb, double wa, double wb,
+                                             double reach)
+{
+    return fabs(xa - xb) > reach * ((wa + wb) * 0.5) * (1.0 + 1e-12);
+}
+__device__ __forceinline__ bool lam_out_of_reach(double la, double lb, double wa, double wb,
+                                                 double reach)
+{
+    double a = fabs(la - lb);
+    if (a > kPi) a = kTwoPi - a;
+    return a > reach * ((wa + wb) * 0.5) * (1.0 + 1e-12);
+}
+__device__ __forceinline__ bool f_out_of_reach(double fa, double fb, double dfa, double dfb,
+                                               double reach)
+{
+    return out_of_reach(fa, fb, dfa, dfb, reach);
+}
+__device__ __forceinline__ bool any_out_of_reach(const fh_cand_params &a,
+                                                 const fh_cand_params &b, double fa, double fb,
+                                                 double reach)
+{
+    return out_of_reach(fa, fb, a.df, b.df, reach) ||
+           out_of_reach(a.fdot, b.fdot, a.dfdot, b.dfdot, reach) ||
+           out_of_reach(a.beta, b.beta, a.dbeta, b.dbeta, reach) ||
+           lam_out_of_reach(a.lam, b.lam, a.dlam, b.dlam, reach);
+}
+
 // order-preserving map of doubles to unsigned 64-bit keys (for atomic min / max)
 __device__ __forceinline__ unsigned long long okey(double x)
 {
@@ -105,12 +139,22 @@ __global__ void range_kernel(const fh_cand_params *c, const double *fs, int32_t 
         }
         wd = max(wd, okey(x.df));
     }
-    if (!widths_only) {
-        atomicMin(rng + 0, lo);
-        atomicMax(rng + 1, hi);
+    // one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        wd = max(wd, __shfl_xor_sync(0xffffffffu, wd, o));
     }
-    atomicMax(rng + 2, wd);
-    if (bad) atomicOr(err, kErrInvalid);
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (!widths_only) {
+            atomicMin(rng + 0, lo);
+            atomicMax(rng + 1, hi);
+        }
+        atomicMax(rng + 2, wd);
+        if (bad) atomicOr(err, kErrInvalid);
+    }
 }
 
 // bucket width: at least `reach` x max(df) (the largest frequency difference a
@@ -192,18 +236,23 @@ __device__ __forceinline__ void uf_union(int32_t *parent, int32_t a, int32_t b, 
     atomicOr(err, kErrRange);
 }
 
+// threads take the candidates in bucket order, so the lanes of a warp scan
+// the same buckets
 __global__ void link_kernel(const fh_cand_params *c, int32_t n, double d_max, const int32_t *bkt,
                             const int64_t *start, const int32_t *order, int32_t nb,
                             int32_t *parent, int32_t *err)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int32_t i = order[t];
         const fh_cand_params a = c[i];
         const int32_t q = bkt[i];
         for (int32_t qq = max(q - 1, 0); qq <= min(q + 1, nb - 1); ++qq) {
             for (int64_t p = start[qq]; p < start[qq + 1]; ++p) {
                 const int32_t j = order[p];
                 if (j <= i) continue;
+                if (f_out_of_reach(a.f, c[j].f, a.df, c[j].df, d_max)) continue;
                 const fh_cand_params b = c[j];
+                if (any_out_of_reach(a, b, a.f, b.f, d_max)) continue;
                 if (norm_distance(a, b, a.f, b.f) <= d_max) uf_union(parent, i, j, err);
             }
         }
@@ -241,22 +290,32 @@ struct CoinArgs {
     const Buckets *bk;
     const int64_t *start;
     const int32_t *order;
+    const int32_t *order1;  // set 1 in the order of set 2's buckets
 };
 
+// every window must hold; frequency first (with its cheap reject), then the rest
 __device__ __forceinline__ bool coincide(const CoinArgs &a, const fh_cand_params &x, double fx,
                                          int32_t j)
 {
+    const double fy = a.f2[j];
+    const double dfy = a.c2[j].df;
+    if (f_out_of_reach(fx, fy, x.df, dfy, a.w_f)) return false;
     const fh_cand_params y = a.c2[j];
-    return bins_apart(x.lam, y.lam, x.dlam, y.dlam, true) <= a.w_lam &&
+    if (out_of_reach(x.fdot, y.fdot, x.dfdot, y.dfdot, a.w_fdot) ||
+        out_of_reach(x.beta, y.beta, x.dbeta, y.dbeta, a.w_beta) ||
+        lam_out_of_reach(x.lam, y.lam, x.dlam, y.dlam, a.w_lam))
+        return false;
+    return bins_apart(fx, fy, x.df, y.df, false) <= a.w_f &&
+           bins_apart(x.fdot, y.fdot, x.dfdot, y.dfdot, false) <= a.w_fdot &&
            bins_apart(x.beta, y.beta, x.dbeta, y.dbeta, false) <= a.w_beta &&
-           bins_apart(fx, a.f2[j], x.df, y.df, false) <= a.w_f &&
-           bins_apart(x.fdot, y.fdot, x.dfdot, y.dfdot, false) <= a.w_fdot;
+           bins_apart(x.lam, y.lam, x.dlam, y.dlam, true) <= a.w_lam;
 }
 
 __global__ void coin_count_kernel(const CoinArgs a, int32_t *cnt1, int32_t *cnt2)
 {
     const Buckets b = *a.bk;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n1; i += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n1; t += gridDim.x * blockDim.x) {
+        const int32_t i = a.order1[t];
         const fh_cand_params x = a.c1[i];
         const double fx = a.f1[i];
         const long long r = b.raw(fx);
@@ -277,7 +336,8 @@ __global__ void coin_write_kernel(const CoinArgs a, const int64_t *off, int64_t 
                                   int32_t *pairs)
 {
     const Buckets b = *a.bk;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n1; i += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n1; t += gridDim.x * blockDim.x) {
+        const int32_t i = a.order1[t];
         const fh_cand_params x = a.c1[i];
         const double fx = a.f1[i];
         const long long r = b.raw(fx);
@@ -476,7 +536,15 @@ int fh_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = build_buckets(f2, n2, nb, bk, bkt, start, order, sc, s);
-    CoinArgs a{c1, c2, f1, f2, n1, n2, win[0], win[1], win[2], win[3], bk, start, order};
+    // set 1 sorted by the same buckets (clamped), so that a warp's threads scan
+    // the same part of set 2
+    int32_t *bkt1 = nullptr, *order1 = nullptr;
+    int64_t *start1 = nullptr;
+    if (e == cudaSuccess) e = sc.get(&bkt1, (size_t)n1);
+    if (e == cudaSuccess) e = sc.get(&order1, (size_t)n1);
+    if (e == cudaSuccess) e = sc.get(&start1, (size_t)nb + 1);
+    if (e == cudaSuccess) e = build_buckets(f1, n1, nb, bk, bkt1, start1, order1, sc, s);
+    CoinArgs a{c1, c2, f1, f2, n1, n2, win[0], win[1], win[2], win[3], bk, start, order, order1};
     if (e == cudaSuccess) {
         coin_count_kernel<<<grid_for(n1), 256, 0, s>>>(a, cnt1, n_match2);
         e = cudaGetLastError();
