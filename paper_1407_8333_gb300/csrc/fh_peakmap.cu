@@ -164,10 +164,13 @@ struct ExpandArgs {
     double *freq;
 };
 
-// one block per (segment, FFT): 128 words, one per thread, ranks by a block scan
+// One block per (segment, FFT): 128 words, one per thread; a block scan of
+// their counts ranks the segment's peaks, which are staged in shared memory in
+// bin order and written as contiguous runs.
 __global__ void __launch_bounds__(kSegWords) select_expand_kernel(const ExpandArgs a)
 {
     __shared__ int32_t wsum[kSegWords / 32];
+    __shared__ int32_t peaks_s[kSegBins / 2];  // strict maxima: at most every other bin
     const int row = blockIdx.y, seg = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int w = seg * kSegWords + tid;
@@ -181,19 +184,28 @@ __global__ void __launch_bounds__(kSegWords) select_expand_kernel(const ExpandAr
     }
     if (lane == 31) wsum[warp] = p;
     __syncthreads();
-    int before = 0;
-    for (int q = 0; q < warp; ++q) before += wsum[q];
-    int64_t pos = a.seg_base[(int64_t)row * a.n_seg + seg] + before + p - c;
+    int before = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kSegWords / 32; ++q) {
+        before += q < warp ? wsum[q] : 0;
+        total += wsum[q];
+    }
+    int pos = before + p - c;
     uint32_t m = word;
     while (m) {
         const int bit = __ffs(m) - 1;
         m &= m - 1;
-        if (pos < a.capacity) {
-            const int b = w * 32 + bit;
-            a.bins[pos] = b;
-            if (a.freq) a.freq[pos] = a.fq(b);
+        peaks_s[pos++] = w * 32 + bit;
+    }
+    __syncthreads();
+    const int64_t base = a.seg_base[(int64_t)row * a.n_seg + seg];
+    for (int k = tid; k < total; k += kSegWords) {
+        const int64_t out = base + k;
+        if (out < a.capacity) {
+            const int32_t b = peaks_s[k];
+            a.bins[out] = b;
+            if (a.freq) a.freq[out] = a.fq(b);
         }
-        ++pos;
     }
 }
 
