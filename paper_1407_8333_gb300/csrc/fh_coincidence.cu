@@ -86,6 +86,42 @@ __device__ __forceinline__ bool f_out_of_reach(double fa, double fb, double dfa,
 {
     return out_of_reach(fa, fb, dfa, dfb, reach);
 }
+
+// The same rejects in binary32, whose pipe is many times GB300's binary64 one.
+// A value rounded to float is off by at most half a float ulp, and the float
+// difference of two such values by another, so |x2 - x1| >= the float
+// difference - 2 ulp (ulp bounded by 2^-23 |x| plus the smallest normal); the
+// width sum and the product carry relative errors of a few 2^-24, covered by
+// the factor 1 + 1e-5.  A pair rejected here is rejected by the exact test;
+// infinities and NaN never reject.
+__device__ __forceinline__ float ulp2(float x) { return fabsf(x) * 2.4e-7f + 2.4e-38f; }
+__device__ __forceinline__ bool far32(double xa, double xb, double wa, double wb, float reach)
+{
+    const float a = (float)xa, b = (float)xb;
+    const float lim = reach * (((float)wa + (float)wb) * 0.5f) * 1.00001f;
+    return fabsf(a - b) - 2.0f * ulp2(fmaxf(fabsf(a), fabsf(b))) > lim;
+}
+__device__ __forceinline__ bool lam_far32(double la, double lb, double wa, double wb, float reach)
+{
+    const float a0 = (float)la, b0 = (float)lb;
+    float a = fabsf(a0 - b0);
+    if (a > 3.14159265f) a = 6.28318531f - a;
+    const float lim = reach * (((float)wa + (float)wb) * 0.5f) * 1.00001f;
+    // near a difference of pi the two sides of the wrap differ by twice the
+    // error of a, and the float constants by a few 1e-7
+    return a - 4.0f * ulp2(fmaxf(fmaxf(fabsf(a0), fabsf(b0)), 6.3f)) - 1e-6f > lim;
+}
+// all four, evaluated without branches so that the lanes of a warp stay together
+__device__ __forceinline__ bool any_far32(const fh_cand_params &a, const fh_cand_params &b,
+                                          double fa, double fb, float reach_f, float reach_d,
+                                          float reach_b, float reach_l)
+{
+    const bool r = far32(fa, fb, a.df, b.df, reach_f) | far32(a.fdot, b.fdot, a.dfdot, b.dfdot,
+                                                              reach_d) |
+                   far32(a.beta, b.beta, a.dbeta, b.dbeta, reach_b) |
+                   lam_far32(a.lam, b.lam, a.dlam, b.dlam, reach_l);
+    return r;
+}
 __device__ __forceinline__ bool any_out_of_reach(const fh_cand_params &a,
                                                  const fh_cand_params &b, double fa, double fb,
                                                  double reach)
@@ -242,6 +278,7 @@ __global__ void link_kernel(const fh_cand_params *c, int32_t n, double d_max, co
                             const int64_t *start, const int32_t *order, int32_t nb,
                             int32_t *parent, int32_t *err)
 {
+    const float dm32 = (float)d_max;  // rounds to nearest: the 1e-5 factor covers it
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const int32_t i = order[t];
         const fh_cand_params a = c[i];
@@ -250,9 +287,8 @@ __global__ void link_kernel(const fh_cand_params *c, int32_t n, double d_max, co
             for (int64_t p = start[qq]; p < start[qq + 1]; ++p) {
                 const int32_t j = order[p];
                 if (j <= i) continue;
-                if (f_out_of_reach(a.f, c[j].f, a.df, c[j].df, d_max)) continue;
                 const fh_cand_params b = c[j];
-                if (any_out_of_reach(a, b, a.f, b.f, d_max)) continue;
+                if (any_far32(a, b, a.f, b.f, dm32, dm32, dm32, dm32)) continue;
                 if (norm_distance(a, b, a.f, b.f) <= d_max) uf_union(parent, i, j, err);
             }
         }
@@ -298,12 +334,9 @@ __device__ __forceinline__ bool coincide(const CoinArgs &a, const fh_cand_params
                                          int32_t j)
 {
     const double fy = a.f2[j];
-    const double dfy = a.c2[j].df;
-    if (f_out_of_reach(fx, fy, x.df, dfy, a.w_f)) return false;
     const fh_cand_params y = a.c2[j];
-    if (out_of_reach(x.fdot, y.fdot, x.dfdot, y.dfdot, a.w_fdot) ||
-        out_of_reach(x.beta, y.beta, x.dbeta, y.dbeta, a.w_beta) ||
-        lam_out_of_reach(x.lam, y.lam, x.dlam, y.dlam, a.w_lam))
+    if (any_far32(x, y, fx, fy, (float)a.w_f, (float)a.w_fdot, (float)a.w_beta,
+                  (float)a.w_lam))
         return false;
     return bins_apart(fx, fy, x.df, y.df, false) <= a.w_f &&
            bins_apart(x.fdot, y.fdot, x.dfdot, y.dfdot, false) <= a.w_fdot &&
