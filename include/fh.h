@@ -262,6 +262,17 @@ int fh_plan_set_timing(fh_plan plan, int32_t on);
 int fh_plan_kernel_times(fh_plan plan, int64_t *n_groups, double *windows_ms,
                          double *transform_ms);
 
+/* Where fh_correct_doppler checks HOST inputs.  FH_CHECKS_HOST (the default):
+ * on the host, before anything is launched; a failed check returns its error
+ * from fh_correct_doppler and leaves the plan without a peakmap.
+ * FH_CHECKS_DEVICE: the inputs are copied and checked by the kernels, exactly
+ * as device inputs are (CSR, ordering, finiteness, fixed-point range), so the
+ * call returns as soon as the work is enqueued; a failure is reported, as for
+ * device inputs, by the next fh_sync or host-output fh_select_candidates, and
+ * no input can make a kernel leave its buffers. */
+enum { FH_CHECKS_HOST = 0, FH_CHECKS_DEVICE = 1 };
+int fh_plan_set_input_checks(fh_plan plan, int32_t where);
+
 /* ---- peakmap construction and cleaning ------------------------------------ */
 /* A binned peakmap: offsets (n_fft + 1, int64, a CSR by FFT, offsets[0] = 0) and
  * the band-relative bin index of every peak (int32, ascending within an FFT);

@@ -99,8 +99,10 @@ int32_t default_guard(const fh_plan_desc &d)
 int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft)
 {
     double m = 0.0;
-    for (int32_t i = 0; i < n_fft; ++i)
-        m = std::max(m, std::fabs(d.fdot_step * ((t[i] - d.t_ref) * kt)));
+    for (int32_t i = 0; i < n_fft; ++i) {
+        const double x = std::fabs(d.fdot_step * ((t[i] - d.t_ref) * kt));
+        if (x > m && x < 1e9) m = x;  // non-finite or absurd times are left to the checks
+    }
     return guard_for((unsigned long long)(m * 4294967296.0) + 4);
 }
 
@@ -145,7 +147,7 @@ struct Sizes {
     int64_t t, offsets, tables, freq, v, sky, A, profile, cand;
     int64_t total() const
     {
-        return t + offsets + 2 * tables + freq + v + sky + A + profile + cand + 256;
+        return t + 2 * offsets + 2 * tables + freq + v + sky + A + profile + cand + 256;
     }
 };
 
@@ -180,6 +182,8 @@ struct fh_plan_s {
     int32_t block_warps = 32;
     double *t = nullptr, *freq = nullptr, *v = nullptr, *sky = nullptr;
     int64_t *offsets = nullptr, *S0 = nullptr, *D = nullptr, *A = nullptr;
+    int64_t *offsets_raw = nullptr;  // host offsets as copied, for the device checks
+    int32_t input_checks = FH_CHECKS_HOST;
     uint64_t *profile = nullptr;
     fh_candidate *cand = nullptr;
     int32_t *err = nullptr;
@@ -209,12 +213,13 @@ struct fh_plan_s {
     {
         for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
         tev.clear();
-        void *bufs[] = {t, freq, v, sky, offsets, S0, D, A, profile, cand, err, dmax, win, wq, ws};
+        void *bufs[] = {t,    freq, v,   sky,  offsets, offsets_raw, S0, D,
+                        A,    profile, cand, err, dmax, win,  wq,  ws};
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
         t = freq = v = sky = nullptr;
-        offsets = S0 = D = A = nullptr;
+        offsets = S0 = D = A = offsets_raw = nullptr;
         profile = nullptr;
         cand = nullptr;
         err = h_err = nullptr;
@@ -405,6 +410,7 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
         void **ptr;
         int64_t bytes;
     } allocs[] = {{(void **)&p->t, s.t},           {(void **)&p->offsets, s.offsets},
+                  {(void **)&p->offsets_raw, s.offsets},
                   {(void **)&p->S0, s.tables},     {(void **)&p->D, s.tables},
                   {(void **)&p->freq, s.freq},     {(void **)&p->v, s.v},
                   {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
@@ -445,6 +451,15 @@ int fh_destroy_plan(fh_plan p)
 }
 
 int64_t fh_plan_launches(fh_plan p) { return p ? p->launches : -1; }
+
+int fh_plan_set_input_checks(fh_plan p, int32_t where)
+{
+    if (!p) return set_error(FH_ERR_INVALID_ARG, "null plan");
+    if (where != FH_CHECKS_HOST && where != FH_CHECKS_DEVICE)
+        return set_error(FH_ERR_INVALID_ARG, "checks must be FH_CHECKS_HOST or FH_CHECKS_DEVICE");
+    p->input_checks = where;
+    return FH_OK;
+}
 
 int fh_refine(fh_plan p, const fh_peakmap *pm, const double *v_over_c, const int32_t *cand_cell,
               const int32_t *cand_row, int32_t n_cand, const double *sky_ref, int32_t n_ref,
@@ -606,6 +621,7 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     const int32_t n = pm->n_fft;
     const int64_t np = pm->n_peaks;
     const double *t_src, *f_src, *v_src, *sky_src;
+    const bool host_checks = p->input_checks == FH_CHECKS_HOST;
     p->weighted = false;  // a new peakmap starts with unit weights
     cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->dmax, 0, sizeof(unsigned long long), s);
@@ -619,7 +635,7 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
             void *dst;
             const void *src;
             size_t bytes;
-        } cp[] = {{p->offsets, pm->offsets, 8 * ((size_t)n + 1)},
+        } cp[] = {{host_checks ? p->offsets : p->offsets_raw, pm->offsets, 8 * ((size_t)n + 1)},
                   {p->t, pm->t_fft, 8 * (size_t)n},
                   {p->freq, pm->freq, 8 * (size_t)np},
                   {p->v, v_over_c, 24 * (size_t)n},
@@ -630,9 +646,18 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
             e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(H2D inputs)");
         }
-        int rc = validate_host_inputs(p->d, p->kt, pm, v_over_c, sky_n, n_dir);
-        if (rc) return rc;
-        p->guard = std::max(default_guard(p->d), host_guard(p->d, p->kt, pm->t_fft, n));
+        if (host_checks) {
+            int rc = validate_host_inputs(p->d, p->kt, pm, v_over_c, sky_n, n_dir);
+            if (rc) return rc;
+        }
+        // the guard from the FFT times (the device checks of FH_CHECKS_DEVICE see the
+        // rest); one that would not leave room for a tile falls back to the plan's
+        // default, and the transform then takes its clamped walk if the drift is larger
+        int32_t gd = std::max(default_guard(p->d), host_guard(p->d, p->kt, pm->t_fft, n));
+        if (transform_smem_bytes(64, p->d.k_over, p->mode, p->block_warps, gd) >
+            (size_t)max_optin_smem(p->device))
+            gd = default_guard(p->d);
+        p->guard = gd;
         t_src = p->t;
         f_src = p->freq;
         v_src = p->v;
@@ -646,9 +671,11 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
         sky_src = sky_n;
     }
     const fh_plan_desc &d = p->d;
-    const bool on_device = pm->mem_kind == FH_MEM_DEVICE;
+    // device checks: for device inputs, and for host inputs under FH_CHECKS_DEVICE
+    const bool on_device = pm->mem_kind == FH_MEM_DEVICE || !host_checks;
     PrepArgs pa{};
-    pa.offsets_in = on_device ? pm->offsets : nullptr;  // host inputs were checked on the host
+    pa.offsets_in = pm->mem_kind == FH_MEM_DEVICE ? pm->offsets
+                                                  : (host_checks ? nullptr : p->offsets_raw);
     pa.offsets_out = p->offsets;
     pa.t = t_src;
     pa.v = v_src;

@@ -104,6 +104,7 @@ _SIGS = {
     "fh_cluster": ([_P, _i32, _f64, _P, _P, _P], ctypes.c_int),
     "fh_coincidences": ([_P, _i32, _f64, _P, _i32, _f64, _f64, _P, _P, _i64, _P, _P, _P, _P],
                         ctypes.c_int),
+    "fh_plan_set_input_checks": ([_P, _i32], ctypes.c_int),
     "fh_refine": ([_P, ctypes.POINTER(fh_peakmap), _P, _P, _P, _i32, _P, _i32, _i32, _P, _i64, _P],
                   ctypes.c_int),
     "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
@@ -291,6 +292,14 @@ def fh_autotune(plan, dir_begin: int, n_dir: int, stream=None) -> tuple:
 
 def fh_plan_launches(plan) -> int:
     return int(load().fh_plan_launches(plan))
+
+
+FH_CHECKS_HOST, FH_CHECKS_DEVICE = 0, 1
+
+
+def fh_plan_set_input_checks(plan, where: int) -> None:
+    """FH_CHECKS_HOST (default) or FH_CHECKS_DEVICE for host inputs."""
+    _check(load().fh_plan_set_input_checks(plan, int(where)), "fh_plan_set_input_checks")
 
 
 def _dev_ptr(x):

@@ -30,7 +30,7 @@ def fh():
 
 
 def run_gpu(fh, inp, pp, mode=0, schedule=0, tile=0, warps=0, maps=True, device_inputs=True,
-            autotune=False):
+            autotune=False, checks=None):
     import torch
     n_fft = inp.t.shape[0]
     n_peaks = inp.n_peaks
@@ -39,6 +39,8 @@ def run_gpu(fh, inp, pp, mode=0, schedule=0, tile=0, warps=0, maps=True, device_
                         tile_cells=tile, block_warps=warps)
     plan = fh.fh_create_plan(desc)
     try:
+        if checks is not None:
+            fh.fh_plan_set_input_checks(plan, checks)
         if device_inputs:
             args = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
         else:
@@ -370,3 +372,58 @@ def test_workload_highfreq_900Hz_sampled(fh, oracle_mod):
     top = g["cand"].reshape(2, -1, pp["top_k"])[0, q, 0]
     assert abs(int(top["cell"]) - true_cell) <= w.k_over
     assert int(top["count"]) > 0.6 * w.n_fft
+
+
+@pytest.mark.parametrize("seed", [41, 42])
+def test_host_inputs_checked_on_the_device_match_oracle(fh, oracle_mod, seed):
+    """FH_CHECKS_DEVICE: host inputs copied and checked by the kernels give the
+    same positions, maps, profiles and candidates as the oracle."""
+    inp, pp = synth.random_case(seed, n_fft=33, n_bins=70, n_dir=3, p=0.4)
+    g = run_gpu(fh, inp, pp, device_inputs=False, checks=fh.FH_CHECKS_DEVICE)
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    compare(g, o, pp, inp.t.shape[0])
+
+
+def test_host_input_errors_checked_on_the_device(fh):
+    """FH_CHECKS_DEVICE: unsorted frequencies, a broken CSR, a NaN time and an
+    infinite velocity in HOST memory are reported by the next synchronising
+    call (no fault), and the plan stays usable."""
+    inp, pp = synth.random_case(17, n_fft=10, n_bins=20, n_dir=1, p=0.5)
+    plan = fh.fh_create_plan(fh.make_desc(pp, 10, 1, inp.n_peaks))
+    try:
+        fh.fh_plan_set_input_checks(plan, fh.FH_CHECKS_DEVICE)
+        f = inp.freq.copy()
+        a = int(inp.offsets[3])
+        f[a], f[a + 1] = f[a + 1], f[a]
+        fh.fh_correct_doppler(plan, inp.t, inp.offsets, f, inp.v, inp.sky)
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_select_candidates(plan, 0, 1)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
+        off = inp.offsets.copy()
+        off[5] = inp.n_peaks + 1000
+        off[6] = -3
+        fh.fh_correct_doppler(plan, inp.t, off, inp.freq, inp.v, inp.sky, n_peaks=inp.n_peaks)
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_sync(plan)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
+        t = inp.t.copy()
+        t[4] = np.nan
+        fh.fh_correct_doppler(plan, t, inp.offsets, inp.freq, inp.v, inp.sky)
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError):
+            fh.fh_select_candidates(plan, 0, 1)
+        v = inp.v.copy()
+        v[2, 1] = np.inf
+        fh.fh_correct_doppler(plan, inp.t, inp.offsets, inp.freq, v, inp.sky)
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError):
+            fh.fh_select_candidates(plan, 0, 1)
+        fh.fh_correct_doppler(plan, inp.t, inp.offsets, inp.freq, inp.v, inp.sky)
+        fh.fh_transform(plan, 0, 1)
+        fh.fh_select_candidates(plan, 0, 1)
+        with pytest.raises(fh.FHError):
+            fh.fh_plan_set_input_checks(plan, 7)
+    finally:
+        fh.fh_destroy_plan(plan)
