@@ -451,12 +451,17 @@ def refine_leg(fh, synth, w, inp, pp, host_out, steps):
     n_d = synth.doppler_number(w.f_hi, w.t_fft)
     sky = np.stack([synth.refined_sky(inp.sky[int(c["dir"])], n_d, 3) for c in cand])
     k_fdot = 4
+    import torch
     plan = fh.fh_create_plan(fh.make_desc(pp, inp.t.shape[0], 1, inp.n_peaks))
+    # pinned host inputs, checked by the kernels (FH_CHECKS_DEVICE)
+    pin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+           for x in (inp.t, inp.offsets, inp.freq, inp.v, sky)]
+    fh.fh_plan_set_input_checks(plan, fh.FH_CHECKS_DEVICE)
     try:
         ts = []
         for k in range(2 + steps):
             t0 = time.perf_counter()
-            r = fh.fh_refine(plan, inp.t, inp.offsets, inp.freq, inp.v, cells, rows, sky, k_fdot)
+            r = fh.fh_refine(plan, pin[0], pin[1], pin[2], pin[3], cells, rows, pin[4], k_fdot)
             if k >= 2:
                 ts.append((time.perf_counter() - t0) * 1e3)
     finally:
@@ -466,7 +471,7 @@ def refine_leg(fh, synth, w, inp, pp, host_out, steps):
     res = {"n_cand": int(cand.shape[0]), "n_ref": int(sky.shape[1]), "k_fdot": k_fdot,
            "ms_per_call": ms, "candidates_per_s": cand.shape[0] / (ms * 1e-3),
            "count_gain_median": float(np.median(gain)) if gain.size else None,
-           "inputs": "host (pageable) peakmap, copied every call"}
+           "inputs": "host (pinned) peakmap copied every call, checked by the kernels"}
     sel = slice(0, min(3, cand.shape[0]))
     return res, (cells[sel], rows[sel], sky[sel], k_fdot)
 

@@ -53,6 +53,10 @@ struct DeviceGuard {
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+
+namespace fh {
+
 int device_error_code(int32_t bits)
 {
     if (bits & (kErrCsr | kErrUnsorted))
@@ -65,9 +69,6 @@ int device_error_code(int32_t bits)
     return FH_OK;
 }
 
-}  // namespace
-
-namespace fh {
 
 int max_optin_smem(int device)
 {
@@ -483,7 +484,7 @@ int fh_refine(fh_plan p, const fh_peakmap *pm, const double *v_over_c, const int
     if (n_cand == 0) return FH_OK;
     DeviceGuard g(p->device);
     return refine_impl(p->d, p->n_sm, pm, v_over_c, cand_cell, cand_row, n_cand, sky_ref, n_ref,
-                       k_fdot, out, as_stream(stream));
+                       k_fdot, out, p->input_checks == FH_CHECKS_HOST, as_stream(stream));
 }
 
 int fh_set_weights(fh_plan p, const double *w, int32_t n_dir, int32_t frac_bits, void *stream)

@@ -86,7 +86,9 @@ cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
 int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm, const double *v_over_c,
                 const int32_t *cand_cell, const int32_t *cand_row, int32_t n_cand,
                 const double *sky_ref, int32_t n_ref, int32_t k_fdot, fh_candidate *out,
-                cudaStream_t s);
+                bool host_checks, cudaStream_t s);
+// the error of a device error word (0: FH_OK)
+int device_error_code(int32_t bits);
 cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
                                 double fdot_min, double fdot_step, int32_t n_fdot,
                                 int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,

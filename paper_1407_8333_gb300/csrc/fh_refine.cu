@@ -187,7 +187,7 @@ namespace fh {
 int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
                 const double *v_over_c, const int32_t *cand_cell, const int32_t *cand_row,
                 int32_t n_cand, const double *sky_ref, int32_t n_ref, int32_t k_fdot,
-                fh_candidate *out, cudaStream_t s)
+                fh_candidate *out, bool host_checks, cudaStream_t s)
 {
     const double kt = (double)d.k_over * d.t_fft;
     const int32_t n = pm->n_fft;
@@ -196,8 +196,11 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     const int32_t n_f0r = 2 * K + 1;
     const int32_t n_rows = 4 * k_fdot;
     const double step_ref = d.fdot_step / (double)k_fdot;
-    int rc = validate_host_inputs(d, kt, pm, v_over_c, sky_ref, n_cand * n_ref);
-    if (rc) return rc;
+    // the inputs are checked on the host, or (FH_CHECKS_DEVICE) by the kernels
+    if (host_checks) {
+        const int rc = validate_host_inputs(d, kt, pm, v_over_c, sky_ref, n_cand * n_ref);
+        if (rc) return rc;
+    }
     for (int32_t c = 0; c < n_cand; ++c)
         if ((int64_t)cand_cell[c] - K < -(int64_t(1) << 27) ||
             (int64_t)cand_cell[c] + K >= (int64_t(1) << 27) || cand_row[c] < -(1 << 27) ||
@@ -216,6 +219,8 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     if (e == cudaSuccess) e = sc.get(&v, 3 * (size_t)n);
     if (e == cudaSuccess) e = sc.get(&sky, 3 * (size_t)n_cand * n_ref);
     if (e == cudaSuccess) e = sc.get(&off, (size_t)n + 1);
+    int64_t *off_raw = nullptr;
+    if (e == cudaSuccess && !host_checks) e = sc.get(&off_raw, (size_t)n + 1);
     if (e == cudaSuccess) e = sc.get(&S0, (size_t)n);
     if (e == cudaSuccess) e = sc.get(&D, (size_t)n);
     if (e == cudaSuccess) e = sc.get(&S0x, (size_t)n);
@@ -236,7 +241,7 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
               {freq, pm->freq, 8 * (size_t)np},
               {v, v_over_c, 24 * (size_t)n},
               {sky, sky_ref, 24 * (size_t)n_cand * n_ref},
-              {off, pm->offsets, 8 * ((size_t)n + 1)},
+              {host_checks ? off : off_raw, pm->offsets, 8 * ((size_t)n + 1)},
               {cc, cand_cell, 4 * (size_t)n_cand},
               {cr, cand_row, 4 * (size_t)n_cand}};
     for (auto &x : cp)
@@ -246,7 +251,9 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, 16, s);
     // coarse shift tables, then the refined step D' (and its largest |D'|)
     PrepArgs pa{};
+    pa.offsets_in = host_checks ? nullptr : off_raw;  // sanitised into off by the checks
     pa.offsets_out = off;
+    pa.validate = host_checks ? 0 : 1;
     pa.t = t;
     pa.v = v;
     pa.sky = sky;
@@ -263,7 +270,13 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     pa.dmax = dmax + 1;  // the coarse drift is not needed
     pa.err = err;
     if (e == cudaSuccess) e = launch_prep(pa, s);
+    // device checks: every peak's frequency too (the positions below cover only
+    // the peaks near each candidate, and the range searches need sorted FFTs)
+    if (e == cudaSuccess && !host_checks)
+        e = launch_validate_device_inputs(t, freq, off, v, sky, n, n_cand * n_ref, err, s);
     PrepArgs pr = pa;
+    pr.offsets_in = nullptr;  // sanitised and checked by the first launch
+    pr.validate = 0;
     pr.n_fdot = n_rows;
     pr.fdot_min = 0.0;
     pr.fdot_step = step_ref;
@@ -334,14 +347,16 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
             e = cudaMemsetAsync(prof[c], 0, 8 * (size_t)n_ref * n_f0r, s);
         if (e == cudaSuccess)
             e = launch_positions(freq, sub_off + (size_t)c * (n + 1), v, sky + 3 * (size_t)c * n_ref,
-                                 n, n_sub[c], n_ref, d.f0_min, kt, K, A[c], nullptr, err, false,
-                                 s, start + (size_t)c * n);
+                                 n, n_sub[c], n_ref, d.f0_min, kt, K, A[c], nullptr, err,
+                                 !host_checks, s, start + (size_t)c * n);
     }
     if (e != cudaSuccess) return cuda_error(e, "refinement positions");
     // the refined drift on the host, for the guard cells (as the device's D')
     double m = 0.0;
-    for (int32_t i = 0; i < n; ++i)
-        m = std::max(m, std::fabs(step_ref * ((pm->t_fft[i] - d.t_ref) * kt)));
+    for (int32_t i = 0; i < n; ++i) {
+        const double x = std::fabs(step_ref * ((pm->t_fft[i] - d.t_ref) * kt));
+        if (x > m && x < 1e9) m = x;  // non-finite times are left to the checks
+    }
     const int32_t guard = guard_for((unsigned long long)(m * 4294967296.0) + 4);
     const int nwarps = 16;
     const size_t smem = transform_smem_bytes(n_f0r, K, FH_MODE_START, nwarps, guard);
@@ -419,7 +434,7 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "refinement pick");
-    if (h_err & kErrRange) return set_error(FH_ERR_RANGE, "refined positions out of range");
+    if (h_err) return device_error_code(h_err);
     return FH_OK;
 }
 

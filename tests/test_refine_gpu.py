@@ -29,9 +29,11 @@ def fh():
     return fhmod
 
 
-def gpu_refine(fh, inp, pp, cells, rows, sky_ref, k_fdot):
+def gpu_refine(fh, inp, pp, cells, rows, sky_ref, k_fdot, checks=None):
     plan = fh.fh_create_plan(fh.make_desc(pp, inp.t.shape[0], 1, max(1, inp.n_peaks)))
     try:
+        if checks is not None:
+            fh.fh_plan_set_input_checks(plan, checks)
         return fh.fh_refine(plan, inp.t, inp.offsets, inp.freq, inp.v, cells, rows, sky_ref,
                             k_fdot)
     finally:
@@ -126,3 +128,29 @@ def test_the_50Hz_line_on_a_refined_sky(fh, oracle_mod, k_fdot):
     r = oracle_mod.refine(inp, pp, cells, rows, sky, k_fdot)
     check(g, r, len(sbs))
     assert g["count"][0] >= int(o["count"][0, sb, 0])
+
+
+def test_refine_with_device_checks(fh, oracle_mod):
+    """FH_CHECKS_DEVICE: the same refined candidates; unsorted frequencies are
+    reported by the call (it synchronises) as FH_ERR_UNSORTED."""
+    inp, pp = synth.random_case(336, n_fft=30, n_bins=40, n_fdot=12, n_dir=1, p=0.4)
+    cells = np.array([10, pp["n_f0"] // 2, pp["n_f0"] - 3], dtype=np.int32)
+    rows = np.array([3, 6, 9], dtype=np.int32)
+    sky = random_sky_ref(337, 3, 4)
+    g = gpu_refine(fh, inp, pp, cells, rows, sky, 3, checks=fh.FH_CHECKS_DEVICE)
+    check(g, oracle_mod.refine(inp, pp, cells, rows, sky, 3), 3)
+    # the two highest peaks of one FFT swapped, far from candidates near the
+    # bottom of the band: found by the check of every frequency, not only of
+    # the peaks near the candidates
+    f = inp.freq.copy()
+    b = int(inp.offsets[5]) - 1
+    f[b - 1], f[b] = f[b], f[b - 1]
+    low = np.array([8, 12], dtype=np.int32)
+    plan = fh.fh_create_plan(fh.make_desc(pp, inp.t.shape[0], 1, inp.n_peaks))
+    try:
+        fh.fh_plan_set_input_checks(plan, fh.FH_CHECKS_DEVICE)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_refine(plan, inp.t, inp.offsets, f, inp.v, low, rows[:2], sky[:2], 3)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
+    finally:
+        fh.fh_destroy_plan(plan)
