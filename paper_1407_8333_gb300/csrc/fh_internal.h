@@ -98,6 +98,16 @@ cudaError_t launch_positions(const double *freq, const int64_t *offsets, const d
                              double f0_min, double kt, int32_t k_over, int64_t *A,
                              double *out_r, int32_t *err, bool validate, cudaStream_t s,
                              const int64_t *src = nullptr);
+// positions of n_batch peakmaps (refinement): batch c has offsets
+// offsets + c (n_fft + 1), source index src + c n_fft, sky + 3 c n_dir, its peak
+// count n_peaks[c] (device) and its positions at A + a_base[c] (device),
+// direction-major as for launch_positions
+cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
+                                     const double *v, const double *sky, int32_t n_fft,
+                                     int32_t n_dir, int32_t n_batch, const int64_t *a_base,
+                                     const int64_t *n_peaks, double f0_min, double kt,
+                                     int32_t k_over, int64_t *A, int32_t *err, bool validate,
+                                     const int64_t *src, cudaStream_t s);
 cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
                                     int64_t *out, int32_t *err, cudaStream_t s);
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,

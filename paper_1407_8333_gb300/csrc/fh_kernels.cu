@@ -13,6 +13,7 @@
 // and the results are the IEEE values of the operations in the stated order.
 // The final floor(x 2^32) of a peak position is taken exactly from the IEEE
 // fields of x with integer operations.  After it the path is integer only.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 #include <utility>
@@ -28,6 +29,11 @@ constexpr int kPosFfts = 8;
 constexpr int kPosThreads = 256;
 
 // ---------------------------------------------------------------- a1 + a2
+// several peakmaps in one launch (see positions_kernel); null a_base: one
+struct PosBatch {
+    const int64_t *a_base, *n_peaks;
+};
+
 // floor(x 2^32) for |x| < 2^28, exactly: x = m 2^(e - 1075) with m the
 // significand (hidden bit included for normal numbers), so x 2^32 =
 // m 2^(e - 1043), a left shift by at most 7 bits, or a right shift whose
@@ -64,8 +70,18 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
                  int64_t n_peaks, double f0_min, double kt, double cshift,
                  int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
-                 int32_t validate, const int64_t *__restrict__ src)
+                 int32_t validate, const int64_t *__restrict__ src, PosBatch batch)
 {
+    // batches (refinement): block z is one peakmap of several, each with its own
+    // offsets, source index, sky directions, output base and peak count
+    if (batch.a_base) {
+        const int c = blockIdx.z;
+        offsets += (int64_t)c * (n_fft + 1);
+        src += (int64_t)c * n_fft;
+        sky += 3 * (int64_t)c * gridDim.y;
+        A += batch.a_base[c];
+        n_peaks = batch.n_peaks[c];
+    }
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
     __shared__ int64_t src_s[kPosFfts];  // where each FFT's peaks start in freq
@@ -1197,8 +1213,30 @@ cudaError_t launch_positions(const double *freq, const int64_t *offsets, const d
     dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
     positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
                                                   kt, cshift, A, out_r, err, validate ? 1 : 0,
-                                                  src);
+                                                  src, PosBatch{nullptr, nullptr});
     return cudaGetLastError();
+}
+
+cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
+                                     const double *v, const double *sky, int32_t n_fft,
+                                     int32_t n_dir, int32_t n_batch, const int64_t *a_base,
+                                     const int64_t *n_peaks, double f0_min, double kt,
+                                     int32_t k_over, int64_t *A, int32_t *err, bool validate,
+                                     const int64_t *src, cudaStream_t s)
+{
+    if (n_fft <= 0 || n_dir <= 0 || n_batch <= 0) return cudaSuccess;
+    const double cshift = 0.5 - 0.5 * (double)k_over;
+    for (int32_t b0 = 0; b0 < n_batch; b0 += 65535) {
+        const int32_t nb = std::min(65535, n_batch - b0);
+        dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir, nb);
+        positions_kernel<<<grid, kPosThreads, 0, s>>>(
+            freq, offsets + (int64_t)b0 * (n_fft + 1), v, sky + 3 * (int64_t)b0 * n_dir, n_fft,
+            0, f0_min, kt, cshift, A, nullptr, err, validate ? 1 : 0, src + (int64_t)b0 * n_fft,
+            PosBatch{a_base + b0, n_peaks + b0});
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,

@@ -335,21 +335,40 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sub_off, h_off.data(), 8 * h_off.size(), cudaMemcpyHostToDevice, s);
     // positions, profiles and windows of every candidate
+    // one allocation each for all candidates' positions and profiles
     std::vector<int64_t *> A(n_cand, nullptr);
     std::vector<uint64_t *> prof(n_cand, nullptr);
-    std::vector<int2 *> win(n_cand, nullptr);
     const int32_t n_slabs = (n_rows + kRows - 1) / kRows;
-    for (int32_t c = 0; c < n_cand && e == cudaSuccess; ++c) {
-        e = sc.get(&A[c], (size_t)n_ref * std::max<int64_t>(1, n_sub[c]));
-        if (e == cudaSuccess) e = sc.get(&prof[c], (size_t)n_ref * n_f0r);
-        if (e == cudaSuccess) e = sc.get(&win[c], (size_t)n_ref * n_slabs * std::max(1, n));
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(prof[c], 0, 8 * (size_t)n_ref * n_f0r, s);
-        if (e == cudaSuccess)
-            e = launch_positions(freq, sub_off + (size_t)c * (n + 1), v, sky + 3 * (size_t)c * n_ref,
-                                 n, n_sub[c], n_ref, d.f0_min, kt, K, A[c], nullptr, err,
-                                 !host_checks, s, start + (size_t)c * n);
+    size_t a_total = 0;
+    for (int32_t c = 0; c < n_cand; ++c)
+        a_total += (size_t)n_ref * std::max<int64_t>(1, n_sub[c]);
+    const size_t prof_each = (size_t)n_ref * n_f0r;
+    int64_t *a_all = nullptr;
+    uint64_t *prof_all = nullptr;
+    if (e == cudaSuccess) e = sc.get(&a_all, a_total);
+    if (e == cudaSuccess) e = sc.get(&prof_all, prof_each * n_cand);
+    if (e == cudaSuccess) e = cudaMemsetAsync(prof_all, 0, 8 * prof_each * n_cand, s);
+    size_t a_at = 0;
+    for (int32_t c = 0; c < n_cand; ++c) {
+        A[c] = a_all + a_at;
+        a_at += (size_t)n_ref * std::max<int64_t>(1, n_sub[c]);
+        prof[c] = prof_all + prof_each * c;
     }
+    // every candidate's positions in one launch
+    std::vector<int64_t> h_batch(2 * (size_t)n_cand);
+    for (int32_t c = 0; c < n_cand; ++c) {
+        h_batch[c] = A[c] - a_all;
+        h_batch[n_cand + c] = n_sub[c];
+    }
+    int64_t *d_batch = nullptr;
+    if (e == cudaSuccess) e = sc.get(&d_batch, h_batch.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_batch, h_batch.data(), 8 * h_batch.size(), cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess)
+        e = launch_positions_batched(freq, sub_off, v, sky, n, n_ref, n_cand, d_batch,
+                                     d_batch + n_cand, d.f0_min, kt, K, a_all, err, !host_checks,
+                                     start, s);
     if (e != cudaSuccess) return cuda_error(e, "refinement positions");
     // the refined drift on the host, for the guard cells (as the device's D')
     double m = 0.0;
@@ -378,7 +397,9 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
             j.err = err;
             j.weights = nullptr;
             j.count_bound = n_sub[c];
-            j.windows = win[c];
+            // no window table: a candidate's ranges hold a few peaks per FFT, so
+            // the transform's own binary search per FFT costs less than a pre-pass
+            j.windows = nullptr;
             j.n_peaks = n_sub[c];
             j.n_fft = n;
             j.n_f0 = n_f0r;
@@ -392,8 +413,7 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm,
             j.item_begin = items;
             j.n_items = (int64_t)n_slabs * n_ref;
             items += j.n_items;
-            e = launch_windows(j, win[c], s);
-            if (e != cudaSuccess) return cuda_error(e, "refinement windows");
+
         }
         const int32_t grid = (int32_t)std::min<int64_t>(items, (int64_t)n_sm * bps);
         e = launch_transform(FH_MODE_START, tbl, items, grid, nwarps, smem, guard, s);
