@@ -108,8 +108,6 @@ cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
                                      const int64_t *n_peaks, double f0_min, double kt,
                                      int32_t k_over, int64_t *A, int32_t *err, bool validate,
                                      const int64_t *src, cudaStream_t s);
-cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
-                                    int64_t *out, int32_t *err, cudaStream_t s);
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
                                           const int64_t *offsets, const double *v,
                                           const double *sky, int32_t n_fft, int32_t n_dir,

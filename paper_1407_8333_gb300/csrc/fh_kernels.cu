@@ -275,52 +275,10 @@ __global__ void shift_tables_kernel(const double *__restrict__ t, int32_t n_fft,
 }
 
 // ---------------------------------------------------------------- device inputs
-// One block: copy offsets[0..n_fft] into a valid CSR (clamped to [0, n_peaks],
-// made non-decreasing by a running maximum, last entry = n_peaks) and flag
-// any entry that had to change.  Later kernels index peaks only through the
-// sanitised copy, so a bad device peakmap cannot make them read out of range.
-__global__ void __launch_bounds__(1024)
-sanitize_offsets_kernel(const int64_t *__restrict__ in, int32_t n_fft, int64_t n_peaks,
-                        int64_t *__restrict__ out, int32_t *err)
-{
-    __shared__ int64_t wmax[32];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    bool bad = false;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base <= n_fft; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        int64_t x = 0;
-        if (i <= n_fft) {
-            x = in[i];
-            if (x < 0 || x > n_peaks) bad = true;
-            if (i == 0 && x != 0) bad = true;
-            if (i == n_fft && x != n_peaks) bad = true;
-            if (i > 0 && x < in[i - 1]) bad = true;
-            x = x < 0 ? 0 : (x > n_peaks ? n_peaks : x);
-            if (i == 0) x = 0;
-        }
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o && y > x) x = y;
-        }
-        if (lane == 31) wmax[warp] = x;
-        __syncthreads();
-        int64_t pre = carry;
-        for (int w = 0; w < warp; ++w) pre = wmax[w] > pre ? wmax[w] : pre;
-        if (pre > x) x = pre;
-        if (i <= n_fft) out[i] = (i == n_fft) ? n_peaks : x;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = x;
-        __syncthreads();
-    }
-    if (bad) atomicOr(err, kErrCsr);
-}
-
-// Flags non-finite / unordered device inputs: one warp per FFT (its peaks are
-// read coalesced and compared with their left neighbour) and one thread per
-// sky direction.
+// Flags non-finite / unordered device inputs (the refined-grid search under
+// device-side checks): one warp per FFT (its peaks are read coalesced and
+// compared with their left neighbour, through an already sanitised CSR) and
+// one thread per sky direction.
 __global__ void validate_device_inputs_kernel(const double *__restrict__ t,
                                               const double *__restrict__ freq,
                                               const int64_t *__restrict__ offsets,
@@ -1237,13 +1195,6 @@ cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-cudaError_t launch_sanitize_offsets(const int64_t *in, int32_t n_fft, int64_t n_peaks,
-                                    int64_t *out, int32_t *err, cudaStream_t s)
-{
-    sanitize_offsets_kernel<<<1, 1024, 0, s>>>(in, n_fft, n_peaks, out, err);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
