@@ -217,3 +217,32 @@ def test_frequencies_for_a_t_fft_that_is_not_a_power_of_two(fh, pm):
         assert np.array_equal(host(gb), wb)
         assert np.array_equal(host(gf).view(np.uint64),
                               pm.peak_frequencies(wb, s.k0, s.t_fft).view(np.uint64))
+
+
+def test_select_captured_in_a_cuda_graph(fh, pm):
+    """The asynchronous selection with a workspace allocates nothing, so it can
+    be captured once and replayed; every replay gives the oracle's peakmap."""
+    import torch
+    s = synth.spectra_case(36, 40, 9000, wander_amp=30.0, wander_f=(50.1, 50.6), wander_width=9)
+    wo, wb = pm.select_peaks(s.s_p, s.s_ar, 2.5)
+    sp, sa = dev(s.s_p), dev(s.s_ar)
+    cap = len(wb) + 64
+    out = (torch.empty(41, dtype=torch.int64, device="cuda"),
+           torch.empty(cap, dtype=torch.int32, device="cuda"),
+           torch.empty(cap, dtype=torch.float64, device="cuda"))
+    ws = torch.empty(fh.fh_peakmap_select_workspace(40, 9000), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        fh.fh_peakmap_select(sp, sa, 2.5, s.k0, s.t_fft, out=out, workspace=ws, stream=st)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        fh.fh_peakmap_select(sp, sa, 2.5, s.k0, s.t_fft, out=out, workspace=ws, stream=st)
+    for rep in range(3):
+        out[0].fill_(-1)
+        out[1].fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host(out[0]), wo)
+        assert np.array_equal(host(out[1])[:len(wb)], wb)
+        assert np.array_equal(host(out[2])[:len(wb)], pm.peak_frequencies(wb, s.k0, s.t_fft))
