@@ -72,6 +72,7 @@ struct SelArgs {
     float theta;
     uint32_t *mask;     // [fft][word]
     int32_t *seg_count; // [fft][seg]
+    int32_t *err;       // bulk-copy waits that ran out
 };
 
 __device__ __forceinline__ float ratio_at(const float *sp, const float *sa, int j, int n_bins)
@@ -80,6 +81,97 @@ __device__ __forceinline__ float ratio_at(const float *sp, const float *sa, int 
     // n_bins - 1 are false), so any value serves there
     return (j >= 0 && j < n_bins) ? __fdiv_rn(__ldg(sp + j), __ldg(sa + j)) : 0.0f;
 }
+
+constexpr int kBulkPolls = 1 << 22;  // a bulk copy always completes; this only bounds the wait
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// The selection pass with the two spectrum rows of a tile brought into shared
+// memory by bulk copies (cp.async.bulk, the 1-D form of the tensor memory
+// accelerator) that complete on one mbarrier: 32 KB per block in flight at
+// once, no registers held by loads.  Used when both spectra are 16-byte
+// aligned, the pitch is a multiple of 4 floats and so is n_bins, so that every
+// copy starts on a 16-byte boundary and moves a multiple of 16 bytes.  The
+// ratios are formed in place; flags and counts as in select_mask_kernel.
+__global__ void __launch_bounds__(kSegThreads) select_mask_bulk_kernel(const SelArgs a)
+{
+    __shared__ __align__(128) float p_s[kSegBins + 8];  // p_s[4 + k]: S_P, then R, of bin j0 + k
+    __shared__ __align__(128) float q_s[kSegBins];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int32_t warp_cnt[kSegThreads / 32];
+    const int row = blockIdx.y, seg = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = seg * kSegBins;
+    const int nb = min(kSegBins, a.n_bins - j0);
+    const float *sp = a.s_p + (int64_t)row * a.pitch;
+    const float *sa = a.s_ar + (int64_t)row * a.pitch;
+    const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (tid == 0) {
+        const uint32_t bytes = 4u * (uint32_t)nb;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"(2u * bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(p_s + 4)),
+            "l"(sp + j0), "r"(bytes), "r"(bar_a)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(q_s)),
+            "l"(sa + j0), "r"(bytes), "r"(bar_a)
+            : "memory");
+    }
+    // the halo bins (outside the copies)
+    if (tid == 32) p_s[3] = ratio_at(sp, sa, j0 - 1, a.n_bins);
+    if (tid == 64) p_s[4 + kSegBins] = ratio_at(sp, sa, j0 + kSegBins, a.n_bins);
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    bool done = false;
+    for (int it = 0; it < kBulkPolls && !done; ++it) done = mbar_try_wait(bar_a, 0);
+    if (!done) {
+        // never expected: report, then still wait (bounded) for the block's own
+        // copies before the shared memory is given up
+        if (tid == 0) atomicOr(a.err, kErrRange);
+        for (int it = 0; it < kBulkPolls && !done; ++it) done = mbar_try_wait(bar_a, 0);
+    }
+    for (int k = tid; k < nb; k += kSegThreads) p_s[4 + k] = __fdiv_rn(p_s[4 + k], q_s[k]);
+    __syncthreads();
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kSegWords / (kSegThreads / 32); ++k) {
+        const int wl = k * (kSegThreads / 32) + warp;  // word of the segment
+        const int loc = wl * 32 + lane;
+        const int j = j0 + loc;
+        const float r = p_s[4 + loc];
+        const bool f = j >= 1 && j <= a.n_bins - 2 && r > a.theta && r > p_s[3 + loc] &&
+                       r > p_s[5 + loc];
+        const unsigned word = __ballot_sync(kFull, f);
+        const int w = seg * kSegWords + wl;
+        if (lane == 0 && w < a.n_words) a.mask[(int64_t)row * a.n_words + w] = word;
+        cnt += __popc(word);
+    }
+    if (lane == 0) warp_cnt[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        int c = lane < kSegThreads / 32 ? warp_cnt[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0) a.seg_count[(int64_t)row * a.n_seg + seg] = c;
+    }
+}
+
 
 // A block takes 4096 bins of one FFT.  Loads: 16 bins per thread, as four
 // float4 per spectrum when the rows are 16-byte aligned (VEC), so that each
@@ -597,7 +689,7 @@ int64_t fh_peakmap_select_workspace(int32_t n_fft, int32_t n_bins)
     const int64_t n_seg = (n_bins + kSegBins - 1) / kSegBins;
     const int64_t n_words = (n_bins + 31) / 32;
     auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
-    return up(4 * n_fft * n_words) + up(4 * n_fft * n_seg) + up(8 * (n_fft * n_seg + 1));
+    return up(4 * n_fft * n_words) + up(4 * n_fft * n_seg) + up(8 * (n_fft * n_seg + 1)) + 256;
 }
 
 int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_t n_bins,
@@ -627,7 +719,7 @@ int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_
     if (n_fft > 65535) return set_error(FH_ERR_INVALID_ARG, "at most 65535 FFTs per call");
     Scratch sc(s);
     uint32_t *mask = nullptr;
-    int32_t *seg_count = nullptr;
+    int32_t *seg_count = nullptr, *err = nullptr;
     int64_t *seg_base = nullptr;
     cudaError_t e = cudaSuccess;
     const int64_t need = fh_peakmap_select_workspace(n_fft, n_bins);
@@ -641,16 +733,22 @@ int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_
         seg_count = reinterpret_cast<int32_t *>(w + up(4 * (int64_t)n_fft * n_words));
         seg_base = reinterpret_cast<int64_t *>(w + up(4 * (int64_t)n_fft * n_words) +
                                                up(4 * (int64_t)n_fft * n_seg));
+        err = reinterpret_cast<int32_t *>(w + need - 256);
     } else {
         e = sc.get(&mask, (size_t)n_fft * n_words);
         if (e == cudaSuccess) e = sc.get(&seg_count, (size_t)n_fft * n_seg);
         if (e == cudaSuccess) e = sc.get(&seg_base, (size_t)n_fft * n_seg + 1);
+        if (e == cudaSuccess) e = sc.get(&err, 4);
         if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync (peakmap)");
     }
-    SelArgs a{s_p, s_ar, pitch, n_fft, n_bins, n_seg, n_words, theta, mask, seg_count};
+    SelArgs a{s_p, s_ar, pitch, n_fft, n_bins, n_seg, n_words, theta, mask, seg_count, err};
     const bool vec = ((reinterpret_cast<uintptr_t>(s_p) | reinterpret_cast<uintptr_t>(s_ar)) &
                       15u) == 0 && (pitch & 3) == 0;
-    if (vec)
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync (peakmap)");
+    if (vec && (n_bins & 3) == 0)
+        select_mask_bulk_kernel<<<dim3(n_seg, n_fft), kSegThreads, 0, s>>>(a);
+    else if (vec)
         select_mask_kernel<true><<<dim3(n_seg, n_fft), kSegThreads, 0, s>>>(a);
     else
         select_mask_kernel<false><<<dim3(n_seg, n_fft), kSegThreads, 0, s>>>(a);
@@ -669,9 +767,12 @@ int fh_peakmap_select(const float *s_p, const float *s_ar, int32_t n_fft, int32_
     if (e != cudaSuccess) return cuda_error(e, "peak selection");
     if (!n_peaks) return FH_OK;  // asynchronous: the total is offsets[n_fft]
     int64_t total = 0;
+    int32_t h_err = 0;
     e = cudaMemcpyAsync(&total, offsets + n_fft, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "peak selection");
+    if (h_err) return set_error(FH_ERR_TIMEOUT, "peak selection: a bulk-copy wait ran out");
     *n_peaks = total;
     if (total > capacity)
         return set_error(FH_ERR_CAPACITY, "%lld peaks selected, capacity %lld", (long long)total,
