@@ -174,3 +174,35 @@ def test_persistency_veto_removes_constant_lines(pm):
     assert as_rows(o2, b2) == want
     # the noise counts are binomial(300, p0-ish): median near 300 p0
     assert abs(m1 - 300 * 0.0755) < 3.0
+
+
+def constant_line_case():
+    """A peakmap (built by the oracle's selection) with constant lines at 50.1
+    and 50.4 Hz in 80 % of 400 FFTs, for the frequency-Hough transform without
+    Doppler correction (v = 0) on three spin-down rows around 0."""
+    import oracle
+    s = synth.spectra_case(17, 400, 4096, const_lines=(50.1, 50.4), const_amp=40.0,
+                           const_frac=0.8)
+    o, b = oracle.peakmap.select_peaks(s.s_p, s.s_ar, 2.5)
+    freq = oracle.peakmap.peak_frequencies(b, s.k0, s.t_fft)
+    inp = synth.Inputs(w=None, t=s.t, offsets=o, freq=freq, v=np.zeros((len(s.t), 3)),
+                       sky=np.array([[1.0, 0.0, 0.0]]))
+    t_obs = s.t[-1] - s.t[0] + s.t_fft
+    step = 1.0 / (s.t_fft * t_obs)
+    pp = dict(t_fft=s.t_fft, k_over=10, f0_min=s.k0 / s.t_fft, n_f0=4096 * 10, fdot_min=-step,
+              fdot_step=step, n_fdot=3, t_ref=0.5 * (s.t[0] + s.t[-1]), subband_cells=4096 * 10,
+              top_k=2, excl_cells=40, sep_cells=80, n_thr=0, p0=0.0755)
+    return s, inp, pp
+
+
+def test_constant_lines_found_by_the_transform_without_doppler(oracle_mod):
+    """Sec. "Removal of spectral lines of constant frequency", third option: the
+    transform on the uncorrected peakmap (v = 0) puts the constant lines at
+    spin-down 0 as the two strongest candidates, at their own frequencies."""
+    s, inp, pp = constant_line_case()
+    o = oracle_mod.search(inp, pp)
+    rows = o["row"][0, 0, :2]
+    f0 = np.sort(o["f0"][0, 0, :2])
+    assert list(rows) == [1, 1]                       # the fdot = 0 row
+    assert np.all(np.abs(f0 - np.array([50.1, 50.4])) < 1.0 / s.t_fft)
+    assert np.all(o["count"][0, 0, :2] > 0.7 * len(s.t))

@@ -246,3 +246,27 @@ def test_select_captured_in_a_cuda_graph(fh, pm):
         assert np.array_equal(host(out[0]), wo)
         assert np.array_equal(host(out[1])[:len(wb)], wb)
         assert np.array_equal(host(out[2])[:len(wb)], pm.peak_frequencies(wb, s.k0, s.t_fft))
+
+
+def test_constant_lines_by_the_transform_without_doppler(fh, oracle_mod):
+    """The third constant-line method (the transform at v = 0 near fdot = 0) is
+    the library's ordinary path with zero velocities: its candidates equal the
+    oracle's, the lines at spin-down 0."""
+    import torch
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_peakmap_pins import constant_line_case
+    s, inp, pp = constant_line_case()
+    plan = fh.fh_create_plan(fh.make_desc(pp, inp.t.shape[0], 1, inp.n_peaks))
+    try:
+        args = [torch.from_numpy(np.ascontiguousarray(x)).cuda()
+                for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+        fh.fh_correct_doppler(plan, *args)
+        fh.fh_transform(plan, 0, 1)
+        cand = fh.fh_select_candidates(plan, 0, 1)
+    finally:
+        fh.fh_destroy_plan(plan)
+    o = oracle_mod.search(inp, pp)
+    for k in ("row", "cell", "count"):
+        assert np.array_equal(cand[k][:2].astype(np.int64), o[k][0, 0, :2].astype(np.int64)), k
+    assert list(cand["row"][:2]) == [1, 1]
