@@ -397,25 +397,6 @@ __global__ void coin_write_kernel(const CoinArgs a, const int64_t *off, int64_t 
     }
 }
 
-struct Scratch {
-    cudaStream_t s;
-    std::vector<void *> bufs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
-    template <typename T>
-    cudaError_t get(T **p, size_t n)
-    {
-        void *q = nullptr;
-        const cudaError_t e = cudaMallocAsync(&q, (n ? n : 1) * sizeof(T), s);
-        if (e == cudaSuccess) bufs.push_back(q);
-        *p = static_cast<T *>(q);
-        return e;
-    }
-    ~Scratch()
-    {
-        for (void *b : bufs) cudaFreeAsync(b, s);
-    }
-};
-
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
 // buckets of n candidates by the frequencies fs: bkt, start (nb + 1), order

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fh.h"
 
@@ -136,6 +137,29 @@ cudaError_t launch_smem_atomic_bench(int32_t variant, int32_t iters, int32_t gri
 // null) and strided[r] = pref[r * stride] for r = 0 .. n / stride (may be null).
 cudaError_t launch_exclusive_scan(const int32_t *cnt, int64_t n, int64_t *pref, int32_t stride,
                                   int64_t *strided, cudaStream_t s);
+
+// Device buffers of one call, taken stream-ordered (cudaMallocAsync) and
+// returned stream-ordered when the object goes out of scope.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> bufs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    template <typename T>
+    cudaError_t get(T **p, size_t n)
+    {
+        void *q = nullptr;
+        const cudaError_t e = cudaMallocAsync(&q, (n ? n : 1) * sizeof(T), s);
+        if (e == cudaSuccess) bufs.push_back(q);
+        *p = static_cast<T *>(q);
+        return e;
+    }
+    ~Scratch()
+    {
+        for (void *b : bufs) cudaFreeAsync(b, s);
+    }
+};
 
 // ---- host helpers (fh_api.cu) ----
 int set_error(int code, const char *fmt, ...);

@@ -589,26 +589,6 @@ __global__ void filter_write_kernel(const int64_t *o, const int32_t *bins, int32
     }
 }
 
-// stream-ordered scratch of one call, returned at the end
-struct Scratch {
-    cudaStream_t s;
-    std::vector<void *> bufs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
-    template <typename T>
-    cudaError_t get(T **p, size_t n)
-    {
-        void *q = nullptr;
-        const cudaError_t e = cudaMallocAsync(&q, (n ? n : 1) * sizeof(T), s);
-        if (e == cudaSuccess) bufs.push_back(q);
-        *p = static_cast<T *>(q);
-        return e;
-    }
-    ~Scratch()
-    {
-        for (void *b : bufs) cudaFreeAsync(b, s);
-    }
-};
-
 }  // namespace
 
 cudaError_t launch_exclusive_scan(const int32_t *cnt, int64_t n, int64_t *pref, int32_t stride,

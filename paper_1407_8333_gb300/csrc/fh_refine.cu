@@ -160,26 +160,6 @@ __global__ void refine_pick_kernel(const PickArgs a)
     a.out[c] = r;
 }
 
-// stream-ordered device buffers of one call, freed (stream-ordered) at the end
-struct Scratch {
-    cudaStream_t s;
-    std::vector<void *> bufs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
-    template <typename T>
-    cudaError_t get(T **p, size_t n)
-    {
-        void *q = nullptr;
-        const cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(n, 1) * sizeof(T), s);
-        if (e == cudaSuccess) bufs.push_back(q);
-        *p = static_cast<T *>(q);
-        return e;
-    }
-    ~Scratch()
-    {
-        for (void *b : bufs) cudaFreeAsync(b, s);
-    }
-};
-
 }  // namespace
 
 namespace fh {
