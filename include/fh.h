@@ -370,6 +370,21 @@ int fh_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
                     const double *win, int32_t *pairs, int64_t capacity, int64_t *n_pairs,
                     int32_t *n_match1, int32_t *n_match2, void *stream);
 
+/* Coincidences among clusters (Sec. "Candidate clustering and coincidences"):
+ * two clusters coincide when at least one pair of their members does; each
+ * coincident pair of clusters keeps only its nearest coincident pair, the
+ * smallest distance of Eq. norm at the common time t_c (ties: the smallest
+ * (i, j)).  label1 / label2 (DEVICE): the clusters of fh_cluster; pairs
+ * (DEVICE, 2 x n_pairs int32): coincident pairs in strictly increasing (i, j)
+ * order, as fh_coincidences writes them (checked).  out (DEVICE, 4 x capacity
+ * int32): cluster 1, cluster 2, i, j of each kept pair, in (i, j) order;
+ * out_d (DEVICE, nullable): its distance; *n_out (HOST).  Synchronises. */
+int fh_cluster_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
+                            const int32_t *label1, const fh_cand_params *c2, int32_t n2,
+                            double t_ref2, const int32_t *label2, double t_c,
+                            const int32_t *pairs, int64_t n_pairs, int32_t *out, double *out_d,
+                            int64_t capacity, int64_t *n_out, void *stream);
+
 /* ---- refined grid around coarse candidates -------------------------------- */
 
 /* Refined-grid search (Sec. "Refined Grid in the parameter space"): one

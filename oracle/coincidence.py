@@ -17,7 +17,11 @@ coincidences"):
 * coincidences between two sets: each candidate's frequency is referred to a
   common time, f' = f + fdot (t_c - t_ref); two candidates coincide when, in
   every parameter, k <= the caller's window (in bins, the sum of the two sets'
-  half-windows n_1 + n_2 of the appendix).
+  half-windows n_1 + n_2 of the appendix);
+* coincidences among clusters: two clusters coincide when at least one pair of
+  their members does, and each coincident pair of clusters keeps only its
+  nearest coincident pair (smallest distance at the common time; ties to the
+  smallest (i, j)).
 
 Every number is binary64 in the order written (numpy evaluates the array
 expressions operation by operation, no fused multiply-add).
@@ -119,3 +123,22 @@ def coincidences(cands1, cands2, t_ref1: float, t_ref2: float, t_c: float, win):
         n2[hit] += 1
     p = np.array(pairs, dtype=np.int64).reshape(-1, 2)
     return p, n1, n2
+
+
+def cluster_coincidences(cands1, cands2, t_ref1: float, t_ref2: float, t_c: float, label1,
+                         label2, pairs):
+    """Each coincident pair of clusters (label1[i], label2[j]) with its nearest
+    coincident pair (i, j) and their distance, in the order of those pairs.
+    Returns (rows (k, 4) int64: cluster 1, cluster 2, i, j; distances (k,))."""
+    a = shift_to(cands1, t_ref1, t_c)
+    b = shift_to(cands2, t_ref2, t_c)
+    best = {}
+    for i, j in np.asarray(pairs, dtype=np.int64).reshape(-1, 2):
+        d = float(distance(a[i], b[j]))
+        key = (int(label1[i]), int(label2[j]))
+        cand = (d, int(i), int(j))
+        if key not in best or cand < best[key]:
+            best[key] = cand
+    reps = sorted((i, j, key, d) for key, (d, i, j) in best.items())
+    rows = np.array([(key[0], key[1], i, j) for i, j, key, d in reps], dtype=np.int64)
+    return rows.reshape(-1, 4), np.array([d for *_, d in reps], dtype=np.float64)

@@ -397,6 +397,116 @@ __global__ void coin_write_kernel(const CoinArgs a, const int64_t *off, int64_t 
     }
 }
 
+// ---------------------------------------------------------------- cluster coincidences
+// Each coincident pair of clusters keeps its nearest coincident pair.  A hash
+// table (open addressing, 64-bit keys cluster1 << 32 | cluster2, twice as many
+// slots as pairs) gives every pair of clusters a slot; the slot keeps the
+// smallest distance (atomic minimum of the bits of a non-negative double, which
+// order like the values) and then the smallest pair index at that distance.
+// The pairs come in (i, j) order, so the representatives, compacted in pair
+// order, come out in (i, j) order too.
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+struct CCArgs {
+    const fh_cand_params *c1, *c2;
+    const int32_t *label1, *label2, *pairs;
+    int32_t n1, n2;
+    int64_t n_pairs;
+    double dt1, dt2;  // t_c - t_ref of each set
+    unsigned long long *keys, *dmin, *best;
+    int64_t tmask;
+    int32_t *slot, *flag;
+    double *dist;
+    int32_t *err;
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void cc_insert_kernel(const CCArgs a)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = a.pairs[2 * p], j = a.pairs[2 * p + 1];
+        bool ok = i >= 0 && i < a.n1 && j >= 0 && j < a.n2;
+        if (ok && p > 0) {
+            const int32_t pi = a.pairs[2 * p - 2], pj = a.pairs[2 * p - 1];
+            ok = pi < i || (pi == i && pj < j);  // strictly increasing (i, j)
+        }
+        const int32_t la = ok ? a.label1[i] : -1, lb = ok ? a.label2[j] : -1;
+        ok = ok && la >= 0 && la < a.n1 && lb >= 0 && lb < a.n2;
+        if (!ok) {
+            atomicOr(a.err, kErrInvalid);
+            a.slot[p] = -1;
+            continue;
+        }
+        const unsigned long long key = ((unsigned long long)(uint32_t)la << 32) | (uint32_t)lb;
+        int64_t h = (int64_t)(mix64(key) & (unsigned long long)a.tmask);
+        int32_t at = -1;
+        for (int64_t it = 0; it <= a.tmask; ++it) {  // the table is at most half full
+            const unsigned long long old = atomicCAS(a.keys + h, kEmptyKey, key);
+            if (old == kEmptyKey || old == key) {
+                at = (int32_t)h;
+                break;
+            }
+            h = (h + 1) & a.tmask;
+        }
+        if (at < 0) {
+            atomicOr(a.err, kErrRange);
+            a.slot[p] = -1;
+            continue;
+        }
+        const fh_cand_params x = a.c1[i], y = a.c2[j];
+        const double fx = __dadd_rn(x.f, __dmul_rn(x.fdot, a.dt1));
+        const double fy = __dadd_rn(y.f, __dmul_rn(y.fdot, a.dt2));
+        const double d = norm_distance(x, y, fx, fy);
+        a.dist[p] = d;
+        a.slot[p] = at;
+        atomicMin(a.dmin + at, (unsigned long long)__double_as_longlong(d));
+    }
+}
+
+__global__ void cc_best_kernel(const CCArgs a)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t h = a.slot[p];
+        if (h >= 0 &&
+            (unsigned long long)__double_as_longlong(a.dist[p]) == a.dmin[h])
+            atomicMin(a.best + h, (unsigned long long)p);
+    }
+}
+
+__global__ void cc_flag_kernel(const CCArgs a)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t h = a.slot[p];
+        a.flag[p] = (h >= 0 && a.best[h] == (unsigned long long)p) ? 1 : 0;
+    }
+}
+
+__global__ void cc_write_kernel(const CCArgs a, const int64_t *off, int64_t capacity,
+                                int32_t *out, double *out_d)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (!a.flag[p]) continue;
+        const int64_t k = off[p];
+        if (k >= capacity) continue;
+        const int32_t i = a.pairs[2 * p], j = a.pairs[2 * p + 1];
+        out[4 * k] = a.label1[i];
+        out[4 * k + 1] = a.label2[j];
+        out[4 * k + 2] = i;
+        out[4 * k + 3] = j;
+        if (out_d) out_d[k] = a.dist[p];
+    }
+}
+
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
 // buckets of n candidates by the frequencies fs: bkt, start (nb + 1), order
@@ -581,6 +691,73 @@ int fh_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
     if (total > capacity)
         return set_error(FH_ERR_CAPACITY, "%lld coincident pairs, capacity %lld",
                          (long long)total, (long long)capacity);
+    return FH_OK;
+}
+
+int fh_cluster_coincidences(const fh_cand_params *c1, int32_t n1, double t_ref1,
+                            const int32_t *label1, const fh_cand_params *c2, int32_t n2,
+                            double t_ref2, const int32_t *label2, double t_c,
+                            const int32_t *pairs, int64_t n_pairs, int32_t *out, double *out_d,
+                            int64_t capacity, int64_t *n_out, void *stream)
+{
+    if (!n_out || n_pairs < 0 || n_pairs > ((int64_t)1 << 30) || capacity < 0 || n1 < 0 ||
+        n2 < 0 || (n_pairs > 0 && (!c1 || !c2 || !label1 || !label2 || !pairs)) ||
+        (capacity > 0 && !out))
+        return set_error(FH_ERR_INVALID_ARG, "bad candidate sets, labels, pairs or outputs");
+    if (!std::isfinite(t_ref1) || !std::isfinite(t_ref2) || !std::isfinite(t_c))
+        return set_error(FH_ERR_INVALID_ARG, "reference times must be finite");
+    *n_out = 0;
+    if (n_pairs == 0) return FH_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch sc(s);
+    int64_t tsize = 2;
+    while (tsize < 2 * n_pairs) tsize <<= 1;
+    unsigned long long *keys = nullptr, *dmin = nullptr, *best = nullptr;
+    int32_t *slot = nullptr, *flag = nullptr, *err = nullptr;
+    double *dist = nullptr;
+    int64_t *off = nullptr;
+    cudaError_t e = sc.get(&keys, (size_t)tsize);
+    if (e == cudaSuccess) e = sc.get(&dmin, (size_t)tsize);
+    if (e == cudaSuccess) e = sc.get(&best, (size_t)tsize);
+    if (e == cudaSuccess) e = sc.get(&slot, (size_t)n_pairs);
+    if (e == cudaSuccess) e = sc.get(&flag, (size_t)n_pairs);
+    if (e == cudaSuccess) e = sc.get(&dist, (size_t)n_pairs);
+    if (e == cudaSuccess) e = sc.get(&off, (size_t)n_pairs + 1);
+    if (e == cudaSuccess) e = sc.get(&err, 1);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync (cluster coincidences)");
+    e = cudaMemsetAsync(keys, 0xFF, 8 * (size_t)tsize, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmin, 0xFF, 8 * (size_t)tsize, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(best, 0xFF, 8 * (size_t)tsize, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, s);
+    CCArgs a{c1, c2, label1, label2, pairs, n1, n2, n_pairs, t_c - t_ref1, t_c - t_ref2,
+             keys, dmin, best, tsize - 1, slot, flag, dist, err};
+    const int grid = grid_for(n_pairs);
+    if (e == cudaSuccess) {
+        cc_insert_kernel<<<grid, 256, 0, s>>>(a);
+        cc_best_kernel<<<grid, 256, 0, s>>>(a);
+        cc_flag_kernel<<<grid, 256, 0, s>>>(a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_exclusive_scan(flag, n_pairs, off, 1, nullptr, s);
+    if (e == cudaSuccess && capacity > 0) {
+        cc_write_kernel<<<grid, 256, 0, s>>>(a, off, capacity, out, out_d);
+        e = cudaGetLastError();
+    }
+    int64_t total = 0;
+    int32_t h_err = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, off + n_pairs, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "cluster coincidences");
+    if (h_err & kErrInvalid)
+        return set_error(FH_ERR_INVALID_ARG, "pairs out of range or not in (i, j) order, or "
+                                             "labels out of range");
+    if (h_err) return set_error(FH_ERR_RANGE, "cluster-pair table full");
+    *n_out = total;
+    if (total > capacity)
+        return set_error(FH_ERR_CAPACITY, "%lld cluster pairs, capacity %lld", (long long)total,
+                         (long long)capacity);
     return FH_OK;
 }
 

@@ -105,6 +105,8 @@ _SIGS = {
     "fh_coincidences": ([_P, _i32, _f64, _P, _i32, _f64, _f64, _P, _P, _i64, _P, _P, _P, _P],
                         ctypes.c_int),
     "fh_plan_set_input_checks": ([_P, _i32], ctypes.c_int),
+    "fh_cluster_coincidences": ([_P, _i32, _f64, _P, _P, _i32, _f64, _P, _f64, _P, _i64, _P, _P,
+                                 _i64, _P, _P], ctypes.c_int),
     "fh_refine": ([_P, ctypes.POINTER(fh_peakmap), _P, _P, _P, _i32, _P, _i32, _i32, _P, _i64, _P],
                   ctypes.c_int),
     "fh_plan_set_timing": ([_P, _i32], ctypes.c_int),
@@ -398,6 +400,27 @@ def fh_peakmap_persistency_veto(offsets, bins, n_bins: int, k_sigma: float, k0: 
                                               _stream(stream)), "fh_peakmap_persistency_veto")
     k = n.value
     return o2, b2[:k], (f2[:k] if f2 is not None else None), hist, tuple(stats)
+
+
+def fh_cluster_coincidences(c1, c2, t_ref1: float, t_ref2: float, t_c: float, label1, label2,
+                            pairs, stream=None):
+    """The nearest coincident pair of each coincident pair of clusters: rows
+    (cluster 1, cluster 2, i, j) ((k, 4) device int32) and distances."""
+    torch = _torch()
+    a, b = _cands(c1), _cands(c2)
+    pairs = pairs.contiguous()  # kept referenced for the call
+    n_pairs = int(pairs.shape[0])
+    cap = max(1, n_pairs)
+    out = torch.empty((cap, 4), dtype=torch.int32, device=a.device)
+    dist = torch.empty(cap, dtype=torch.float64, device=a.device)
+    n = ctypes.c_int64(0)
+    _check(load().fh_cluster_coincidences(_dev_ptr(a), int(a.shape[0]), float(t_ref1),
+                                          _dev_ptr(label1), _dev_ptr(b), int(b.shape[0]),
+                                          float(t_ref2), _dev_ptr(label2), float(t_c),
+                                          _dev_ptr(pairs), n_pairs, _dev_ptr(out),
+                                          _dev_ptr(dist), cap, ctypes.byref(n), _stream(stream)),
+           "fh_cluster_coincidences")
+    return out[:n.value], dist[:n.value]
 
 
 def _cands(c):

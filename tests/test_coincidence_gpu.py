@@ -130,3 +130,36 @@ def test_twenty_thousand_candidates(fh, co):
     check_cluster(fh, co, a, 4.0)
     wp = check_coinc(fh, co, a, b, 1.0e6, 2.0e6, 1.5e6, (2, 2, 2, 2))
     assert {(i, i) for i in range(50)} <= {tuple(x) for x in wp}
+
+
+def test_cluster_coincidences_match_oracle(fh, co):
+    """Clusters of both sets, their coincident pairs, and the nearest pair of
+    each coincident pair of clusters: rows and distances equal the oracle's."""
+    import torch
+    seeds = synth.candidate_set(47, 0, 160, clusters=20, cluster_size=8)[::8, :4]
+    later = seeds.copy()
+    later[:, 2] += later[:, 3] * 1.0e6
+    a = synth.candidate_set(47, 1, 3000, signals=seeds, clusters=60, cluster_size=6)
+    b = synth.candidate_set(47, 2, 2800, signals=later, clusters=60, cluster_size=6)
+    da, db = dev(a), dev(b)
+    la, _ = fh.fh_cluster(da, 4.0)
+    lb, _ = fh.fh_cluster(db, 4.0)
+    pairs, _, _ = fh.fh_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, (3, 3, 3, 3))
+    rows, dist = fh.fh_cluster_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, la, lb, pairs)
+    wla, _ = co.cluster(a, 4.0)
+    wlb, _ = co.cluster(b, 4.0)
+    wp, _, _ = co.coincidences(a, b, 1.0e6, 2.0e6, 1.5e6, (3, 3, 3, 3))
+    wrows, wd = co.cluster_coincidences(a, b, 1.0e6, 2.0e6, 1.5e6, wla, wlb, wp)
+    assert np.array_equal(rows.cpu().numpy(), wrows)
+    assert np.array_equal(dist.cpu().numpy().view(np.uint64), wd.view(np.uint64))
+    assert len(wrows) < len(wp)
+    # pairs out of (i, j) order, or out of range, are refused
+    bad = pairs.flip(0).contiguous()
+    if bad.shape[0] > 1:
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_cluster_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, la, lb, bad)
+        assert ei.value.code == fh.FH_ERR_INVALID_ARG
+    out = torch.tensor([[0, 5000]], dtype=torch.int32, device="cuda")
+    with pytest.raises(fh.FHError) as ei:
+        fh.fh_cluster_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, la, lb, out)
+    assert ei.value.code == fh.FH_ERR_INVALID_ARG

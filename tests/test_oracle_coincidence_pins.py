@@ -127,6 +127,54 @@ def test_expected_number_of_coincidences(co, th, m, win_cells, n):
         assert abs(got - want * edge) < 4.0 * math.sqrt(want)
 
 
+def test_cluster_coincidences_keep_the_nearest_pair(co):
+    """Clusters {0, 1} and {2} of set 1, {0} and {1, 2} of set 2; pairs
+    (0, 0), (1, 0), (1, 1), (2, 2): cluster pairs (0, 0) keeps the nearer of
+    (0, 0) and (1, 0), (0, 1) keeps (1, 1), (2, 1) keeps (2, 2)."""
+    a = co.as_cands([cand(f=0.0), cand(f=3.0), cand(f=20.0)])
+    b = co.as_cands([cand(f=2.0), cand(f=3.5), cand(f=20.0)])
+    rows, d = co.cluster_coincidences(a, b, 0.0, 0.0, 0.0, [0, 0, 2], [0, 1, 1],
+                                      [(0, 0), (1, 0), (1, 1), (2, 2)])
+    assert rows.tolist() == [[0, 0, 1, 0], [0, 1, 1, 1], [2, 1, 2, 2]]
+    assert d.tolist() == [1.0, 0.5, 0.0]
+    # ties go to the smallest (i, j)
+    b2 = co.as_cands([cand(f=1.0), cand(f=4.0), cand(f=20.0)])
+    rows, _ = co.cluster_coincidences(a, b2, 0.0, 0.0, 0.0, [0, 0, 2], [0, 0, 1],
+                                      [(0, 0), (1, 1)])
+    assert rows.tolist() == [[0, 0, 0, 0]]
+
+
+def test_cluster_coincidences_by_brute_force(co):
+    seeds = synth.candidate_set(6, 0, 64, clusters=8, cluster_size=8)[::8, :4]
+    a = synth.candidate_set(6, 1, 300, signals=seeds, clusters=20, cluster_size=5)
+    b = synth.candidate_set(6, 2, 280, signals=seeds, clusters=20, cluster_size=5)
+    la, _ = co.cluster(a, 4.0)
+    lb, _ = co.cluster(b, 4.0)
+    p, _, _ = co.coincidences(a, b, 1e6, 2e6, 1.5e6, (3, 3, 3, 3))
+    rows, d = co.cluster_coincidences(a, b, 1e6, 2e6, 1.5e6, la, lb, p)
+    al, bl = a.tolist(), b.tolist()
+    best = {}
+    for i, j in p.tolist():
+        fa = al[i][2] + al[i][3] * (1.5e6 - 1e6)
+        fb = bl[j][2] + bl[j][3] * (1.5e6 - 2e6)
+        ks = []
+        for q, (x, y, wx, wy) in enumerate(((al[i][0], bl[j][0], al[i][4], bl[j][4]),
+                                            (al[i][1], bl[j][1], al[i][5], bl[j][5]),
+                                            (fa, fb, al[i][6], bl[j][6]),
+                                            (al[i][3], bl[j][3], al[i][7], bl[j][7]))):
+            dx = abs(y - x)
+            if q == 0 and dx > math.pi:
+                dx = 2 * math.pi - dx
+            ks.append(dx / ((wx + wy) * 0.5))
+        dist = math.sqrt(((ks[0] ** 2 + ks[1] ** 2) + ks[2] ** 2) + ks[3] ** 2)
+        key = (int(la[i]), int(lb[j]))
+        if key not in best or (dist, i, j) < best[key]:
+            best[key] = (dist, i, j)
+    want = sorted((i, j, k) for k, (dd, i, j) in best.items())
+    assert [tuple(r) for r in rows.tolist()] == [(k[0], k[1], i, j) for i, j, k in want]
+    assert len(rows) < len(p)      # clusters merge pairs
+
+
 @pytest.fixture(scope="module")
 def th():
     from oracle import theory
