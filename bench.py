@@ -569,7 +569,8 @@ def coincidence_leg(fh, synth, torch, steps):
     for n, bands in ((100000, 1), (1000000, 10)):
         a, b = coincidence_sets(synth, n, bands)
         da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
-        c_ms, k_ms = [], []
+        c_ms, k_ms, q_ms = [], [], []
+        lab_b, _ = fh.fh_cluster(db, 4.0)
         for k in range(2 + steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -577,14 +578,18 @@ def coincidence_leg(fh, synth, torch, steps):
             t1 = time.perf_counter()
             pairs, m1, m2 = fh.fh_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, (2, 2, 2, 2))
             t2 = time.perf_counter()
+            rows, _ = fh.fh_cluster_coincidences(da, db, 1.0e6, 2.0e6, 1.5e6, lab, lab_b, pairs)
+            t3 = time.perf_counter()
             if k >= 2:
                 c_ms.append((t1 - t0) * 1e3)
                 k_ms.append((t2 - t1) * 1e3)
+                q_ms.append((t3 - t2) * 1e3)
         cm, km = statistics.median(c_ms), statistics.median(k_ms)
         res["%dk_x_%dHz" % (n // 1000, bands)] = {
             "n_per_set": n, "clusters": ncl, "pairs": int(pairs.shape[0]),
             "coincident_in_set1": int((m1 > 0).sum().item()),
-            "cluster_ms": cm, "coincidence_ms": km,
+            "cluster_ms": cm, "coincidence_ms": km, "cluster_pairs": int(rows.shape[0]),
+            "cluster_coincidence_ms": statistics.median(q_ms),
             "cluster_candidates_per_s": n / (cm * 1e-3),
             "coincidence_candidates_per_s": 2 * n / (km * 1e-3)}
     res["workload"] = ("two sets per size, sky uniform, f in 1 Hz bands at 100 Hz "
