@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu legs")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--legs", default="adaptive,batched,serving,refine,peakmap,coincidences,cpu",
+    ap.add_argument("--legs", default="adaptive,batched,serving,refine,peakmap,coincidences,"
+                                      "highfreq,cpu",
                     help="extra legs to run after the timed step (comma list)")
     return ap.parse_args()
 
@@ -390,6 +391,11 @@ def run_ours(args):
                 out["coincidences"] = coincidence_leg(fh, synth, torch, args.steps)
             except Exception as e:  # report, do not hide
                 out["coincidences"] = {"error": str(e)[:300]}
+        if "highfreq" in legs:
+            try:
+                out["highfreq"] = highfreq_leg(fh, synth, torch, min(args.steps, 5))
+            except Exception as e:  # report, do not hide
+                out["highfreq"] = {"error": str(e)[:300]}
         if "cpu" in legs:
             out["cpu_baseline"] = cpu_baseline_leg(
                 inp, pp, refine_args=ref_args,
@@ -660,6 +666,54 @@ def batched_vs_plain(fh, synth, torch):
     res["speedup"] = res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"]
     res["speedup_graph"] = res["plain_graph"]["ms_per_step"] / res["batched_graph"]["ms_per_step"]
     return res
+
+
+def highfreq_leg(fh, synth, torch, steps):
+    """The largest single-GPU workload: T_FFT 1024 s over a year (61594 FFTs,
+    ~26.5M peaks), band 900-910 Hz, 356 x 102400 map, 64 sky directions in one
+    batched plan (13.6 GB of positions).  Correction + transform + selection,
+    device-resident inputs (far larger than L2), CUDA events."""
+    w = synth.WORKLOADS["highfreq_T1024_1yr_900Hz_64dir"]
+    t0 = time.perf_counter()
+    inp = synth.make_inputs(w)
+    gen_s = time.perf_counter() - t0
+    pp = w.plan_params()
+    n_dir = inp.sky.shape[0]
+    dev = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+    upd = inp.n_peaks * pp["n_fdot"] * n_dir
+    n_sb = -(-pp["n_f0"] // pp["subband_cells"])
+    cand = torch.empty(n_dir * n_sb * pp["top_k"] * 48, dtype=torch.uint8, device="cuda")
+    plan = fh.fh_create_plan(fh.make_desc(pp, w.n_fft, n_dir, inp.n_peaks))
+    try:
+        fh.fh_correct_doppler(plan, *dev)
+        tile, warps = fh.fh_autotune(plan, 0, n_dir)
+        ts = []
+        n_warm = 2
+        for k in range(n_warm + steps):
+            if k == n_warm:
+                fh.fh_plan_set_timing(plan, True)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            fh.fh_correct_doppler(plan, *dev)
+            fh.fh_transform(plan, 0, n_dir, None)
+            e[1].record()
+            fh.fh_select_candidates(plan, 0, n_dir, cand)
+            e[2].record()
+            torch.cuda.synchronize()
+            if k >= n_warm:
+                ts.append((e[0].elapsed_time(e[2]), e[0].elapsed_time(e[1])))
+        _, win_sum, kern_sum = fh.fh_plan_kernel_times(plan)
+        fh.fh_plan_set_timing(plan, False)
+    finally:
+        fh.fh_destroy_plan(plan)
+    ms = statistics.mean(t for t, _ in ts)
+    return {"workload": w.name, "n_peaks": inp.n_peaks, "n_dir": n_dir,
+            "map": [pp["n_fdot"], pp["n_f0"]], "updates_per_step": upd,
+            "ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3),
+            "correct_plus_transform_ms": statistics.mean(t for _, t in ts),
+            "transform_kernel_ms": kern_sum / len(ts), "window_kernel_ms": win_sum / len(ts),
+            "tile_cells": tile, "block_warps": warps, "steps": len(ts),
+            "input_generation_s": gen_s}
 
 
 def serving_leg(fh, synth, torch, seconds):

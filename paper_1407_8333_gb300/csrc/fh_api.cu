@@ -747,7 +747,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     if (bps < 1) return set_error(FH_ERR_CUDA, "transform kernel cannot be resident");
     // peak windows of a group of directions (bounded table), then the transform
     const size_t per_dir_win = sizeof(int2) * (size_t)per_dir * (size_t)std::max(1, p->n_fft);
-    const size_t win_cap = std::max(per_dir_win, (size_t)1 << 30);
+    const size_t win_cap = std::max(per_dir_win, (size_t)1 << 32);
     // (the windows grid has one block row per direction: at most 65535)
     const size_t zcap = 65535;
     const int32_t group = schedule == FH_SCHED_PLAIN

@@ -27,6 +27,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr double kTwo32 = 4294967296.0;
 constexpr int kPosFfts = 8;
 constexpr int kPosThreads = 256;
+constexpr int kPosUnroll = 4;
 
 // ---------------------------------------------------------------- a1 + a2
 // several peakmaps in one launch (see positions_kernel); null a_base: one
@@ -58,9 +59,11 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
     return (bits >> 63) ? -(int64_t)q - (frac ? 1 : 0) : (int64_t)q;
 }
 
-// grid (ceil(n_fft / 8), n_dir): the block computes r = 1 / (1 + v.n) for 8
+// grid (n_dir * ceil(n_fft / 8)): the block computes r = 1 / (1 + v.n) for 8
 // FFTs of one direction, then the fixed-point position of each of their peaks
-// (a contiguous CSR range, so loads and stores are coalesced).  With `src`,
+// (a contiguous CSR range, so loads and stores are coalesced).  The direction
+// varies fastest, so the blocks that read one group of FFTs' frequencies run
+// together and all but the first find them in L2.  With `src`,
 // FFT i's peaks are read from freq[src[i] ...] (a sub-range of a larger
 // peakmap) and written compactly by `offsets`.  With `validate`, the blocks of
 // direction 0 also flag frequencies that are not finite and positive
@@ -68,25 +71,25 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
 __global__ void __launch_bounds__(kPosThreads)
 positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
-                 int64_t n_peaks, double f0_min, double kt, double cshift,
+                 int32_t n_dir, int64_t n_peaks, double f0_min, double kt, double cshift,
                  int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
                  int32_t validate, const int64_t *__restrict__ src, PosBatch batch)
 {
-    // batches (refinement): block z is one peakmap of several, each with its own
-    // offsets, source index, sky directions, output base and peak count
+    // batches (refinement): block row y is one peakmap of several, each with its
+    // own offsets, source index, sky directions, output base and peak count
     if (batch.a_base) {
-        const int c = blockIdx.z;
+        const int c = blockIdx.y;
         offsets += (int64_t)c * (n_fft + 1);
         src += (int64_t)c * n_fft;
-        sky += 3 * (int64_t)c * gridDim.y;
+        sky += 3 * (int64_t)c * n_dir;
         A += batch.a_base[c];
         n_peaks = batch.n_peaks[c];
     }
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
     __shared__ int64_t src_s[kPosFfts];  // where each FFT's peaks start in freq
-    const int d = blockIdx.y;
-    const int i0 = blockIdx.x * kPosFfts;
+    const int d = (int)(blockIdx.x % (unsigned)n_dir);
+    const int i0 = (int)(blockIdx.x / (unsigned)n_dir) * kPosFfts;
     const int nf = min(kPosFfts, n_fft - i0);
     if (threadIdx.x < nf) {
         const int i = i0 + threadIdx.x;
@@ -109,35 +112,53 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
     const int lane = threadIdx.x & 31;
     bool bad = false;
     int32_t ev = 0;
-    // whole warps step together (the shuffle below needs all lanes)
-    for (int64_t pw = p_begin + (threadIdx.x & ~31); pw < p_end; pw += blockDim.x) {
-        const int64_t p = pw + lane;
-        const bool in = p < p_end;
-        int lo = 0, hi = nf;  // off_s[lo] <= p < off_s[hi]
-        while (hi - lo > 1) {
-            const int m = (lo + hi) >> 1;
-            if (off_s[m] <= p) lo = m; else hi = m;
-        }
-        const int64_t fp = src_s[lo] + (p - off_s[lo]);
-        const double f = in ? freq[fp] : 1.0;
-        if (check) {
-            // positive finite doubles order like their bit patterns
-            const int64_t fb = __double_as_longlong(f);
-            int64_t prev = __shfl_up_sync(kFull, fb, 1);
-            if (lane == 0 && in && p > p_begin) prev = __double_as_longlong(freq[fp - 1]);
-            if (in) {
-                if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
-                if (p > off_s[lo] && !(fb > prev)) ev |= kErrUnsorted;
+    // whole warps step together (the shuffles below need all lanes); a warp
+    // takes kPosUnroll runs of 32 consecutive peaks, their loads issued first
+    for (int64_t pw = p_begin + (int64_t)(threadIdx.x & ~31) * kPosUnroll; pw < p_end;
+         pw += (int64_t)blockDim.x * kPosUnroll) {
+        double f[kPosUnroll];
+        int fi[kPosUnroll];
+#pragma unroll
+        for (int u = 0; u < kPosUnroll; ++u) {
+            const int64_t p = pw + 32 * u + lane;
+            int lo = 0, hi = nf;  // off_s[lo] <= p < off_s[hi]
+            while (hi - lo > 1) {
+                const int m = (lo + hi) >> 1;
+                if (off_s[m] <= p) lo = m; else hi = m;
             }
+            fi[u] = lo;
+            f[u] = p < p_end ? freq[src_s[lo] + (p - off_s[lo])] : 1.0;
         }
-        if (in) {
-            const double u = __dmul_rn(f, r_s[lo]);
-            const double x = __dsub_rn(u, f0_min);
-            const double y = __dmul_rn(x, kt);
-            const double a = __dadd_rn(y, cshift);
-            // |a| < 2^28 exactly when the biased exponent is below 1023 + 28
-            bad |= ((__double_as_longlong(a) >> 52) & 0x7FF) >= 1051;
-            Ad[p] = floor_times_2p32(a);
+#pragma unroll
+        for (int u = 0; u < kPosUnroll; ++u) {
+            const int64_t p = pw + 32 * u + lane;
+            const bool in = p < p_end;
+            const int lo = fi[u];
+            if (check) {
+                // positive finite doubles order like their bit patterns; lane 0's
+                // left neighbour is lane 31 of the previous run, or in memory
+                const int64_t fb = __double_as_longlong(f[u]);
+                int64_t prev = __shfl_up_sync(kFull, fb, 1);
+                const int64_t last =
+                    __shfl_sync(kFull, u > 0 ? __double_as_longlong(f[u > 0 ? u - 1 : 0]) : 0, 31);
+                const bool first = p == off_s[lo];  // first peak of its FFT: no neighbour
+                if (lane == 0 && in && !first)
+                    prev = u > 0 ? last
+                                 : __double_as_longlong(freq[src_s[lo] + (p - off_s[lo]) - 1]);
+                if (in) {
+                    if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
+                    if (!first && !(fb > prev)) ev |= kErrUnsorted;
+                }
+            }
+            if (in) {
+                const double uu = __dmul_rn(f[u], r_s[lo]);
+                const double x = __dsub_rn(uu, f0_min);
+                const double y = __dmul_rn(x, kt);
+                const double a = __dadd_rn(y, cshift);
+                // |a| < 2^28 exactly when the biased exponent is below 1023 + 28
+                bad |= ((__double_as_longlong(a) >> 52) & 0x7FF) >= 1051;
+                Ad[p] = floor_times_2p32(a);
+            }
         }
     }
     if (ev) atomicOr(err, ev);
@@ -360,22 +381,25 @@ __device__ __forceinline__ void lookup_window(const int64_t *__restrict__ Ad,
 // on each side; those extra peaks reach only guard cells (the transform's
 // guard keeps a margin of two cells), so they change no count.
 //
-// A block takes 8 FFTs of one direction, two warps per FFT; the FFT's peak
-// cells (ascending) are copied into shared memory once, between four sentinels
-// on each side (an FFT with more than kWinPeaks - 8 peaks is read from global
-// memory, with bounds checks).  Lanes take tiles, one each (64 per pass), and
-// walk the slabs in order: the first slab's bounds come from a binary search,
-// each later one from a step in the direction of the FFT's drift D (both
-// bounds move monotonically with the slab, by 32 D).
-// Each (slab, 64 tiles) result is staged as [FFT][tile] (row pitch 68 entries:
-// both the lanes' writes and the 8-FFT runs read back take the minimum of
-// shared-memory wavefronts) and written as 64-byte runs of 8 FFTs, the layout
-// the transform reads with one 8-byte load per lane.
-// grid (ceil(n_fft / 8), n_dir), 512 threads.
+// A block takes 8 FFTs of one direction, one warp per FFT; the FFT's peak
+// cells (ascending) are copied into shared memory once, between one sentinel
+// on each side (an FFT with more than kWinPeaks - 2 peaks is read from global
+// memory, with bounds checks).  Lane l takes tiles l, l + 32, ... (M per pass,
+// M = 1 .. 3 from the tile count: the lane's per-slab work -- the 64-bit
+// bounds, the branches, the barrier -- is shared by M entries, and the M
+// searches of a slab are independent) and walks the slabs in order: the first
+// slab's bounds come from a binary search, each later one from a step in the
+// direction of the FFT's drift D (both bounds move monotonically with the
+// slab, by 32 D).
+// Each (slab, 32 M tiles) result is staged as [FFT][tile] (row pitch 32 M + 4
+// entries = 4 mod 16 eight-byte banks: both the lanes' writes and the 8-FFT
+// runs read back take the minimum of shared-memory wavefronts) and written as
+// 64-byte runs of 8 FFTs, the layout the transform reads with one 8-byte load
+// per lane.
+// grid (ceil(n_fft / 8), n_dir), 256 threads.
 constexpr int kWinPeaks = 1024;
-constexpr int kWinTiles = 64;
 constexpr int kWinPad = 1;
-constexpr int kWinPitch = 68;  // = 4 mod 16 eight-byte banks
+constexpr int kWinMaxM = 3;
 __device__ __forceinline__ int lower_bound_cell(const int32_t *a, int n, int x)
 {
     int lo = 0, hi = n;
@@ -412,13 +436,15 @@ __device__ __forceinline__ int step_down(const int32_t *a, int q, int x)
     return q;
 }
 
-__global__ void __launch_bounds__(512, 3)
+template <int M>
+__global__ void __launch_bounds__(256, 4)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
+    constexpr int kTiles = 32 * M;     // tiles per pass
+    constexpr int kPitch = kTiles + 4;  // = 4 mod 16 eight-byte banks
     __shared__ int32_t cell_s[8][kWinPeaks];
-    __shared__ int2 stage[2][8][kWinPitch];  // double buffer: one barrier per slab
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int f = warp & 7, half = warp >> 3;  // FFT of the block, tile half
+    __shared__ int2 stage[2][8][kPitch];  // double buffer: one barrier per slab
+    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;  // warp = FFT of the block
     const int i = blockIdx.x * 8 + f;
     const bool live = i < J.n_fft;
     const int d_rel = blockIdx.y;
@@ -430,32 +456,41 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     const int64_t *Ai = Ad + o0;
     int32_t *cs = &cell_s[f][kWinPad];
     if (staged) {
-        for (int k = half * 32 + lane; k < n; k += 64) cs[k] = global_cell(Ai, k);
-        if (half == 0 && lane < kWinPad) {
+        for (int k = lane; k < n; k += 32) cs[k] = global_cell(Ai, k);
+        if (lane < kWinPad) {
             cs[-1 - lane] = INT_MIN;
             cs[n + lane] = INT_MAX;
         }
     }
-    __syncthreads();
+    __syncwarp();  // a warp reads only its own FFT's cells
     const int64_t dv = live ? J.D[i] : 0;
     const int64_t s0 = live ? J.S0[i] : 0;
     const int K = J.k_over, W = J.tile_cells;
     const int64_t nf = J.n_fft;
     const int64_t slab_stride = (int64_t)J.n_tiles * nf;
     int2 *out = windows + (int64_t)d_rel * J.n_slabs * slab_stride;
-    for (int t0 = 0; t0 < J.n_tiles; t0 += kWinTiles) {
-        const int nt = min(kWinTiles, J.n_tiles - t0);
-        // this lane's tile: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
-        const int tt = half * 32 + lane;
-        const bool tile_ok = live && tt < nt;
-        const int b0 = (t0 + tt) * W;
-        const int blo = b0 - K + 1;
-        const int bhi = b0 + min(W, J.n_f0 - b0);
-        int qa = 0, qb = 0;
-        // this thread's staged entry goes to a fixed (tile, FFT) place of every slab
-        const int est = threadIdx.x >> 3, efi = blockIdx.x * 8 + (threadIdx.x & 7);
-        const bool dst_ok = est < nt && efi < J.n_fft;
-        int2 *dst = out + (int64_t)(t0 + est) * nf + efi;
+    const int efi = blockIdx.x * 8 + (threadIdx.x & 7);  // FFT of this thread's staged entries
+    for (int t0 = 0; t0 < J.n_tiles; t0 += kTiles) {
+        const int nt = min(kTiles, J.n_tiles - t0);
+        // the lane's tiles: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
+        int blo[M], bhi[M], qa[M], qb[M];
+        bool ok[M];
+        // this thread's staged entries go to fixed (tile, FFT) places of every slab
+        int2 *dst[M];
+        bool dst_ok[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int tt = lane + 32 * m;
+            ok[m] = live && tt < nt;
+            const int b0 = (t0 + tt) * W;
+            blo[m] = b0 - K + 1;
+            bhi[m] = b0 + min(W, J.n_f0 - b0);
+            qa[m] = 0;
+            qb[m] = 0;
+            const int est = (threadIdx.x >> 3) + 32 * m;
+            dst_ok[m] = est < nt && efi < J.n_fft;
+            dst[m] = out + (int64_t)(t0 + est) * nf + efi;
+        }
         // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
         // ceil((S0 + j0 D + max(0, (R-1) D)) / 2^32) (+ the tile's terms), kept
         // as 64-bit sums that advance by 32 D per full slab
@@ -471,38 +506,61 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
                 u = s0 + jd + (span < 0 ? span : 0);
                 w = s0 + jd + (span > 0 ? span : 0);
             }
-            const int xl = (int)(u >> 32) + blo;
-            const int xh = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0) + bhi;
-            if (tile_ok) {
-                if (!staged) {
+            const int ul = (int)(u >> 32);
+            const int wh = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0);
+            if (!staged) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    if (!ok[m]) continue;
+                    const int xl = ul + blo[m], xh = wh + bhi[m];
+                    int a = qa[m], b = qb[m];
                     if (slab == 0) {
-                        qa = lower_bound_cell_g(Ai, n, xl);
-                        qb = lower_bound_cell_g(Ai, n, xh);
+                        a = lower_bound_cell_g(Ai, n, xl);
+                        b = lower_bound_cell_g(Ai, n, xh);
                     } else {
-                        while (qa < n && global_cell(Ai, qa) < xl) ++qa;
-                        while (qa > 0 && global_cell(Ai, qa - 1) >= xl) --qa;
-                        while (qb < n && global_cell(Ai, qb) < xh) ++qb;
-                        while (qb > 0 && global_cell(Ai, qb - 1) >= xh) --qb;
+                        while (a < n && global_cell(Ai, a) < xl) ++a;
+                        while (a > 0 && global_cell(Ai, a - 1) >= xl) --a;
+                        while (b < n && global_cell(Ai, b) < xh) ++b;
+                        while (b > 0 && global_cell(Ai, b - 1) >= xh) --b;
                     }
-                } else if (slab == 0) {
-                    qa = lower_bound_cell(cs, n, xl);
-                    qb = lower_bound_cell(cs, n, xh);
-                } else if (dv >= 0) {
-                    qa = step_up(cs, qa, xl);
-                    qb = step_up(cs, qb, xh);
-                } else {
-                    qa = step_down(cs, qa, xl);
-                    qb = step_down(cs, qb, xh);
+                    qa[m] = a;
+                    qb[m] = b;
                 }
-                stage[slab & 1][f][tt] = make_int2((int)(o0 + qa), (int)(o0 + max(qa, qb)));
+            } else if (slab == 0) {
+                // every lane searches (the sentinels bound the tiles past the last one)
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    qa[m] = lower_bound_cell(cs, n, ul + blo[m]);
+                    qb[m] = lower_bound_cell(cs, n, wh + bhi[m]);
+                }
+            } else if (dv >= 0) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    qa[m] = step_up(cs, qa[m], ul + blo[m]);
+                    qb[m] = step_up(cs, qb[m], wh + bhi[m]);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    qa[m] = step_down(cs, qa[m], ul + blo[m]);
+                    qb[m] = step_down(cs, qb[m], wh + bhi[m]);
+                }
             }
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (ok[m])
+                    stage[slab & 1][f][lane + 32 * m] =
+                        make_int2((int)(o0 + qa[m]), (int)(o0 + max(qa[m], qb[m])));
             u += 32 * dv;
             w += 32 * dv;
             // this slab's entries are complete; the buffer is written again two
             // slabs later, after the next barrier
             __syncthreads();
-            if (dst_ok) *dst = stage[slab & 1][threadIdx.x & 7][est];
-            dst += slab_stride;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                if (dst_ok[m]) *dst[m] = stage[slab & 1][threadIdx.x & 7][(threadIdx.x >> 3) + 32 * m];
+                dst[m] += slab_stride;
+            }
         }
         __syncthreads();  // the next pass of tiles reuses both buffers
     }
@@ -1168,11 +1226,20 @@ cudaError_t launch_positions(const double *freq, const int64_t *offsets, const d
 {
     if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
-    dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
-    positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
-                                                  kt, cshift, A, out_r, err, validate ? 1 : 0,
-                                                  src, PosBatch{nullptr, nullptr});
-    return cudaGetLastError();
+    const int64_t groups = (n_fft + kPosFfts - 1) / kPosFfts;
+    // directions in runs that keep the grid below 2^31 blocks (the checks of
+    // `validate` need the run with direction 0 only)
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(n_dir, 2147483647LL / groups));
+    for (int64_t d0 = 0; d0 < n_dir; d0 += per) {
+        const int32_t nd = (int32_t)std::min<int64_t>(per, n_dir - d0);
+        positions_kernel<<<(unsigned)(groups * nd), kPosThreads, 0, s>>>(
+            freq, offsets, v, sky + 3 * d0, n_fft, nd, n_peaks, f0_min, kt, cshift,
+            A + d0 * n_peaks, out_r ? out_r + d0 * n_fft : nullptr, err,
+            (validate && d0 == 0) ? 1 : 0, src, PosBatch{nullptr, nullptr});
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
@@ -1184,13 +1251,15 @@ cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
 {
     if (n_fft <= 0 || n_dir <= 0 || n_batch <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
+    const int64_t blocks = (int64_t)n_dir * ((n_fft + kPosFfts - 1) / kPosFfts);
+    if (blocks > 2147483647LL) return cudaErrorInvalidConfiguration;
     for (int32_t b0 = 0; b0 < n_batch; b0 += 65535) {
         const int32_t nb = std::min(65535, n_batch - b0);
-        dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir, nb);
+        dim3 grid((unsigned)blocks, nb);
         positions_kernel<<<grid, kPosThreads, 0, s>>>(
             freq, offsets + (int64_t)b0 * (n_fft + 1), v, sky + 3 * (int64_t)b0 * n_dir, n_fft,
-            0, f0_min, kt, cshift, A, nullptr, err, validate ? 1 : 0, src + (int64_t)b0 * n_fft,
-            PosBatch{a_base + b0, n_peaks + b0});
+            n_dir, 0, f0_min, kt, cshift, A, nullptr, err, validate ? 1 : 0,
+            src + (int64_t)b0 * n_fft, PosBatch{a_base + b0, n_peaks + b0});
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1299,7 +1368,14 @@ cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t 
 {
     if (job.n_fft <= 0 || job.n_dir <= 0) return cudaSuccess;
     dim3 grid((job.n_fft + 7) / 8, job.n_dir);
-    windows_kernel<<<grid, 512, 0, s>>>(job, windows);
+    // tiles per lane and pass: enough for all tiles in one pass, at most kWinMaxM
+    const int m = std::min(kWinMaxM, std::max(1, (job.n_tiles + 31) / 32));
+    if (m == 1)
+        windows_kernel<1><<<grid, 256, 0, s>>>(job, windows);
+    else if (m == 2)
+        windows_kernel<2><<<grid, 256, 0, s>>>(job, windows);
+    else
+        windows_kernel<3><<<grid, 256, 0, s>>>(job, windows);
     return cudaGetLastError();
 }
 

@@ -262,6 +262,11 @@ def fh_transform(plan, dir_begin: int, n_dir: int, out_maps=None, stream=None) -
 
 
 def fh_copy_profile(plan, dir_begin: int, n_dir: int, out, stream=None) -> None:
+    """Enqueue a device-to-device copy of the profile into ``out`` (a CUDA
+    tensor or a raw device address); host arrays are refused, since the copy
+    is asynchronous."""
+    if isinstance(out, np.ndarray) or (_is_torch(out) and not out.is_cuda):
+        raise TypeError("fh_copy_profile writes device memory: pass a CUDA tensor")
     _check(load().fh_copy_profile(plan, int(dir_begin), int(n_dir), _ptr(out), _stream(stream)),
            "fh_copy_profile")
 

@@ -86,6 +86,18 @@ def test_invalid_plan_is_rejected_without_gpu(lib):
         fh.fh_create_plan(fh.make_desc(pp, 10, 1, 100))
 
 
+def test_device_only_outputs_refuse_host_buffers():
+    """fh_copy_profile enqueues an asynchronous device-to-device copy: a host
+    array is refused before the library is called."""
+    import numpy as np
+    from paper_1407_8333_gb300 import fh
+    with pytest.raises(TypeError):
+        fh.fh_copy_profile(None, 0, 1, np.zeros(8, dtype=np.uint64))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        fh.fh_copy_profile(None, 0, 1, torch.zeros(8, dtype=torch.int64))
+
+
 def test_product_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1407_8333_gb300")
     for dirpath, _, files in os.walk(pkg):
