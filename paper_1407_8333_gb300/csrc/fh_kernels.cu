@@ -27,7 +27,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr double kTwo32 = 4294967296.0;
 constexpr int kPosFfts = 8;
 constexpr int kPosThreads = 256;
-constexpr int kPosUnroll = 4;
 
 // ---------------------------------------------------------------- a1 + a2
 // several peakmaps in one launch (see positions_kernel); null a_base: one
@@ -59,11 +58,9 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
     return (bits >> 63) ? -(int64_t)q - (frac ? 1 : 0) : (int64_t)q;
 }
 
-// grid (n_dir * ceil(n_fft / 8)): the block computes r = 1 / (1 + v.n) for 8
+// grid (ceil(n_fft / 8), n_dir): the block computes r = 1 / (1 + v.n) for 8
 // FFTs of one direction, then the fixed-point position of each of their peaks
-// (a contiguous CSR range, so loads and stores are coalesced).  The direction
-// varies fastest, so the blocks that read one group of FFTs' frequencies run
-// together and all but the first find them in L2.  With `src`,
+// (a contiguous CSR range, so loads and stores are coalesced).  With `src`,
 // FFT i's peaks are read from freq[src[i] ...] (a sub-range of a larger
 // peakmap) and written compactly by `offsets`.  With `validate`, the blocks of
 // direction 0 also flag frequencies that are not finite and positive
@@ -71,25 +68,25 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
 __global__ void __launch_bounds__(kPosThreads)
 positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
                  const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
-                 int32_t n_dir, int64_t n_peaks, double f0_min, double kt, double cshift,
+                 int64_t n_peaks, double f0_min, double kt, double cshift,
                  int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
                  int32_t validate, const int64_t *__restrict__ src, PosBatch batch)
 {
-    // batches (refinement): block row y is one peakmap of several, each with its
-    // own offsets, source index, sky directions, output base and peak count
+    // batches (refinement): block z is one peakmap of several, each with its own
+    // offsets, source index, sky directions, output base and peak count
     if (batch.a_base) {
-        const int c = blockIdx.y;
+        const int c = blockIdx.z;
         offsets += (int64_t)c * (n_fft + 1);
         src += (int64_t)c * n_fft;
-        sky += 3 * (int64_t)c * n_dir;
+        sky += 3 * (int64_t)c * gridDim.y;
         A += batch.a_base[c];
         n_peaks = batch.n_peaks[c];
     }
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
     __shared__ int64_t src_s[kPosFfts];  // where each FFT's peaks start in freq
-    const int d = (int)(blockIdx.x % (unsigned)n_dir);
-    const int i0 = (int)(blockIdx.x / (unsigned)n_dir) * kPosFfts;
+    const int d = blockIdx.y;
+    const int i0 = blockIdx.x * kPosFfts;
     const int nf = min(kPosFfts, n_fft - i0);
     if (threadIdx.x < nf) {
         const int i = i0 + threadIdx.x;
@@ -112,53 +109,35 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
     const int lane = threadIdx.x & 31;
     bool bad = false;
     int32_t ev = 0;
-    // whole warps step together (the shuffles below need all lanes); a warp
-    // takes kPosUnroll runs of 32 consecutive peaks, their loads issued first
-    for (int64_t pw = p_begin + (int64_t)(threadIdx.x & ~31) * kPosUnroll; pw < p_end;
-         pw += (int64_t)blockDim.x * kPosUnroll) {
-        double f[kPosUnroll];
-        int fi[kPosUnroll];
-#pragma unroll
-        for (int u = 0; u < kPosUnroll; ++u) {
-            const int64_t p = pw + 32 * u + lane;
-            int lo = 0, hi = nf;  // off_s[lo] <= p < off_s[hi]
-            while (hi - lo > 1) {
-                const int m = (lo + hi) >> 1;
-                if (off_s[m] <= p) lo = m; else hi = m;
-            }
-            fi[u] = lo;
-            f[u] = p < p_end ? freq[src_s[lo] + (p - off_s[lo])] : 1.0;
+    // whole warps step together (the shuffle below needs all lanes)
+    for (int64_t pw = p_begin + (threadIdx.x & ~31); pw < p_end; pw += blockDim.x) {
+        const int64_t p = pw + lane;
+        const bool in = p < p_end;
+        int lo = 0, hi = nf;  // off_s[lo] <= p < off_s[hi]
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (off_s[m] <= p) lo = m; else hi = m;
         }
-#pragma unroll
-        for (int u = 0; u < kPosUnroll; ++u) {
-            const int64_t p = pw + 32 * u + lane;
-            const bool in = p < p_end;
-            const int lo = fi[u];
-            if (check) {
-                // positive finite doubles order like their bit patterns; lane 0's
-                // left neighbour is lane 31 of the previous run, or in memory
-                const int64_t fb = __double_as_longlong(f[u]);
-                int64_t prev = __shfl_up_sync(kFull, fb, 1);
-                const int64_t last =
-                    __shfl_sync(kFull, u > 0 ? __double_as_longlong(f[u > 0 ? u - 1 : 0]) : 0, 31);
-                const bool first = p == off_s[lo];  // first peak of its FFT: no neighbour
-                if (lane == 0 && in && !first)
-                    prev = u > 0 ? last
-                                 : __double_as_longlong(freq[src_s[lo] + (p - off_s[lo]) - 1]);
-                if (in) {
-                    if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
-                    if (!first && !(fb > prev)) ev |= kErrUnsorted;
-                }
-            }
+        const int64_t fp = src_s[lo] + (p - off_s[lo]);
+        const double f = in ? freq[fp] : 1.0;
+        if (check) {
+            // positive finite doubles order like their bit patterns
+            const int64_t fb = __double_as_longlong(f);
+            int64_t prev = __shfl_up_sync(kFull, fb, 1);
+            if (lane == 0 && in && p > p_begin) prev = __double_as_longlong(freq[fp - 1]);
             if (in) {
-                const double uu = __dmul_rn(f[u], r_s[lo]);
-                const double x = __dsub_rn(uu, f0_min);
-                const double y = __dmul_rn(x, kt);
-                const double a = __dadd_rn(y, cshift);
-                // |a| < 2^28 exactly when the biased exponent is below 1023 + 28
-                bad |= ((__double_as_longlong(a) >> 52) & 0x7FF) >= 1051;
-                Ad[p] = floor_times_2p32(a);
+                if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
+                if (p > off_s[lo] && !(fb > prev)) ev |= kErrUnsorted;
             }
+        }
+        if (in) {
+            const double u = __dmul_rn(f, r_s[lo]);
+            const double x = __dsub_rn(u, f0_min);
+            const double y = __dmul_rn(x, kt);
+            const double a = __dadd_rn(y, cshift);
+            // |a| < 2^28 exactly when the biased exponent is below 1023 + 28
+            bad |= ((__double_as_longlong(a) >> 52) & 0x7FF) >= 1051;
+            Ad[p] = floor_times_2p32(a);
         }
     }
     if (ev) atomicOr(err, ev);
@@ -1226,20 +1205,11 @@ cudaError_t launch_positions(const double *freq, const int64_t *offsets, const d
 {
     if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
-    const int64_t groups = (n_fft + kPosFfts - 1) / kPosFfts;
-    // directions in runs that keep the grid below 2^31 blocks (the checks of
-    // `validate` need the run with direction 0 only)
-    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(n_dir, 2147483647LL / groups));
-    for (int64_t d0 = 0; d0 < n_dir; d0 += per) {
-        const int32_t nd = (int32_t)std::min<int64_t>(per, n_dir - d0);
-        positions_kernel<<<(unsigned)(groups * nd), kPosThreads, 0, s>>>(
-            freq, offsets, v, sky + 3 * d0, n_fft, nd, n_peaks, f0_min, kt, cshift,
-            A + d0 * n_peaks, out_r ? out_r + d0 * n_fft : nullptr, err,
-            (validate && d0 == 0) ? 1 : 0, src, PosBatch{nullptr, nullptr});
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
+    positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
+                                                  kt, cshift, A, out_r, err, validate ? 1 : 0,
+                                                  src, PosBatch{nullptr, nullptr});
+    return cudaGetLastError();
 }
 
 cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
@@ -1251,15 +1221,13 @@ cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
 {
     if (n_fft <= 0 || n_dir <= 0 || n_batch <= 0) return cudaSuccess;
     const double cshift = 0.5 - 0.5 * (double)k_over;
-    const int64_t blocks = (int64_t)n_dir * ((n_fft + kPosFfts - 1) / kPosFfts);
-    if (blocks > 2147483647LL) return cudaErrorInvalidConfiguration;
     for (int32_t b0 = 0; b0 < n_batch; b0 += 65535) {
         const int32_t nb = std::min(65535, n_batch - b0);
-        dim3 grid((unsigned)blocks, nb);
+        dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir, nb);
         positions_kernel<<<grid, kPosThreads, 0, s>>>(
             freq, offsets + (int64_t)b0 * (n_fft + 1), v, sky + 3 * (int64_t)b0 * n_dir, n_fft,
-            n_dir, 0, f0_min, kt, cshift, A, nullptr, err, validate ? 1 : 0,
-            src + (int64_t)b0 * n_fft, PosBatch{a_base + b0, n_peaks + b0});
+            0, f0_min, kt, cshift, A, nullptr, err, validate ? 1 : 0, src + (int64_t)b0 * n_fft,
+            PosBatch{a_base + b0, n_peaks + b0});
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
