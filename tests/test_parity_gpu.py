@@ -374,6 +374,48 @@ def test_workload_highfreq_900Hz_sampled(fh, oracle_mod):
     assert int(top["count"]) > 0.6 * w.n_fft
 
 
+def test_workload_highfreq_900Hz_all_directions_bench_configuration(fh, oracle_mod):
+    """The largest workload as the benchmark runs it: all 64 directions in one
+    batched plan (window tables in groups of directions), autotuned tile.
+    Three directions in different groups, the line's among them, are checked
+    bit for bit against the oracle's full maps: profile keys and candidates
+    (reporting columns to 1e-12)."""
+    import torch
+    w = synth.WORKLOADS["highfreq_T1024_1yr_900Hz_64dir"]
+    inp = synth.make_inputs(w)
+    pp = w.plan_params()
+    n_dir = inp.sky.shape[0]
+    dev = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+    plan = fh.fh_create_plan(fh.make_desc(pp, w.n_fft, n_dir, inp.n_peaks))
+    try:
+        fh.fh_correct_doppler(plan, *dev)
+        fh.fh_autotune(plan, 0, n_dir)
+        fh.fh_transform(plan, 0, n_dir)
+        prof = torch.empty((n_dir, pp["n_f0"]), dtype=torch.int64, device="cuda")
+        fh.fh_copy_profile(plan, 0, n_dir, prof)
+        cand = fh.fh_select_candidates(plan, 0, n_dir).reshape(n_dir, -1, pp["top_k"])
+        prof = prof.cpu().numpy().view(np.uint64)
+    finally:
+        fh.fh_destroy_plan(plan)
+    kt = float(pp["k_over"]) * pp["t_fft"]
+    S0, D = oracle_mod.shift_tables(inp.t, pp["t_ref"], kt, pp["fdot_min"], pp["fdot_step"])
+    for d in sorted({w.line_dir, 30, 63}):
+        r = oracle_mod.doppler_factor(inp.v, inp.sky[d:d + 1])
+        A = oracle_mod.positions(inp.offsets, inp.freq, r, pp["f0_min"], kt, pp["k_over"])[0]
+        m = oracle_mod.hough_map(inp.offsets, A, S0, D, pp["k_over"], pp["n_f0"], n_fdot=pp["n_fdot"])
+        pc, pr = oracle_mod.profile(m)
+        del m
+        assert np.array_equal(prof[d], oracle_profile_keys(pc, pr)), d
+        c, rr, n = oracle_mod.select(pc, pr, pp["subband_cells"], pp["top_k"], pp["excl_cells"],
+                                     pp["sep_cells"], pp["n_thr"])
+        assert np.array_equal(cand[d]["cell"], c) and np.array_equal(cand[d]["row"], rr)
+        assert np.array_equal(cand[d]["count"], n) and np.all(cand[d]["dir"] == d)
+        f0, fdot, cr = oracle_mod.report(c, rr, n, pp["f0_min"], kt, pp["fdot_min"],
+                                         pp["fdot_step"], w.n_fft, pp["p0"])
+        for got, want in ((cand[d]["f0"], f0), (cand[d]["fdot"], fdot), (cand[d]["cr"], cr)):
+            assert np.all(np.abs(got - want) <= REL_TOL * np.maximum(np.abs(want), 1e-300))
+
+
 @pytest.mark.parametrize("seed", [41, 42])
 def test_host_inputs_checked_on_the_device_match_oracle(fh, oracle_mod, seed):
     """FH_CHECKS_DEVICE: host inputs copied and checked by the kernels give the
