@@ -160,7 +160,12 @@ int64_t fh_plan_device_bytes(const fh_plan_desc *desc);
  * FFT), fixed-point corrected position of every (direction, peak) and the
  * spin-down shift tables, into the plan's buffers.  These directions are the
  * ones fh_transform and fh_select_candidates refer to by index.
- *   pm        peakmap; host arrays are validated on the host and copied;
+ *   pm        peakmap; host arrays are validated on the host (or, after
+ *             fh_plan_set_input_checks(FH_CHECKS_DEVICE), by the kernels) and
+ *             copied -- except that with n_dir == 1, page-locked (pinned or
+ *             registered) host arrays are read in place by the enqueued kernels
+ *             over the host link, so they must stay valid and unchanged until
+ *             the next synchronising call, as for any asynchronous copy;
  *             device arrays are read in place by the enqueued kernels and
  *             validated on the device (a failure is reported by the next
  *             fh_sync / host-output fh_select_candidates as FH_ERR_UNSORTED or

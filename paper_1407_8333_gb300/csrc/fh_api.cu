@@ -77,6 +77,18 @@ int max_optin_smem(int device)
     return v > 0 ? v : 48 * 1024;
 }
 
+// Device address of a page-locked (pinned or registered, mapped) host array,
+// which kernels can read in place; nullptr for pageable or unknown memory.
+const void *pinned_device_address(const void *h)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) ? a.devicePointer : nullptr;
+}
+
 // largest multiple-of-32 tile width whose counters fit the per-block limit
 int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nwarps, int32_t guard)
 {
@@ -622,6 +634,7 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     const int32_t n = pm->n_fft;
     const int64_t np = pm->n_peaks;
     const double *t_src, *f_src, *v_src, *sky_src;
+    const int64_t *offs_in_place = nullptr;  // page-locked host offsets read in place
     const bool host_checks = p->input_checks == FH_CHECKS_HOST;
     p->weighted = false;  // a new peakmap starts with unit weights
     cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
@@ -630,17 +643,31 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     if (pm->mem_kind == FH_MEM_HOST) {
         if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
             return set_error(FH_ERR_INVALID_ARG, "null peakmap array");
+        // With one direction every input array is read once, so page-locked
+        // arrays are read in place by the kernels over the host link (no copy
+        // in front of them); pageable arrays, and every array when several
+        // directions would re-read it, are copied into the plan's buffers.
+        const bool in_place = n_dir == 1;
+        auto mapped = [&](const void *h, size_t bytes) -> const void * {
+            return (in_place && bytes > 0) ? pinned_device_address(h) : nullptr;
+        };
+        const void *off_m = mapped(pm->offsets, 8 * ((size_t)n + 1));
+        const void *t_m = mapped(pm->t_fft, 8 * (size_t)n);
+        const void *f_m = mapped(pm->freq, 8 * (size_t)np);
+        const void *v_m = mapped(v_over_c, 24 * (size_t)n);
+        const void *sky_m = mapped(sky_n, 24 * (size_t)n_dir);
         // the copies are enqueued first, so that the host checks below run while
         // the inputs move; a failed check leaves the plan without a peakmap
         struct {
             void *dst;
             const void *src;
             size_t bytes;
-        } cp[] = {{host_checks ? p->offsets : p->offsets_raw, pm->offsets, 8 * ((size_t)n + 1)},
-                  {p->t, pm->t_fft, 8 * (size_t)n},
-                  {p->freq, pm->freq, 8 * (size_t)np},
-                  {p->v, v_over_c, 24 * (size_t)n},
-                  {p->sky, sky_n, 24 * (size_t)n_dir}};
+        } cp[] = {{host_checks ? p->offsets : p->offsets_raw, pm->offsets,
+                   off_m ? 0 : 8 * ((size_t)n + 1)},
+                  {p->t, pm->t_fft, t_m ? 0 : 8 * (size_t)n},
+                  {p->freq, pm->freq, f_m ? 0 : 8 * (size_t)np},
+                  {p->v, v_over_c, v_m ? 0 : 24 * (size_t)n},
+                  {p->sky, sky_n, sky_m ? 0 : 24 * (size_t)n_dir}};
         p->n_fft = -1;
         for (auto &c : cp) {
             if (c.bytes == 0) continue;
@@ -659,10 +686,11 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
             (size_t)max_optin_smem(p->device))
             gd = default_guard(p->d);
         p->guard = gd;
-        t_src = p->t;
-        f_src = p->freq;
-        v_src = p->v;
-        sky_src = p->sky;
+        t_src = t_m ? static_cast<const double *>(t_m) : p->t;
+        f_src = f_m ? static_cast<const double *>(f_m) : p->freq;
+        v_src = v_m ? static_cast<const double *>(v_m) : p->v;
+        sky_src = sky_m ? static_cast<const double *>(sky_m) : p->sky;
+        offs_in_place = static_cast<const int64_t *>(off_m);
     } else {
         if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
             return set_error(FH_ERR_INVALID_ARG, "null device peakmap array");
@@ -675,8 +703,10 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     // device checks: for device inputs, and for host inputs under FH_CHECKS_DEVICE
     const bool on_device = pm->mem_kind == FH_MEM_DEVICE || !host_checks;
     PrepArgs pa{};
-    pa.offsets_in = pm->mem_kind == FH_MEM_DEVICE ? pm->offsets
-                                                  : (host_checks ? nullptr : p->offsets_raw);
+    pa.offsets_in = pm->mem_kind == FH_MEM_DEVICE
+                        ? pm->offsets
+                        : (offs_in_place ? offs_in_place
+                                         : (host_checks ? nullptr : p->offsets_raw));
     pa.offsets_out = p->offsets;
     pa.t = t_src;
     pa.v = v_src;

@@ -30,7 +30,7 @@ def fh():
 
 
 def run_gpu(fh, inp, pp, mode=0, schedule=0, tile=0, warps=0, maps=True, device_inputs=True,
-            autotune=False, checks=None):
+            autotune=False, checks=None, pinned=False):
     import torch
     n_fft = inp.t.shape[0]
     n_peaks = inp.n_peaks
@@ -43,6 +43,10 @@ def run_gpu(fh, inp, pp, mode=0, schedule=0, tile=0, warps=0, maps=True, device_
             fh.fh_plan_set_input_checks(plan, checks)
         if device_inputs:
             args = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+        elif pinned:
+            # page-locked host arrays (read in place by the kernels for one direction)
+            args = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+                    for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
         else:
             args = [inp.t, inp.offsets, inp.freq, inp.v, inp.sky]
         r = torch.empty((n_dir, max(1, n_fft)), dtype=torch.float64, device="cuda")
@@ -424,6 +428,58 @@ def test_host_inputs_checked_on_the_device_match_oracle(fh, oracle_mod, seed):
     g = run_gpu(fh, inp, pp, device_inputs=False, checks=fh.FH_CHECKS_DEVICE)
     o = oracle_mod.search(inp, pp, want_maps=True)
     compare(g, o, pp, inp.t.shape[0])
+
+
+@pytest.mark.parametrize("seed, n_dir", [(43, 1), (44, 1), (45, 3)])
+def test_pinned_host_inputs_match_oracle(fh, oracle_mod, seed, n_dir):
+    """Page-locked host inputs (read in place by the kernels for one direction,
+    copied for several), under host and under device checks: the oracle's
+    positions, maps, profiles and candidates."""
+    inp, pp = synth.random_case(seed, n_fft=41, n_bins=90, n_dir=n_dir, p=0.3)
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    for checks in (fh.FH_CHECKS_HOST, fh.FH_CHECKS_DEVICE):
+        g = run_gpu(fh, inp, pp, device_inputs=False, pinned=True, checks=checks)
+        compare(g, o, pp, inp.t.shape[0])
+
+
+def test_pinned_host_input_errors_checked_on_the_device(fh):
+    """FH_CHECKS_DEVICE with page-locked host inputs read in place: unsorted
+    frequencies and a broken CSR are reported at the next synchronising call,
+    and the plan stays usable."""
+    import torch
+    inp, pp = synth.random_case(18, n_fft=12, n_bins=30, n_dir=1, p=0.5)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+    plan = fh.fh_create_plan(fh.make_desc(pp, 12, 1, inp.n_peaks))
+    try:
+        fh.fh_plan_set_input_checks(plan, fh.FH_CHECKS_DEVICE)
+        f = pin(inp.freq)
+        a = int(inp.offsets[4])
+        f[a], f[a + 1] = f[a + 1], f[a]
+        args = [pin(inp.t), pin(inp.offsets), f, pin(inp.v), pin(inp.sky)]
+        fh.fh_correct_doppler(plan, *args)
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_select_candidates(plan, 0, 1)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
+        off = pin(inp.offsets)
+        off[6] = inp.n_peaks + 50
+        fh.fh_correct_doppler(plan, args[0], off, pin(inp.freq), args[3], args[4],
+                              n_peaks=inp.n_peaks)
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_sync(plan)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
+        # valid page-locked inputs again: the oracle's candidates
+        good = [pin(x) for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+        fh.fh_correct_doppler(plan, *good)
+        fh.fh_transform(plan, 0, 1)
+        cand = fh.fh_select_candidates(plan, 0, 1)
+    finally:
+        fh.fh_destroy_plan(plan)
+    import oracle
+    o = oracle.search(inp, pp)
+    c = cand.reshape(1, -1, pp["top_k"])
+    assert np.array_equal(c["cell"], o["cell"]) and np.array_equal(c["count"], o["count"])
 
 
 def test_host_input_errors_checked_on_the_device(fh):
