@@ -63,31 +63,10 @@ __device__ __forceinline__ double norm_distance(const fh_cand_params &a, const f
 }
 
 // A pair farther apart in one parameter than `reach` bins cannot link or
-// coincide: that k exceeds reach, and the distance is at least each k to a unit
-// in the last place.  These tests multiply instead of dividing and keep a
-// margin of 1e-12, so they only reject pairs the exact test rejects too; they
-// run in the order that rejects most pairs first (frequency, spin-down,
-// latitude, longitude), and the divisions and the square root are left to
-// the few pairs that pass all four.
-__device__ __forceinline__ bool out_of_reach(double xa, double xb, double wa, double wb,
-                                             double reach)
-{
-    return fabs(xa - xb) > reach * ((wa + wb) * 0.5) * (1.0 + 1e-12);
-}
-__device__ __forceinline__ bool lam_out_of_reach(double la, double lb, double wa, double wb,
-                                                 double reach)
-{
-    double a = fabs(la - lb);
-    if (a > kPi) a = kTwoPi - a;
-    return a > reach * ((wa + wb) * 0.5) * (1.0 + 1e-12);
-}
-__device__ __forceinline__ bool f_out_of_reach(double fa, double fb, double dfa, double dfb,
-                                               double reach)
-{
-    return out_of_reach(fa, fb, dfa, dfb, reach);
-}
-
-// The same rejects in binary32, whose pipe is many times GB300's binary64 one.
+// coincide: that k exceeds reach, and the distance is at least each k.  These
+// rejects run in binary32, whose pipe is many times GB300's binary64 one, and
+// multiply instead of dividing; the exact binary64 divisions and square root
+// are left to the few pairs that pass all four.
 // A value rounded to float is off by at most half a float ulp, and the float
 // difference of two such values by another, so |x2 - x1| >= the float
 // difference - 2 ulp (ulp bounded by 2^-23 |x| plus the smallest normal); the
@@ -121,15 +100,6 @@ __device__ __forceinline__ bool any_far32(const fh_cand_params &a, const fh_cand
                    far32(a.beta, b.beta, a.dbeta, b.dbeta, reach_b) |
                    lam_far32(a.lam, b.lam, a.dlam, b.dlam, reach_l);
     return r;
-}
-__device__ __forceinline__ bool any_out_of_reach(const fh_cand_params &a,
-                                                 const fh_cand_params &b, double fa, double fb,
-                                                 double reach)
-{
-    return out_of_reach(fa, fb, a.df, b.df, reach) ||
-           out_of_reach(a.fdot, b.fdot, a.dfdot, b.dfdot, reach) ||
-           out_of_reach(a.beta, b.beta, a.dbeta, b.dbeta, reach) ||
-           lam_out_of_reach(a.lam, b.lam, a.dlam, b.dlam, reach);
 }
 
 // order-preserving map of doubles to unsigned 64-bit keys (for atomic min / max)
