@@ -875,18 +875,53 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             int own_nx = 0;
             if (T > 0) fetch(0, a1_nx, a2_nx, two_nx, own_nx);
             for (int base = 0; base < T; base += 32) {
-                const int64_t a1 = a1_nx, a2 = a2_nx;
-                const bool two = two_nx;
-                const int owner = own_nx;
+                int64_t a1 = a1_nx, a2 = a2_nx;
+                bool two = two_nx;
+                int owner = own_nx;
                 if (base + 32 < T) fetch(base + 32, a1_nx, a2_nx, two_nx, own_nx);
+                // A last round of L <= 16 slots (unclamped START walk): S = the
+                // power of two >= L; slot q = lane mod S is walked by the 32 / S
+                // lanes lane = q + S p, lane p taking rows S p .. S p + S - 1 in
+                // S Gray-code steps (row = lane ^ g(t), t < S).  Every (slot, row)
+                // is added once, the 32 lanes stay on 32 banks, and the start
+                // X = A - cb - lane D and the step table are those of a full round.
+                int S = 32;
+                if (MODE == FH_MODE_START && fast && T - base <= 16) {
+                    const int L = T - base;
+                    S = L <= 1 ? 1 : (L <= 2 ? 2 : (L <= 4 ? 4 : (L <= 8 ? 8 : 16)));
+                    const int src = lane & (S - 1);
+                    a1 = __shfl_sync(kFull, a1, src);
+                    a2 = __shfl_sync(kFull, a2, src);
+                    two = __shfl_sync(kFull, (int)two, src) != 0;
+                    owner = __shfl_sync(kFull, owner, src);
+                }
                 int64_t X1, X2 = 0, e[5];
                 int32_t ow;
-                setup(base + lane, a1, a2, two, owner, X1, X2, e, ow);
+                setup(base + (lane & (S - 1)), a1, a2, two, owner, X1, X2, e, ow);
                 if (MODE == FH_MODE_START) {
-                    if (fast)
-                        pair_steps<false, WEIGHTED>(std::make_integer_sequence<int, 32>{}, rbase, X1,
-                                                    X2, e, cell_stride, (uint32_t)E, (uint32_t)ow);
-                    else
+                    if (fast) {
+                        using std::make_integer_sequence;
+                        const uint32_t st = cell_stride, ee = (uint32_t)E, ww = (uint32_t)ow;
+                        switch (S) {
+                        case 1:
+                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 1>{}, rbase, X1, X2, e, st, ee, ww);
+                            break;
+                        case 2:
+                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 2>{}, rbase, X1, X2, e, st, ee, ww);
+                            break;
+                        case 4:
+                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 4>{}, rbase, X1, X2, e, st, ee, ww);
+                            break;
+                        case 8:
+                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 8>{}, rbase, X1, X2, e, st, ee, ww);
+                            break;
+                        case 16:
+                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 16>{}, rbase, X1, X2, e, st, ee, ww);
+                            break;
+                        default:
+                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 32>{}, rbase, X1, X2, e, st, ee, ww);
+                        }
+                    } else
                         pair_steps<true, WEIGHTED>(std::make_integer_sequence<int, 32>{}, rbase, X1,
                                                    X2, e, cell_stride, (uint32_t)E, (uint32_t)ow);
                 } else if (base + lane < T) {
