@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu legs")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--legs", default="adaptive,batched,serving,refine,peakmap,coincidences,"
+    ap.add_argument("--legs", default="maps,adaptive,batched,serving,refine,peakmap,coincidences,"
                                       "highfreq,cpu",
                     help="extra legs to run after the timed step (comma list)")
     return ap.parse_args()
@@ -162,10 +162,14 @@ def peaks_path():
     return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None, coinc=None):
-    """The oracle as it stands, whole path a1-a6 on the same workload (and, given
-    refine_args = (cells, rows, sky_ref, k_fdot), its refined-grid search on a
-    few of the workload's candidates)."""
+def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None, coinc=None,
+                     highfreq=None):
+    """The oracle as it stands, whole path a1-a6 on the same workload, with all
+    host threads and with one (and, given refine_args = (cells, rows, sky_ref,
+    k_fdot), its refined-grid search on a few of the workload's candidates;
+    given highfreq = (inputs, params), one of the 900 Hz workload's 64
+    directions, whose rate stands for all 64)."""
+    import numpy as np
     import oracle
     oracle.build()
     ref = None
@@ -190,6 +194,30 @@ def cpu_baseline_leg(inp, pp, budget_s=12.0, refine_args=None, peakmap=None, coi
     out = {"value": upd / best, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
            "sample": "whole path a1-a6 (maps, profile, selection) on the full workload, "
                      "1 direction, best of %d runs (%.2f s each)" % (len(times), best)}
+    n_thr = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.search(inp, pp)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(n_thr)
+    out["one_thread"] = {"value": upd / dt1, "unit": UNIT, "cores": 1,
+                         "sample": "the same whole path on one thread, one run (%.2f s)" % dt1}
+    if highfreq is not None:
+        hinp, hpp = highfreq
+        from paper_1407_8333_gb300 import synth
+        d = hinp.w.line_dir
+        one = synth.Inputs(w=hinp.w, t=hinp.t, offsets=hinp.offsets, freq=hinp.freq, v=hinp.v,
+                           sky=np.ascontiguousarray(hinp.sky[[d]]))
+        t0 = time.perf_counter()
+        oracle.search(one, hpp)
+        dth = time.perf_counter() - t0
+        hupd = one.n_peaks * hpp["n_fdot"]
+        out["highfreq"] = {"value": hupd / dth, "unit": UNIT, "cores": n_thr,
+                           "sample": "whole path on direction %d of the 900 Hz workload's 64 "
+                                     "(%.3g updates, one run, %.2f s); the per-update rate "
+                                     "stands for all 64" % (d, hupd, dth)}
     if ref is not None:
         out["refine"] = ref
     if coinc is not None:
@@ -396,16 +424,23 @@ def run_ours(args):
                 out["coincidences"] = coincidence_leg(fh, synth, torch, args.steps)
             except Exception as e:  # report, do not hide
                 out["coincidences"] = {"error": str(e)[:300]}
+        if "maps" in legs:
+            try:
+                out["maps_written"] = maps_leg(fh, w, inp, pp, dev, flush, torch, args.steps)
+            except Exception as e:  # report, do not hide
+                out["maps_written"] = {"error": str(e)[:300]}
+        hf_inputs = None
         if "highfreq" in legs:
             try:
-                out["highfreq"] = highfreq_leg(fh, synth, torch, min(args.steps, 5))
+                out["highfreq"], hf_inputs = highfreq_leg(fh, synth, torch, min(args.steps, 5))
             except Exception as e:  # report, do not hide
                 out["highfreq"] = {"error": str(e)[:300]}
         if "cpu" in legs:
             out["cpu_baseline"] = cpu_baseline_leg(
                 inp, pp, refine_args=ref_args,
                 peakmap=synth.peakmap_workload() if "peakmap" in legs else None,
-                coinc=coincidence_sets(synth, 5000, 1) if "coincidences" in legs else None)
+                coinc=coincidence_sets(synth, 5000, 1) if "coincidences" in legs else None,
+                highfreq=hf_inputs)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -673,6 +708,49 @@ def batched_vs_plain(fh, synth, torch):
     return res
 
 
+def maps_leg(fh, w, inp, pp, dev, flush, torch, steps):
+    """The benchmark step in its second mode: the full number-count map
+    (n_fdot x n_f0 int32 per direction, 383 MB here) written to HBM by the
+    transform's emit as well as the profile and candidates.  Same inputs, L2
+    flushed between steps, CUDA events."""
+    n_dir = inp.sky.shape[0]
+    maps = torch.empty((n_dir, pp["n_fdot"], pp["n_f0"]), dtype=torch.int32, device="cuda")
+    n_sb = -(-pp["n_f0"] // pp["subband_cells"])
+    cand = torch.empty(n_dir * n_sb * pp["top_k"] * 48, dtype=torch.uint8, device="cuda")
+    plan = fh.fh_create_plan(fh.make_desc(pp, w.n_fft, n_dir, inp.n_peaks))
+    try:
+        fh.fh_correct_doppler(plan, *dev)
+        tile, warps = fh.fh_autotune(plan, 0, n_dir)
+        ts = []
+        for k in range(3 + steps):
+            if k == 3:
+                fh.fh_plan_set_timing(plan, True)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fh.fh_correct_doppler(plan, *dev)
+            fh.fh_transform(plan, 0, n_dir, maps)
+            fh.fh_select_candidates(plan, 0, n_dir, cand)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(e0.elapsed_time(e1))
+        ng, win_sum, kern_sum = fh.fh_plan_kernel_times(plan)
+        fh.fh_plan_set_timing(plan, False)
+    finally:
+        fh.fh_destroy_plan(plan)
+    upd = inp.n_peaks * pp["n_fdot"] * n_dir
+    ms = statistics.mean(ts)
+    kern = kern_sum / len(ts)
+    map_bytes = 4 * pp["n_fdot"] * pp["n_f0"] * n_dir
+    return {"mode": "maps written to HBM (int32) plus profile and candidates",
+            "ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3),
+            "transform_kernel_ms": kern, "map_bytes": map_bytes,
+            "map_write_gbs": map_bytes / (kern * 1e-3) / 1e9,
+            "tile_cells": tile, "block_warps": warps, "steps": len(ts)}
+
+
 def highfreq_leg(fh, synth, torch, steps):
     """The largest single-GPU workload: T_FFT 1024 s over a year (61594 FFTs,
     ~26.5M peaks), band 900-910 Hz, 356 x 102400 map, 64 sky directions in one
@@ -712,13 +790,13 @@ def highfreq_leg(fh, synth, torch, steps):
     finally:
         fh.fh_destroy_plan(plan)
     ms = statistics.mean(t for t, _ in ts)
-    return {"workload": w.name, "n_peaks": inp.n_peaks, "n_dir": n_dir,
+    return ({"workload": w.name, "n_peaks": inp.n_peaks, "n_dir": n_dir,
             "map": [pp["n_fdot"], pp["n_f0"]], "updates_per_step": upd,
             "ms_per_step": ms, "updates_per_s": upd / (ms * 1e-3),
             "correct_plus_transform_ms": statistics.mean(t for _, t in ts),
             "transform_kernel_ms": kern_sum / len(ts), "window_kernel_ms": win_sum / len(ts),
             "tile_cells": tile, "block_warps": warps, "steps": len(ts),
-            "input_generation_s": gen_s}
+            "input_generation_s": gen_s}, (inp, pp))
 
 
 def serving_leg(fh, synth, torch, seconds):

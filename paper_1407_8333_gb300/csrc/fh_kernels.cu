@@ -963,6 +963,10 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             int win = row_ok ? 0 : -(1 << 26);
             if (c0 < c1)
                 for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
+            // a lane's map row is written 16 cells (64 bytes) at a time, as four
+            // 16-byte stores where the row is 16-byte aligned (the group's cells
+            // start at a multiple of 16 of the tile), else one cell at a time
+            const bool vec_map = maprow != nullptr && (((uintptr_t)maprow & 15u) == 0);
             auto run = [&](auto map_tag) {
                 constexpr bool kMap = decltype(map_tag)::value;
                 int c = c0;
@@ -970,13 +974,26 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     const int32_t *h0 = H + c * kRows + lane;
                     const int32_t *h1 = h0 + K * kRows;
                     int myv = 0;
+                    int cnts[kMap ? 16 : 1];
 #pragma unroll
                     for (int m = 0; m < 16; ++m) {
                         const int cnt = win;
                         win += h1[m * kRows] - h0[m * kRows];
-                        if (kMap && row_ok) maprow[c + m] = cnt;
+                        if constexpr (kMap) cnts[m] = cnt;
                         const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
                         if (lane == m) myv = v;
+                    }
+                    if constexpr (kMap) {
+                        if (vec_map) {
+                            int4 *d4 = reinterpret_cast<int4 *>(maprow + c);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                d4[q] = make_int4(cnts[4 * q], cnts[4 * q + 1], cnts[4 * q + 2],
+                                                  cnts[4 * q + 3]);
+                        } else if (row_ok) {
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) maprow[c + m] = cnts[m];
+                        }
                     }
                     if (lane < 16) atomicMax(prof + c + lane, key_of(myv));
                 }
