@@ -77,6 +77,10 @@ int max_optin_smem(int device)
     return v > 0 ? v : 48 * 1024;
 }
 
+// the error word (bytes 0..3) and the largest |D| (bytes 16..23) of a plan,
+// one allocation cleared by one memset per call
+constexpr size_t kErrWordsBytes = 32;
+
 // Device address of a page-locked (pinned or registered, mapped) host array,
 // which kernels can read in place; nullptr for pageable or unknown memory.
 const void *pinned_device_address(const void *h)
@@ -201,7 +205,7 @@ struct fh_plan_s {
     fh_candidate *cand = nullptr;
     int32_t *err = nullptr;
     int32_t *h_err = nullptr;  // pinned
-    unsigned long long *dmax = nullptr;  // largest |D_i| of the current peakmap
+    unsigned long long *dmax = nullptr;  // largest |D_i| of the current peakmap (in err's block)
     int2 *win = nullptr;                 // peak windows of the directions being transformed
     size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path
@@ -227,7 +231,7 @@ struct fh_plan_s {
         for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
         tev.clear();
         void *bufs[] = {t,    freq, v,   sky,  offsets, offsets_raw, S0, D,
-                        A,    profile, cand, err, dmax, win,  wq,  ws};
+                        A,    profile, cand, err, win,  wq,  ws};  // dmax lives in err's block
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -428,7 +432,7 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                   {(void **)&p->freq, s.freq},     {(void **)&p->v, s.v},
                   {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
                   {(void **)&p->profile, s.profile}, {(void **)&p->cand, s.cand},
-                  {(void **)&p->err, 16},          {(void **)&p->dmax, 16}};
+                  {(void **)&p->err, kErrWordsBytes}};
     for (auto &a : allocs) {
         e = cudaMalloc(a.ptr, (size_t)std::max<int64_t>(a.bytes, 16));
         if (e != cudaSuccess) {
@@ -439,6 +443,8 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                              (long long)a.bytes, cudaGetErrorString(e));
         }
     }
+    // the largest |D| lives in the error word's allocation, 16 bytes in
+    p->dmax = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(p->err) + 16);
     e = cudaMallocHost(&p->h_err, 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -446,7 +452,7 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
         delete p;
         return set_error(FH_ERR_NOMEM, "cudaMallocHost failed");
     }
-    cudaMemset(p->err, 0, 16);
+    cudaMemset(p->err, 0, kErrWordsBytes);
     *out = p;
     return FH_OK;
 }
@@ -637,8 +643,8 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     const int64_t *offs_in_place = nullptr;  // page-locked host offsets read in place
     const bool host_checks = p->input_checks == FH_CHECKS_HOST;
     p->weighted = false;  // a new peakmap starts with unit weights
-    cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->dmax, 0, sizeof(unsigned long long), s);
+    // the error word and the largest |D| share one allocation: one memset
+    cudaError_t e = cudaMemsetAsync(p->err, 0, kErrWordsBytes, s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
     if (pm->mem_kind == FH_MEM_HOST) {
         if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
@@ -724,12 +730,11 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     pa.D = p->D;
     pa.dmax = p->dmax;
     pa.err = p->err;
-    e = launch_prep(pa, s);
-    if (e != cudaSuccess) return cuda_error(e, "prep launch");
-    e = launch_positions(f_src, p->offsets, v_src, sky_src, n, np, n_dir, d.f0_min, p->kt,
-                         d.k_over, p->A, out_r, p->err, on_device, s);
-    if (e != cudaSuccess) return cuda_error(e, "positions launch");
-    p->launches += ((n > 0 || on_device) ? 1 : 0) + ((n > 0) ? 1 : 0);
+    // a1 - a3 in one launch (the CSR pass, the shift tables and the positions of
+    // every direction run side by side)
+    e = launch_correct(pa, f_src, d.f0_min, d.k_over, p->A, out_r, s);
+    if (e != cudaSuccess) return cuda_error(e, "correction launch");
+    p->launches += (n > 0 || pa.offsets_in || pa.validate) ? 1 : 0;
     if (out_A && np > 0) {
         e = cudaMemcpyAsync(out_A, p->A, 8 * (size_t)np * n_dir, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(out_A)");

@@ -82,6 +82,11 @@ struct PrepArgs {
     int32_t *err;
 };
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s);
+// a1 - a3 in one launch: prep's work (a.offsets_in sanitised into
+// a.offsets_out, shift tables, checks) and the positions of every (direction,
+// peak) of the peakmap described by a, frequencies freq
+cudaError_t launch_correct(const PrepArgs &a, const double *freq, double f0_min,
+                           int32_t k_over, int64_t *A, double *out_r, cudaStream_t s);
 
 // fh_refine on the plan's grid d (host inputs, host output; synchronises)
 int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm, const double *v_over_c,

@@ -65,28 +65,21 @@ __device__ __forceinline__ int64_t floor_times_2p32(double x)
 // peakmap) and written compactly by `offsets`.  With `validate`, the blocks of
 // direction 0 also flag frequencies that are not finite and positive
 // (kErrInvalid) or not strictly increasing within their FFT (kErrUnsorted).
-__global__ void __launch_bounds__(kPosThreads)
-positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
-                 const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
-                 int64_t n_peaks, double f0_min, double kt, double cshift,
-                 int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
-                 int32_t validate, const int64_t *__restrict__ src, PosBatch batch)
+// The body of one positions block: group `group` of 8 FFTs, direction d.
+// With clamp_offsets the CSR entries are raw: each is clamped into
+// [0, n_peaks] and made non-decreasing within the block, which keeps every
+// access in bounds (a valid CSR is unchanged; an invalid one is flagged by the
+// global CSR pass).
+__device__ __forceinline__ void positions_block(
+    const double *__restrict__ freq, const int64_t *__restrict__ offsets, bool clamp_offsets,
+    const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft, int64_t n_peaks,
+    double f0_min, double kt, double cshift, int64_t *__restrict__ A, double *__restrict__ out_r,
+    int32_t *err, int32_t validate, const int64_t *__restrict__ src, int d, int group)
 {
-    // batches (refinement): block z is one peakmap of several, each with its own
-    // offsets, source index, sky directions, output base and peak count
-    if (batch.a_base) {
-        const int c = blockIdx.z;
-        offsets += (int64_t)c * (n_fft + 1);
-        src += (int64_t)c * n_fft;
-        sky += 3 * (int64_t)c * gridDim.y;
-        A += batch.a_base[c];
-        n_peaks = batch.n_peaks[c];
-    }
     __shared__ double r_s[kPosFfts];
     __shared__ int64_t off_s[kPosFfts + 1];
     __shared__ int64_t src_s[kPosFfts];  // where each FFT's peaks start in freq
-    const int d = blockIdx.y;
-    const int i0 = blockIdx.x * kPosFfts;
+    const int i0 = group * kPosFfts;
     const int nf = min(kPosFfts, n_fft - i0);
     if (threadIdx.x < nf) {
         const int i = i0 + threadIdx.x;
@@ -99,10 +92,22 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
         r_s[threadIdx.x] = r;
         if (out_r) out_r[(int64_t)d * n_fft + i] = r;
     }
-    if (threadIdx.x <= nf) off_s[threadIdx.x] = offsets[i0 + threadIdx.x];
-    if (threadIdx.x < nf)
+    if (threadIdx.x <= nf) {
+        int64_t o = offsets[i0 + threadIdx.x];
+        if (clamp_offsets) o = o < 0 ? 0 : (o > n_peaks ? n_peaks : o);
+        off_s[threadIdx.x] = o;
+    }
+    if (!clamp_offsets && threadIdx.x < nf)
         src_s[threadIdx.x] = src ? src[i0 + threadIdx.x] : offsets[i0 + threadIdx.x];
     __syncthreads();
+    if (clamp_offsets) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k <= nf; ++k) {
+                if (k > 0 && off_s[k] < off_s[k - 1]) off_s[k] = off_s[k - 1];
+                if (k < nf) src_s[k] = off_s[k];
+            }
+        __syncthreads();
+    }
     const int64_t p_begin = off_s[0], p_end = off_s[nf];
     int64_t *__restrict__ Ad = A + (int64_t)d * n_peaks;
     const bool check = validate && d == 0;
@@ -124,7 +129,7 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
             // positive finite doubles order like their bit patterns
             const int64_t fb = __double_as_longlong(f);
             int64_t prev = __shfl_up_sync(kFull, fb, 1);
-            if (lane == 0 && in && p > p_begin) prev = __double_as_longlong(freq[fp - 1]);
+            if (lane == 0 && in && p > off_s[lo]) prev = __double_as_longlong(freq[fp - 1]);
             if (in) {
                 if (!(fb > 0 && fb < 0x7FF0000000000000LL)) ev |= kErrInvalid;
                 if (p > off_s[lo] && !(fb > prev)) ev |= kErrUnsorted;
@@ -144,107 +149,182 @@ positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ of
     if (bad) atomicOr(err, kErrRange);
 }
 
+__global__ void __launch_bounds__(kPosThreads)
+positions_kernel(const double *__restrict__ freq, const int64_t *__restrict__ offsets,
+                 const double *__restrict__ v, const double *__restrict__ sky, int32_t n_fft,
+                 int64_t n_peaks, double f0_min, double kt, double cshift,
+                 int64_t *__restrict__ A, double *__restrict__ out_r, int32_t *err,
+                 int32_t validate, const int64_t *__restrict__ src, PosBatch batch)
+{
+    // batches (refinement): block z is one peakmap of several, each with its own
+    // offsets, source index, sky directions, output base and peak count
+    if (batch.a_base) {
+        const int c = blockIdx.z;
+        offsets += (int64_t)c * (n_fft + 1);
+        src += (int64_t)c * n_fft;
+        sky += 3 * (int64_t)c * gridDim.y;
+        A += batch.a_base[c];
+        n_peaks = batch.n_peaks[c];
+    }
+    positions_block(freq, offsets, false, v, sky, n_fft, n_peaks, f0_min, kt, cshift, A, out_r,
+                    err, validate, src, blockIdx.y, blockIdx.x);
+}
+
 // ---------------------------------------------------------------- a3 + per-call set-up
-// grid 1 + ceil(n_fft / 1024), 1024 threads (see PrepArgs).  Block 0 sanitises
-// the CSR and checks the sky directions; block b > 0 takes FFTs
-// (b - 1) * 1024 ... b * 1024 - 1.  The CSR pass takes 4 consecutive entries
-// per thread (4096 per pass): a running maximum inside the thread, a warp
-// scan and one block step carry it across the pass.
-__global__ void __launch_bounds__(1024) prep_kernel(const PrepArgs a)
+// The CSR pass (one block of any size): 4 consecutive entries per thread
+// (4 x blockDim per pass), a running maximum inside the thread, a warp scan and
+// one block step carry it across the pass; raw entries outside [0, n_peaks],
+// a first entry other than 0, a last other than n_peaks or a decrease are
+// flagged (kErrCsr).
+__device__ __forceinline__ void csr_pass(const PrepArgs &a, int32_t &e)
 {
     __shared__ int64_t wmax[32];
     __shared__ int64_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.n_fft;
-    int32_t e = 0;
-    if (blockIdx.x == 0 && a.offsets_in) {
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (int base = 0; base <= n; base += 4 * 1024) {
-            const int i0 = base + 4 * threadIdx.x;
-            int64_t x[4];
-            int64_t prev_raw = (i0 > 0 && i0 <= n) ? a.offsets_in[i0 - 1] : 0;
-            int64_t run = 0;
+    const int nt = blockDim.x;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base <= n; base += 4 * nt) {
+        const int i0 = base + 4 * threadIdx.x;
+        int64_t x[4];
+        int64_t prev_raw = (i0 > 0 && i0 <= n) ? a.offsets_in[i0 - 1] : 0;
+        int64_t run = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = i0 + j;
-                int64_t y = 0;
-                if (i <= n) {
-                    const int64_t raw = a.offsets_in[i];
-                    if (raw < 0 || raw > a.n_peaks) e |= kErrCsr;
-                    if (i == 0 && raw != 0) e |= kErrCsr;
-                    if (i == n && raw != a.n_peaks) e |= kErrCsr;
-                    if (i > 0 && raw < prev_raw) e |= kErrCsr;
-                    prev_raw = raw;
-                    y = raw < 0 ? 0 : (raw > a.n_peaks ? a.n_peaks : raw);
-                    if (i == 0) y = 0;
-                }
-                run = y > run ? y : run;
-                x[j] = run;
+        for (int j = 0; j < 4; ++j) {
+            const int i = i0 + j;
+            int64_t y = 0;
+            if (i <= n) {
+                const int64_t raw = a.offsets_in[i];
+                if (raw < 0 || raw > a.n_peaks) e |= kErrCsr;
+                if (i == 0 && raw != 0) e |= kErrCsr;
+                if (i == n && raw != a.n_peaks) e |= kErrCsr;
+                if (i > 0 && raw < prev_raw) e |= kErrCsr;
+                prev_raw = raw;
+                y = raw < 0 ? 0 : (raw > a.n_peaks ? a.n_peaks : raw);
+                if (i == 0) y = 0;
             }
-            // exclusive running maximum of the threads before this one
-            int64_t inc = run;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o && y > inc) inc = y;
-            }
-            int64_t exc = __shfl_up_sync(kFull, inc, 1);
-            if (lane == 0) exc = 0;
-            if (lane == 31) wmax[warp] = inc;
-            __syncthreads();
-            int64_t pre = carry;
-            for (int w = 0; w < warp; ++w) pre = wmax[w] > pre ? wmax[w] : pre;
-            pre = exc > pre ? exc : pre;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = i0 + j;
-                if (i <= n) a.offsets_out[i] = (i == n) ? a.n_peaks : (x[j] > pre ? x[j] : pre);
-            }
-            __syncthreads();
-            if (threadIdx.x == 1023) carry = inc > pre ? inc : pre;
-            __syncthreads();
+            run = y > run ? y : run;
+            x[j] = run;
         }
+        // exclusive running maximum of the threads before this one
+        int64_t inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o && y > inc) inc = y;
+        }
+        int64_t exc = __shfl_up_sync(kFull, inc, 1);
+        if (lane == 0) exc = 0;
+        if (lane == 31) wmax[warp] = inc;
+        __syncthreads();
+        int64_t pre = carry;
+        for (int w = 0; w < warp; ++w) pre = wmax[w] > pre ? wmax[w] : pre;
+        pre = exc > pre ? exc : pre;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = i0 + j;
+            if (i <= n) a.offsets_out[i] = (i == n) ? a.n_peaks : (x[j] > pre ? x[j] : pre);
+        }
+        __syncthreads();
+        if (threadIdx.x == nt - 1) carry = inc > pre ? inc : pre;
+        __syncthreads();
     }
-    // shift tables (and per-FFT checks)
+}
+
+// Shift tables of FFT i (a3) and its checks; |D_i| into amax.
+__device__ __forceinline__ void fft_tables(const PrepArgs &a, int i, int32_t &e,
+                                           unsigned long long &amax)
+{
     const double f_last = __dadd_rn(a.fdot_min, __dmul_rn((double)(a.n_fdot - 1), a.fdot_step));
     const double absmax = fabs(a.fdot_min) > fabs(f_last) ? fabs(a.fdot_min) : fabs(f_last);
-    unsigned long long amax = 0;
-    const int i = (int)(blockIdx.x - 1) * 1024 + (int)threadIdx.x;
-    if (blockIdx.x > 0 && i < n) {
-        const double ti = a.t[i];
-        const double dt = __dsub_rn(ti, a.t_ref);
-        const double c = __dmul_rn(dt, a.kt);
-        const double s0 = __dmul_rn(a.fdot_min, c);
-        const double dd = __dmul_rn(a.fdot_step, c);
-        if (!(fabs(c) * absmax < (double)kFixedLimit)) e |= kErrRange;
-        a.S0[i] = (int64_t)floor(__dmul_rn(s0, kTwo32));
-        const int64_t Di = (int64_t)floor(__dmul_rn(dd, kTwo32));
-        a.D[i] = Di;
-        const unsigned long long m = (unsigned long long)(Di < 0 ? -Di : Di);
-        amax = m > amax ? m : amax;
-        if (a.validate) {
-            if (!isfinite(ti) || (i > 0 && !(ti > a.t[i - 1]))) e |= kErrUnsorted;
-            for (int k = 0; k < 3; ++k)
-                if (!(fabs(a.v[3 * (int64_t)i + k]) < 0.1)) e |= kErrInvalid;
-        }
+    const double ti = a.t[i];
+    const double dt = __dsub_rn(ti, a.t_ref);
+    const double c = __dmul_rn(dt, a.kt);
+    const double s0 = __dmul_rn(a.fdot_min, c);
+    const double dd = __dmul_rn(a.fdot_step, c);
+    if (!(fabs(c) * absmax < (double)kFixedLimit)) e |= kErrRange;
+    a.S0[i] = (int64_t)floor(__dmul_rn(s0, kTwo32));
+    const int64_t Di = (int64_t)floor(__dmul_rn(dd, kTwo32));
+    a.D[i] = Di;
+    const unsigned long long m = (unsigned long long)(Di < 0 ? -Di : Di);
+    amax = m > amax ? m : amax;
+    if (a.validate) {
+        if (!isfinite(ti) || (i > 0 && !(ti > a.t[i - 1]))) e |= kErrUnsorted;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (!(fabs(a.v[3 * (int64_t)i + k]) < 0.1)) e |= kErrInvalid;
     }
-    if (blockIdx.x == 0 && a.validate) {
-        for (int d = threadIdx.x; d < a.n_dir; d += 1024) {
-            const double x = a.sky[3 * (int64_t)d], y = a.sky[3 * (int64_t)d + 1],
-                         z = a.sky[3 * (int64_t)d + 2];
-            if (!(fabs(x) <= 1.000001 && fabs(y) <= 1.000001 && fabs(z) <= 1.000001))
-                e |= kErrInvalid;
-        }
+}
+
+__device__ __forceinline__ void sky_checks(const PrepArgs &a, int32_t &e)
+{
+    for (int d = threadIdx.x; d < a.n_dir; d += blockDim.x) {
+        const double x = a.sky[3 * (int64_t)d], y = a.sky[3 * (int64_t)d + 1],
+                     z = a.sky[3 * (int64_t)d + 2];
+        if (!(fabs(x) <= 1.000001 && fabs(y) <= 1.000001 && fabs(z) <= 1.000001))
+            e |= kErrInvalid;
     }
-    // largest per-row drift, for the transform's guard cells
+}
+
+// the warp's largest |D| and error bits, one atomic each
+__device__ __forceinline__ void flush_prep(const PrepArgs &a, int32_t e, unsigned long long amax)
+{
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_down_sync(kFull, amax, o);
         amax = y > amax ? y : amax;
     }
-    if (lane == 0 && amax) atomicMax(a.dmax, amax);
+    if ((threadIdx.x & 31) == 0 && amax) atomicMax(a.dmax, amax);
     e = (int32_t)__reduce_or_sync(kFull, (unsigned)e);
-    if (lane == 0 && e) atomicOr(a.err, e);
+    if ((threadIdx.x & 31) == 0 && e) atomicOr(a.err, e);
+}
+
+// grid 1 + ceil(n_fft / 1024), 1024 threads (see PrepArgs).  Block 0 sanitises
+// the CSR and checks the sky directions; block b > 0 takes FFTs
+// (b - 1) * 1024 ... b * 1024 - 1.
+__global__ void __launch_bounds__(1024, 1) prep_kernel(const PrepArgs a)
+{
+    int32_t e = 0;
+    unsigned long long amax = 0;
+    if (blockIdx.x == 0) {
+        if (a.offsets_in) csr_pass(a, e);
+        if (a.validate) sky_checks(a, e);
+    } else {
+        const int i = (int)(blockIdx.x - 1) * 1024 + (int)threadIdx.x;
+        if (i < a.n_fft) fft_tables(a, i, e, amax);
+    }
+    flush_prep(a, e, amax);
+}
+
+// a1 - a3 in one launch (fh_correct_doppler): grid (1 + ceil(n_fft / 8), n_dir),
+// kPosThreads threads.  Block (0, 0) sanitises the CSR for the later kernels
+// and checks the sky directions; block (x, d), x >= 1, computes the positions
+// of FFTs 8 (x - 1) .. 8 (x - 1) + 7 for direction d (clamping the raw CSR
+// entries it reads when they still need sanitising, so it does not wait for
+// block (0, 0)), and the blocks of direction 0 also the shift tables and
+// per-FFT checks of their FFTs.
+__global__ void __launch_bounds__(kPosThreads)
+correct_kernel(const PrepArgs a, const double *__restrict__ freq, double f0_min, double cshift,
+               int64_t *__restrict__ A, double *__restrict__ out_r)
+{
+    int32_t e = 0;
+    unsigned long long amax = 0;
+    if (blockIdx.x == 0) {
+        if (blockIdx.y != 0) return;
+        if (a.offsets_in) csr_pass(a, e);
+        if (a.validate) sky_checks(a, e);
+        flush_prep(a, e, amax);
+        return;
+    }
+    const int group = (int)blockIdx.x - 1, d = (int)blockIdx.y;
+    if (d == 0) {
+        const int i = group * kPosFfts + (int)threadIdx.x;
+        if (threadIdx.x < kPosFfts && i < a.n_fft) fft_tables(a, i, e, amax);
+        if (threadIdx.x < 32) flush_prep(a, e, amax);
+    }
+    const bool raw = a.offsets_in != nullptr;
+    positions_block(freq, raw ? a.offsets_in : a.offsets_out, raw, a.v, a.sky, a.n_fft, a.n_peaks,
+                    f0_min, a.kt, cshift, A, out_r, a.err, a.validate, nullptr, d, group);
 }
 
 // ---------------------------------------------------------------- a3
@@ -1261,6 +1341,17 @@ cudaError_t launch_positions(const double *freq, const int64_t *offsets, const d
     positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
                                                   kt, cshift, A, out_r, err, validate ? 1 : 0,
                                                   src, PosBatch{nullptr, nullptr});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct(const PrepArgs &a, const double *freq, double f0_min,
+                           int32_t k_over, int64_t *A, double *out_r, cudaStream_t s)
+{
+    if (a.n_fft <= 0 && !a.offsets_in && !(a.validate && a.n_dir > 0)) return cudaSuccess;
+    const double cshift = 0.5 - 0.5 * (double)k_over;
+    const unsigned groups = (unsigned)((std::max(0, a.n_fft) + kPosFfts - 1) / kPosFfts);
+    dim3 grid(1 + groups, std::max(1, a.n_dir));
+    correct_kernel<<<grid, kPosThreads, 0, s>>>(a, freq, f0_min, cshift, A, out_r);
     return cudaGetLastError();
 }
 
