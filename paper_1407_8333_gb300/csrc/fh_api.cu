@@ -756,8 +756,12 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps, guard);
     int rc = prepare_transform(p, p->mode, smem);
     if (rc) return rc;
-    cudaError_t e = cudaMemsetAsync(p->profile + (int64_t)dir_begin * d.n_f0, 0,
-                                    sizeof(uint64_t) * (size_t)n_dir * d.n_f0, s);
+    // the window pre-pass clears each direction's profile before the transform
+    // merges into it; without FFTs there is no pre-pass, so clear it here
+    cudaError_t e = cudaSuccess;
+    if (p->n_fft <= 0)
+        e = cudaMemsetAsync(p->profile + (int64_t)dir_begin * d.n_f0, 0,
+                            sizeof(uint64_t) * (size_t)n_dir * d.n_f0, s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(profile)");
     TransformJob job{};
     job.A = p->A;

@@ -509,6 +509,14 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     const int d_rel = blockIdx.y;
     const int d_abs = J.dir_begin + d_rel;
     const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
+    {
+        // the transform merges into this direction's profile by atomicMax from 0:
+        // the blocks of the direction clear it here, a strided slice each
+        uint64_t *pr = J.profile + (int64_t)d_abs * J.n_f0;
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < J.n_f0;
+             k += (int64_t)gridDim.x * blockDim.x)
+            pr[k] = 0;
+    }
     const int64_t o0 = live ? J.offsets[i] : 0;
     const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
     const bool staged = n + 2 * kWinPad <= kWinPeaks;
