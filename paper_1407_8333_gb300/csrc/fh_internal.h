@@ -95,10 +95,6 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm, const dou
                 bool host_checks, cudaStream_t s);
 // the error of a device error word (0: FH_OK)
 int device_error_code(int32_t bits);
-cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
-                                double fdot_min, double fdot_step, int32_t n_fdot,
-                                int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,
-                                cudaStream_t s);
 cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
                              const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
                              double f0_min, double kt, int32_t k_over, int64_t *A,

@@ -1,10 +1,13 @@
 // Kernels of the frequency-Hough hot path (sm_103a).
 //
-//   prep_kernel          a3       per-FFT spin-down shift (Eqs. uno, sdstep), CSR
-//                                 sanitising and per-FFT input checks
-//   positions_kernel     a1 + a2  Doppler factor and 32.32 fixed-point stripe start
-//                                 (Eq. fdopp; Sec. VI; Eq. freqres)
-//   shift_tables_kernel  a3       the shift tables alone (server path)
+//   correct_kernel       a1 - a3  one launch: CSR sanitising, per-FFT spin-down shift
+//                                 (Eqs. uno, sdstep) and input checks, Doppler factor
+//                                 and 32.32 fixed-point stripe start (Eq. fdopp;
+//                                 Sec. VI; Eq. freqres) of every direction
+//   prep_kernel          a3       the shift tables, CSR sanitising and checks alone
+//   positions_kernel     a1 + a2  the positions alone, also of several peakmaps
+//                                 (refined-grid search)
+//   windows_kernel       a4       which peaks can reach each tile; clears the profile
 //   transform_kernel     a4 + a5 + profile half of a6 (Eqs. due, ncount; Sec. VIII)
 //   select_kernel        a6       per-sub-band greedy picks (Sec. VIII; Eq. cr)
 //
@@ -327,32 +330,6 @@ correct_kernel(const PrepArgs a, const double *__restrict__ freq, double f0_min,
                     f0_min, a.kt, cshift, A, out_r, a.err, a.validate, nullptr, d, group);
 }
 
-// ---------------------------------------------------------------- a3
-__global__ void shift_tables_kernel(const double *__restrict__ t, int32_t n_fft, double t_ref,
-                                    double kt, double fdot_min, double fdot_step,
-                                    double fdot_absmax, int64_t *__restrict__ S0,
-                                    int64_t *__restrict__ D, unsigned long long *dmax, int32_t *err)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long amax = 0;
-    if (i < n_fft) {
-        const double dt = __dsub_rn(t[i], t_ref);
-        const double c = __dmul_rn(dt, kt);
-        const double s0 = __dmul_rn(fdot_min, c);
-        const double dd = __dmul_rn(fdot_step, c);
-        if (!(fabs(c) * fdot_absmax < (double)kFixedLimit)) atomicOr(err, kErrRange);
-        S0[i] = (int64_t)floor(__dmul_rn(s0, kTwo32));
-        const int64_t Di = (int64_t)floor(__dmul_rn(dd, kTwo32));
-        D[i] = Di;
-        amax = (unsigned long long)(Di < 0 ? -Di : Di);
-    }
-    // largest per-row drift, for the transform's guard cells
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_down_sync(kFull, amax, o);
-        amax = y > amax ? y : amax;
-    }
-    if ((threadIdx.x & 31) == 0 && amax) atomicMax(dmax, amax);
-}
 
 // ---------------------------------------------------------------- device inputs
 // Flags non-finite / unordered device inputs (the refined-grid search under
@@ -1316,19 +1293,6 @@ smem_atomic_bench_kernel(int32_t variant, int32_t iters, unsigned long long *sin
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_shift_tables(const double *t, int32_t n_fft, double t_ref, double kt,
-                                double fdot_min, double fdot_step, int32_t n_fdot,
-                                int64_t *S0, int64_t *D, unsigned long long *dmax, int32_t *err,
-                                cudaStream_t s)
-{
-    if (n_fft <= 0) return cudaSuccess;
-    const double f_last = fdot_min + (double)(n_fdot - 1) * fdot_step;
-    const double absmax = fabs(fdot_min) > fabs(f_last) ? fabs(fdot_min) : fabs(f_last);
-    shift_tables_kernel<<<(n_fft + 255) / 256, 256, 0, s>>>(t, n_fft, t_ref, kt, fdot_min,
-                                                             fdot_step, absmax, S0, D, dmax, err);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s)
 {
     if (a.n_fft <= 0 && !a.offsets_in && !(a.validate && a.n_dir > 0)) return cudaSuccess;

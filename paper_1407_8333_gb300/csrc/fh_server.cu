@@ -201,13 +201,27 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
                 e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(j->d_err, 0, 16, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(j->d_dmax, 0, 16, s);
-        if (e == cudaSuccess)
-            e = launch_shift_tables(j->d_t, j->n_fft, d.t_ref, j->kt, d.fdot_min, d.fdot_step,
-                                    d.n_fdot, j->d_S0, j->d_D, j->d_dmax, j->d_err, s);
-        if (e == cudaSuccess)
-            e = launch_positions(j->d_freq, j->d_off, j->d_v, j->d_sky, j->n_fft, j->n_peaks,
-                                 j->n_dir, d.f0_min, j->kt, d.k_over, j->d_A, nullptr, j->d_err,
-                                 false, s);
+        // shift tables and positions in one launch (the CSR was checked at submit)
+        PrepArgs pa{};
+        pa.offsets_in = nullptr;
+        pa.offsets_out = j->d_off;
+        pa.t = j->d_t;
+        pa.v = j->d_v;
+        pa.sky = j->d_sky;
+        pa.n_fft = j->n_fft;
+        pa.n_dir = j->n_dir;
+        pa.n_fdot = d.n_fdot;
+        pa.validate = 0;
+        pa.n_peaks = j->n_peaks;
+        pa.t_ref = d.t_ref;
+        pa.kt = j->kt;
+        pa.fdot_min = d.fdot_min;
+        pa.fdot_step = d.fdot_step;
+        pa.S0 = j->d_S0;
+        pa.D = j->d_D;
+        pa.dmax = j->d_dmax;
+        pa.err = j->d_err;
+        if (e == cudaSuccess) e = launch_correct(pa, j->d_freq, d.f0_min, d.k_over, j->d_A, nullptr, s);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(j->d_prof, 0, 8 * (size_t)j->n_dir * d.n_f0, s);
         if (e != cudaSuccess) return cuda_error(e, "job set-up");

@@ -141,10 +141,7 @@ int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const doubl
     pa.D = D;
     pa.dmax = dmax;
     pa.err = err;
-    if (e == cudaSuccess) e = launch_prep(pa, s);
-    if (e == cudaSuccess)
-        e = launch_positions(pm->freq, offsets, v_over_c, sky_n, n, np, 1, d.f0_min, kt, d.k_over, A,
-                             nullptr, err, true, s);
+    if (e == cudaSuccess) e = launch_correct(pa, pm->freq, d.f0_min, d.k_over, A, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "fh_search_static set-up");
 
     const int32_t mode = d.mode == FH_MODE_DIFF ? FH_MODE_DIFF : FH_MODE_START;
