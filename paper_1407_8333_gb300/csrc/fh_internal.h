@@ -95,15 +95,10 @@ int refine_impl(const fh_plan_desc &d, int n_sm, const fh_peakmap *pm, const dou
                 bool host_checks, cudaStream_t s);
 // the error of a device error word (0: FH_OK)
 int device_error_code(int32_t bits);
-cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
-                             const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
-                             double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, bool validate, cudaStream_t s,
-                             const int64_t *src = nullptr);
 // positions of n_batch peakmaps (refinement): batch c has offsets
 // offsets + c (n_fft + 1), source index src + c n_fft, sky + 3 c n_dir, its peak
 // count n_peaks[c] (device) and its positions at A + a_base[c] (device),
-// direction-major as for launch_positions
+// direction-major ([direction][peak] within each batch)
 cudaError_t launch_positions_batched(const double *freq, const int64_t *offsets,
                                      const double *v, const double *sky, int32_t n_fft,
                                      int32_t n_dir, int32_t n_batch, const int64_t *a_base,

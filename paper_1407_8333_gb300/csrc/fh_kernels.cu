@@ -1301,21 +1301,6 @@ cudaError_t launch_prep(const PrepArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_positions(const double *freq, const int64_t *offsets, const double *v,
-                             const double *sky, int32_t n_fft, int64_t n_peaks, int32_t n_dir,
-                             double f0_min, double kt, int32_t k_over, int64_t *A,
-                             double *out_r, int32_t *err, bool validate, cudaStream_t s,
-                             const int64_t *src)
-{
-    if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
-    const double cshift = 0.5 - 0.5 * (double)k_over;
-    dim3 grid((n_fft + kPosFfts - 1) / kPosFfts, n_dir);
-    positions_kernel<<<grid, kPosThreads, 0, s>>>(freq, offsets, v, sky, n_fft, n_peaks, f0_min,
-                                                  kt, cshift, A, out_r, err, validate ? 1 : 0,
-                                                  src, PosBatch{nullptr, nullptr});
-    return cudaGetLastError();
-}
-
 cudaError_t launch_correct(const PrepArgs &a, const double *freq, double f0_min,
                            int32_t k_over, int64_t *A, double *out_r, cudaStream_t s)
 {
