@@ -417,21 +417,19 @@ __device__ __forceinline__ void lookup_window(const int64_t *__restrict__ Ad,
 // on each side; those extra peaks reach only guard cells (the transform's
 // guard keeps a margin of two cells), so they change no count.
 //
-// A block takes 8 FFTs of one direction, one warp per FFT; the FFT's peak
-// cells (ascending) are copied into shared memory once, between one sentinel
-// on each side (an FFT with more than kWinPeaks - 2 peaks is read from global
-// memory, with bounds checks).  Lane l takes tiles l, l + 32, ... (M per pass,
-// M = 1 .. 3 from the tile count: the lane's per-slab work -- the 64-bit
-// bounds, the branches, the barrier -- is shared by M entries, and the M
-// searches of a slab are independent) and walks the slabs in order: the first
-// slab's bounds come from a binary search, each later one from a step in the
-// direction of the FFT's drift D (both bounds move monotonically with the
-// slab, by 32 D).
-// Each (slab, 32 M tiles) result is staged as [FFT][tile] (row pitch 32 M + 4
-// entries = 4 mod 16 eight-byte banks: both the lanes' writes and the 8-FFT
-// runs read back take the minimum of shared-memory wavefronts) and written as
-// 64-byte runs of 8 FFTs, the layout the transform reads with one 8-byte load
-// per lane.
+// A block takes 8 FFTs of one direction; warp w copies FFT w's peak cells
+// (ascending) into shared memory once, between one sentinel on each side (an
+// FFT with more than kWinPeaks - 2 peaks is read from global memory, with
+// bounds checks).  Lane l of warp w then takes FFT l mod 8 and tiles
+// 4 w + l / 8 + 32 m (M per pass, M = 1 .. 3 from the tile count, so that the
+// per-slab work -- the 64-bit bounds, the branches -- is shared by M entries
+// and the M searches of a slab are independent), and walks the slabs in
+// order: the first slab's bounds come from a binary search, each later one
+// from a step in the direction of its FFT's drift D (both bounds move
+// monotonically with the slab, by 32 D).  A warp's 32 entries of a slab are
+// 4 tiles x 8 consecutive FFTs, i.e. four 64-byte runs of the [slab][tile][FFT]
+// table the transform reads with one 8-byte load per lane, so each warp
+// writes its own runs and the slab loop has no barrier.
 // grid (ceil(n_fft / 8), n_dir), 256 threads.
 constexpr int kWinPeaks = 1024;
 constexpr int kWinPad = 1;
@@ -476,13 +474,10 @@ template <int M>
 __global__ void __launch_bounds__(256, 4)
 windows_kernel(const TransformJob J, int2 *__restrict__ windows)
 {
-    constexpr int kTiles = 32 * M;     // tiles per pass
-    constexpr int kPitch = kTiles + 4;  // = 4 mod 16 eight-byte banks
-    __shared__ int32_t cell_s[8][kWinPeaks];
-    __shared__ int2 stage[2][8][kPitch];  // double buffer: one barrier per slab
-    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;  // warp = FFT of the block
-    const int i = blockIdx.x * 8 + f;
-    const bool live = i < J.n_fft;
+    constexpr int kTiles = 32 * M;  // tiles per pass
+    // rows padded by one word: lanes on different FFTs fall on different banks
+    __shared__ int32_t cell_s[8][kWinPeaks + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int d_rel = blockIdx.y;
     const int d_abs = J.dir_begin + d_rel;
     const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
@@ -494,46 +489,55 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
              k += (int64_t)gridDim.x * blockDim.x)
             pr[k] = 0;
     }
+    {
+        // warp w stages FFT w of the block
+        const int is = blockIdx.x * 8 + warp;
+        const bool ls = is < J.n_fft;
+        const int64_t os = ls ? J.offsets[is] : 0;
+        const int ns = ls ? (int)(J.offsets[is + 1] - os) : 0;
+        if (ns + 2 * kWinPad <= kWinPeaks) {
+            int32_t *c = &cell_s[warp][kWinPad];
+            const int64_t *As = Ad + os;
+            for (int k = lane; k < ns; k += 32) c[k] = global_cell(As, k);
+            if (lane < kWinPad) {
+                c[-1 - lane] = INT_MIN;
+                c[ns + lane] = INT_MAX;
+            }
+        }
+    }
+    __syncthreads();
+    // this lane's FFT and tiles
+    const int f = lane & 7;
+    const int tq = 4 * warp + (lane >> 3);
+    const int i = blockIdx.x * 8 + f;
+    const bool live = i < J.n_fft;
     const int64_t o0 = live ? J.offsets[i] : 0;
     const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
     const bool staged = n + 2 * kWinPad <= kWinPeaks;
     const int64_t *Ai = Ad + o0;
-    int32_t *cs = &cell_s[f][kWinPad];
-    if (staged) {
-        for (int k = lane; k < n; k += 32) cs[k] = global_cell(Ai, k);
-        if (lane < kWinPad) {
-            cs[-1 - lane] = INT_MIN;
-            cs[n + lane] = INT_MAX;
-        }
-    }
-    __syncwarp();  // a warp reads only its own FFT's cells
+    const int32_t *cs = &cell_s[f][kWinPad];
     const int64_t dv = live ? J.D[i] : 0;
     const int64_t s0 = live ? J.S0[i] : 0;
     const int K = J.k_over, W = J.tile_cells;
     const int64_t nf = J.n_fft;
     const int64_t slab_stride = (int64_t)J.n_tiles * nf;
     int2 *out = windows + (int64_t)d_rel * J.n_slabs * slab_stride;
-    const int efi = blockIdx.x * 8 + (threadIdx.x & 7);  // FFT of this thread's staged entries
     for (int t0 = 0; t0 < J.n_tiles; t0 += kTiles) {
         const int nt = min(kTiles, J.n_tiles - t0);
         // the lane's tiles: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
         int blo[M], bhi[M], qa[M], qb[M];
         bool ok[M];
-        // this thread's staged entries go to fixed (tile, FFT) places of every slab
         int2 *dst[M];
-        bool dst_ok[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const int tt = lane + 32 * m;
+            const int tt = tq + 32 * m;
             ok[m] = live && tt < nt;
             const int b0 = (t0 + tt) * W;
             blo[m] = b0 - K + 1;
             bhi[m] = b0 + min(W, J.n_f0 - b0);
             qa[m] = 0;
             qb[m] = 0;
-            const int est = (threadIdx.x >> 3) + 32 * m;
-            dst_ok[m] = est < nt && efi < J.n_fft;
-            dst[m] = out + (int64_t)(t0 + est) * nf + efi;
+            dst[m] = out + (int64_t)(t0 + tt) * nf + i;
         }
         // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
         // ceil((S0 + j0 D + max(0, (R-1) D)) / 2^32) (+ the tile's terms), kept
@@ -557,18 +561,18 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
                 for (int m = 0; m < M; ++m) {
                     if (!ok[m]) continue;
                     const int xl = ul + blo[m], xh = wh + bhi[m];
-                    int a = qa[m], b = qb[m];
+                    int qa_m = qa[m], qb_m = qb[m];
                     if (slab == 0) {
-                        a = lower_bound_cell_g(Ai, n, xl);
-                        b = lower_bound_cell_g(Ai, n, xh);
+                        qa_m = lower_bound_cell_g(Ai, n, xl);
+                        qb_m = lower_bound_cell_g(Ai, n, xh);
                     } else {
-                        while (a < n && global_cell(Ai, a) < xl) ++a;
-                        while (a > 0 && global_cell(Ai, a - 1) >= xl) --a;
-                        while (b < n && global_cell(Ai, b) < xh) ++b;
-                        while (b > 0 && global_cell(Ai, b - 1) >= xh) --b;
+                        while (qa_m < n && global_cell(Ai, qa_m) < xl) ++qa_m;
+                        while (qa_m > 0 && global_cell(Ai, qa_m - 1) >= xl) --qa_m;
+                        while (qb_m < n && global_cell(Ai, qb_m) < xh) ++qb_m;
+                        while (qb_m > 0 && global_cell(Ai, qb_m - 1) >= xh) --qb_m;
                     }
-                    qa[m] = a;
-                    qb[m] = b;
+                    qa[m] = qa_m;
+                    qb[m] = qb_m;
                 }
             } else if (slab == 0) {
                 // every lane searches (the sentinels bound the tiles past the last one)
@@ -591,22 +595,13 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
                 }
             }
 #pragma unroll
-            for (int m = 0; m < M; ++m)
-                if (ok[m])
-                    stage[slab & 1][f][lane + 32 * m] =
-                        make_int2((int)(o0 + qa[m]), (int)(o0 + max(qa[m], qb[m])));
-            u += 32 * dv;
-            w += 32 * dv;
-            // this slab's entries are complete; the buffer is written again two
-            // slabs later, after the next barrier
-            __syncthreads();
-#pragma unroll
             for (int m = 0; m < M; ++m) {
-                if (dst_ok[m]) *dst[m] = stage[slab & 1][threadIdx.x & 7][(threadIdx.x >> 3) + 32 * m];
+                if (ok[m]) *dst[m] = make_int2((int)(o0 + qa[m]), (int)(o0 + max(qa[m], qb[m])));
                 dst[m] += slab_stride;
             }
+            u += 32 * dv;
+            w += 32 * dv;
         }
-        __syncthreads();  // the next pass of tiles reuses both buffers
     }
 }
 
