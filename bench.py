@@ -812,6 +812,9 @@ def run_reference(args):
     import oracle
     from paper_1407_8333_gb300 import synth
     oracle.build()
+    if world > 1:
+        # torchrun gives every worker one OpenMP thread; only this rank works here
+        oracle.set_num_threads(os.cpu_count() or 1)
     w = synth.WORKLOADS[args.workload]
     inp = synth.make_inputs(w)
     pp = w.plan_params()
