@@ -104,6 +104,7 @@ CASES = [
     (4, 9, 31, 1, 5, 4, 32, 16),          # K = 1
     (5, 40, 128, 10, 70, 1, 0, 0),        # library default tile (single tile)
     (6, 64, 200, 7, 64, 2, 160, 8),
+    (7, 14, 340, 10, 40, 2, 32, 8),       # 107 tiles: two passes of the window pre-pass
 ]
 
 
