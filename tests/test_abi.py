@@ -86,6 +86,20 @@ def test_invalid_plan_is_rejected_without_gpu(lib):
         fh.fh_create_plan(fh.make_desc(pp, 10, 1, 100))
 
 
+def test_selection_workspace_size(lib):
+    """fh_peakmap_select_workspace covers a bit per bin and a count per
+    4096-bin segment of every FFT, grows with both sizes, and refuses
+    negative sizes, without a GPU."""
+    f = lib.fh_peakmap_select_workspace
+    for n_fft, n_bins in ((1, 1), (3164, 8192), (100, 4097), (65535, 33)):
+        ws = f(n_fft, n_bins)
+        bits = n_fft * -(-n_bins // 32) * 4
+        counts = n_fft * -(-n_bins // 4096) * 4
+        assert ws >= bits + counts
+        assert f(n_fft + 1, n_bins) >= ws and f(n_fft, n_bins + 4096) >= ws
+    assert f(-1, 10) == -1 and f(10, -1) == -1
+
+
 def test_device_only_outputs_refuse_host_buffers():
     """fh_copy_profile enqueues an asynchronous device-to-device copy: a host
     array is refused before the library is called."""
