@@ -16,7 +16,7 @@ buffers, the roofline of the transform kernel, the oracle's CPU baseline,
 SM clocks sampled during the timed region, the plain vs batched comparison
 on a 256-direction sky patch and the served-stream latency figures.
 
-``--impl reference`` times the CPU oracle (the reference arm of this build)
+``--impl reference`` times the CPU oracle (the benchmark's reference arm)
 on the same workload instead.
 """
 from __future__ import annotations
