@@ -205,10 +205,16 @@ int fh_transform(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *out_ma
  * maps, profiles, candidate counts and n_thr are in units of 2^-F, and the
  * critical ratio becomes (n - S1 p0) / sqrt((S2 p0)(1 - p0)), S1 and S2 the
  * direction's sums of W and of W^2 (for unit weights S1 = S2 = N: Eq. cr).
- * The weights are checked and quantised on the host and their copy to the
- * device is enqueued on stream.  Errors: FH_ERR_INVALID_ARG (bad weight,
- * wrong n_dir, no peakmap), FH_ERR_RANGE (a weight or a direction's sum
- * reaching 2^30). */
+ * The weights are checked and quantised on the host and copied to the
+ * device on stream; then the call computes, on the device, a bound of every
+ * count of each direction, sum_i W_i c_i with c_i the most positions of FFT i
+ * inside a half-open window of K cells (two stripes of one FFT share a cell
+ * only if their positions are less than K cells apart), and synchronises the
+ * stream to check it.  Errors: FH_ERR_INVALID_ARG (bad weight, wrong n_dir,
+ * no peakmap), FH_ERR_RANGE (a weight or a direction's sum reaching 2^30, or
+ * a direction's count bound reaching 2^31: dense off-grid peaks of one FFT
+ * under large weights), or the error of the last correction's device-side
+ * input checks (its positions are then not trusted). */
 int fh_set_weights(fh_plan plan, const double *w, int32_t n_dir, int32_t frac_bits,
                    void *stream);
 
@@ -243,9 +249,17 @@ int fh_select_candidates(fh_plan plan, int32_t dir_begin, int32_t n_dir, fh_cand
  * FH_ERR_UNSORTED, FH_ERR_INVALID_ARG) since the last fh_correct_doppler. */
 int fh_sync(fh_plan plan, void *stream);
 
-/* Time fh_transform over tile widths (and block sizes) on the current
- * directions and keep the fastest in the plan; returns it in *tile_cells.
- * Synchronises.  Results are cached per process by grid shape. */
+/* Time fh_transform over its launch shapes on the current directions (at most
+ * 8 of them: the per-item work does not depend on the count) and keep the
+ * fastest in the plan; returns its tile width and block warps.  The shapes
+ * are: rows per slab (64 with two 16-bit counts per shared word, where the
+ * plain START map allows it, and 32), block warps (16, 24, 32) and tile
+ * widths up to the widest that fits shared memory with that slab's guard
+ * cells.  Synchronises.  Results are cached per process by grid shape (GPU
+ * model, counting mode, weighting, n_f0, n_fdot, K, T_FFT, N_t, n_dir); when
+ * the environment variable FH_AUTOTUNE_CACHE names a file, they are also
+ * read from and written to it (JSON, one entry per line), so later processes
+ * reuse them without timing. */
 int fh_autotune(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells,
                 int32_t *block_warps, void *stream);
 
@@ -441,10 +455,16 @@ int fh_refine(fh_plan plan, const fh_peakmap *pm, const double *v_over_c,
  *   device_status nullable device int32: receives the device-side input
  *                 checks (0 = inputs valid) when the enqueued work completes
  * The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call
- * reuses the same array, so calls whose work overlaps on the GPU (different
- * streams, or different host threads) race: serialise them, e.g. on one
- * stream.  Calls only enqueue work; nothing is allocated, nothing is freed. */
+ * device current) and caches it for the life of the process, which assumes the
+ * device's primary context lives as long: after cudaDeviceReset the cached
+ * address is stale.  Under the CUDA runtime's default lazy module loading that
+ * first lookup is also when the driver loads the array, taking its 19.5 MiB of
+ * device memory then: make the first call before reserving the rest of the
+ * GPU for a pool of your own, and before any stream capture.  Every later call
+ * takes no device memory.  Every call reuses the same array, so calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race: serialise them, e.g. on one stream.  Calls only enqueue work; nothing
+ * is allocated, nothing is freed. */
 int fh_search_static(const fh_plan_desc *desc, const fh_peakmap *pm, const double *v_over_c,
                      const double *sky_n, fh_candidate *out, int64_t capacity, int64_t *n_out,
                      int32_t *device_status, void *stream);
@@ -517,6 +537,13 @@ int fh_server_pause(fh_server server, int32_t paused);
  * *atomics_per_s = lane-atomics per second over the whole GPU. */
 int fh_bench_smem_atomics(int32_t variant, int32_t iters, double *atomics_per_s,
                           double *ms, void *stream);
+
+/* Binary64 throughput of this GPU: every SM runs blocks of 512 threads, each
+ * with 8 independent chains of one IEEE multiply and one IEEE add per step
+ * (round to nearest, never fused: the operations the Doppler correction and
+ * positions use, Eq. fdopp).  Synchronises.  *ops_per_s = binary64
+ * operations per second over the whole GPU. */
+int fh_bench_fp64(int32_t iters, double *ops_per_s, double *ms, void *stream);
 
 /* ---- misc -------------------------------------------------------------- */
 const char *fh_last_error(void);

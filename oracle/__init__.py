@@ -170,10 +170,46 @@ def hough_map_direct(offsets, A_dir, S0, D, k_over: int, n_f0: int, n_fdot: int,
     return m
 
 
-# A cell receives at most two stripes from one FFT (neighbouring peaks of an
-# FFT lie at least 0.9 K cells apart once |v.n| < 0.1), so a weighted count is
-# at most 2 sum(W): sums below 2^30 keep every count inside int32.
+# Each direction's quantised weights sum below 2^30 (a cell of a bin-grid
+# peakmap takes at most two stripes of one FFT, so its weighted counts stay
+# below 2^31).  Off-grid peakmaps can put more stripes of one FFT on a cell;
+# ``count_bound`` bounds every count of any peakmap and ``search`` refuses
+# weights whose bound reaches 2^31.
 WEIGHT_SUM_LIMIT = (1 << 30) - 1
+COUNT_LIMIT = 1 << 31
+
+
+def stripe_overlap(offsets, A_dir, k_over: int) -> np.ndarray:
+    """Per FFT, the largest number of its stripes that can cover one cell on
+    any row: the most of its positions inside a half-open window of K cells.
+
+    Two stripes of one FFT (Eq. due: K cells from s = floor((A - shift)/2^32))
+    share a cell only if s_q - s_p <= K - 1, which forces A_q - A_p < K 2^32;
+    so the stripes on a common cell have positions within less than K cells
+    of the smallest, whatever the row.  (For a bin-grid peakmap this is 1 or
+    2; dense off-grid peaks give more.)"""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    A_dir = np.asarray(A_dir, dtype=np.int64)
+    width = int(k_over) << 32
+    n_fft = offsets.shape[0] - 1
+    c = np.zeros(n_fft, dtype=np.int64)
+    for i in range(n_fft):
+        a = A_dir[int(offsets[i]):int(offsets[i + 1])]
+        if a.shape[0] == 0:
+            continue
+        # for each peak p, the first q with A_q >= A_p + K 2^32 (positions ascending)
+        q = np.searchsorted(a, a + width, side="left")
+        c[i] = int((q - np.arange(a.shape[0])).max())
+    return c
+
+
+def count_bound(offsets, A_dir, k_over: int, W=None) -> int:
+    """An upper bound of every count of one direction's map (Eq. ncountadap):
+    sum over FFTs of its weight (1 for the plain map) times stripe_overlap."""
+    c = stripe_overlap(offsets, A_dir, k_over)
+    if W is None:
+        return int(c.sum())
+    return int(sum(int(w) * int(x) for w, x in zip(np.asarray(W).ravel(), c)))
 
 
 def quantize_weights(w, frac_bits: int) -> np.ndarray:
@@ -262,6 +298,10 @@ def search(inp, params: dict, want_maps: bool = False, dirs=None, weights=None,
     if weights is not None:
         W = quantize_weights(np.asarray(weights, dtype=np.float64).reshape(sky.shape[0], -1),
                              frac_bits)
+        for d in range(sky.shape[0]):
+            if count_bound(inp.offsets, A[d], params["k_over"], W[d]) >= COUNT_LIMIT:
+                raise ValueError("direction %d: weighted counts could reach 2^31 (dense peaks "
+                                 "of one FFT under large weights)" % d)
         out["W"] = W
         out["s1"] = W.sum(axis=1)
         out["s2"] = (W * W).sum(axis=1)

@@ -11,7 +11,10 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <string>
 #include <vector>
+
+#include <unistd.h>
 
 #include "fh_internal.h"
 
@@ -106,21 +109,38 @@ int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nw
     return w;
 }
 
-int32_t default_guard(const fh_plan_desc &d)
+unsigned long long default_drift(const fh_plan_desc &d)
 {
     const double cells = 0.5 * d.k_over + 0.25;
-    return guard_for((unsigned long long)(cells * 4294967296.0));
+    return (unsigned long long)(cells * 4294967296.0);
 }
 
-// guard for host-memory FFT times: the largest |D_i| in 32.32 cells per row
-int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft)
+int32_t default_guard(const fh_plan_desc &d) { return guard_for(default_drift(d)); }
+
+// the largest |D_i| in 32.32 cells per row, from host-memory FFT times
+unsigned long long host_drift(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft)
 {
     double m = 0.0;
     for (int32_t i = 0; i < n_fft; ++i) {
         const double x = std::fabs(d.fdot_step * ((t[i] - d.t_ref) * kt));
         if (x > m && x < 1e9) m = x;  // non-finite or absurd times are left to the checks
     }
-    return guard_for((unsigned long long)(m * 4294967296.0) + 4);
+    return (unsigned long long)(m * 4294967296.0) + 4;
+}
+
+int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft)
+{
+    return guard_for(host_drift(d, kt, t, n_fft));
+}
+
+int32_t packed_slab_rows(const fh_plan_desc &d, int device, int32_t n_fft, unsigned long long drift)
+{
+    if (n_fft <= 0 || n_fft >= 65536 || (int64_t)d.k_over * n_fft >= ((int64_t)1 << 25))
+        return kRows;
+    const int32_t g64 = guard_for(drift, 2 * kRows - 1);
+    if (transform_smem_bytes(256, d.k_over, FH_MODE_START, 32, g64) > (size_t)max_optin_smem(device))
+        return kRows;
+    return 2 * kRows;
 }
 
 int validate_desc(const fh_plan_desc &d)
@@ -206,9 +226,13 @@ struct fh_plan_s {
     int32_t *err = nullptr;
     int32_t *h_err = nullptr;  // pinned
     unsigned long long *dmax = nullptr;  // largest |D_i| of the current peakmap (in err's block)
+    int32_t *dense = nullptr;            // set by the window pre-pass: an FFT with two peaks
+                                         // in one cell (in err's block)
     int2 *win = nullptr;                 // peak windows of the directions being transformed
     size_t win_bytes = 0;
-    int32_t guard = 0;                   // guard cells for the transform's fast path
+    int32_t guard = 0;                   // guard cells for the transform's fast path (32 rows)
+    unsigned long long drift = 0;        // bound of max |D_i| the guards are sized for
+    int32_t slab_pref = 0;               // 0: packed 64-row slabs where they apply; 32: never
     int32_t n_fft = -1;
     int64_t n_peaks = 0;
     int32_t n_dir = 0;
@@ -219,7 +243,7 @@ struct fh_plan_s {
     int32_t *wq = nullptr;
     int64_t *ws = nullptr;       // [2][max_dir]: S1 then S2
     bool weighted = false;
-    int64_t w_bound = 0;         // 2 max S1: no weighted count exceeds it
+    int64_t w_bound = 0;         // largest count bound over the directions (fh_set_weights)
     // optional kernel timing: per direction group of fh_transform, events before
     // the window pre-pass, between it and the transform, after the transform
     int32_t timing = 0;
@@ -413,6 +437,7 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
     p->n_sb = (desc->n_f0 + desc->subband_cells - 1) / desc->subband_cells;
     p->mode = desc->mode == FH_MODE_AUTO ? FH_MODE_START : desc->mode;
     p->block_warps = desc->block_warps ? desc->block_warps : 32;
+    p->drift = default_drift(*desc);
     p->guard = default_guard(*desc);
     p->tile_cells = desc->tile_cells ? std::min(desc->tile_cells, desc->n_f0)
                                      : default_tile(*desc, p->device, p->mode, p->block_warps,
@@ -443,8 +468,10 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                              (long long)a.bytes, cudaGetErrorString(e));
         }
     }
-    // the largest |D| lives in the error word's allocation, 16 bytes in
+    // the largest |D| lives in the error word's allocation, 16 bytes in, and
+    // the window pre-pass's dense-FFT flag 24 bytes in
     p->dmax = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(p->err) + 16);
+    p->dense = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(p->err) + 24);
     e = cudaMallocHost(&p->h_err, 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -523,8 +550,10 @@ int fh_set_weights(fh_plan p, const double *w, int32_t n_dir, int32_t frac_bits,
     const fh_plan_desc &d = p->d;
     // quantise on the host: W = rint(w 2^F) (binary64, ties to even; the product
     // by a power of two is exact), every weight finite and >= 0, and each
-    // direction's sum below 2^30 (a cell takes at most two stripes of one FFT,
-    // so every count stays inside int32)
+    // direction's sum below 2^30 (a cell of a bin-grid peakmap takes at most
+    // two stripes of one FFT); then the exact count bound of this peakmap,
+    // sum_i W_i c_i with c_i the most stripes of FFT i on one cell (from the
+    // positions), must stay below 2^31
     const double scale = std::ldexp(1.0, frac_bits);
     std::vector<int32_t> W((size_t)n_dir * (size_t)std::max(1, n));
     std::vector<int64_t> sums(2 * (size_t)d.max_dir, 0);
@@ -555,7 +584,8 @@ int fh_set_weights(fh_plan p, const double *w, int32_t n_dir, int32_t frac_bits,
     cudaError_t e = cudaSuccess;
     if (!p->wq) {
         e = cudaMalloc(&p->wq, sizeof(int32_t) * (size_t)d.max_dir * (size_t)std::max(1, d.max_fft));
-        if (e == cudaSuccess) e = cudaMalloc(&p->ws, sizeof(int64_t) * 2 * (size_t)d.max_dir);
+        // S1, S2 and the count bound per direction
+        if (e == cudaSuccess) e = cudaMalloc(&p->ws, sizeof(int64_t) * 3 * (size_t)d.max_dir);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_error(FH_ERR_NOMEM, "cudaMalloc (weights) failed");
@@ -569,8 +599,34 @@ int fh_set_weights(fh_plan p, const double *w, int32_t n_dir, int32_t frac_bits,
         e = cudaMemcpyAsync(p->ws, sums.data(), sizeof(int64_t) * sums.size(),
                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(weights)");
+    // the count bound of every direction from its positions (synchronises)
+    unsigned long long *bound = reinterpret_cast<unsigned long long *>(p->ws + 2 * d.max_dir);
+    e = cudaMemsetAsync(bound, 0, sizeof(unsigned long long) * (size_t)n_dir, s);
+    if (e == cudaSuccess)
+        e = launch_weight_bound(p->A, p->offsets, p->wq, n, n_dir, p->n_peaks, d.k_over, bound, s);
+    std::vector<unsigned long long> hb((size_t)std::max(1, n_dir), 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb.data(), bound, sizeof(unsigned long long) * (size_t)n_dir,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->h_err, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "weight count bound");
+    // an input rejected by the device checks is reported as such (its
+    // positions are not trusted, so neither is their bound)
+    int rc = device_error_code(*p->h_err);
+    if (rc) return rc;
+    unsigned long long bmax = 0;
+    for (int32_t k = 0; k < n_dir; ++k) {
+        if (hb[k] >= (1ull << 31))
+            return set_error(FH_ERR_RANGE,
+                             "direction %d: weighted counts could reach 2^31 (bound %llu: "
+                             "dense peaks of one FFT under large weights)", k, hb[k]);
+        bmax = std::max(bmax, hb[k]);
+    }
+    (void)smax;
     p->weighted = true;
-    p->w_bound = 2 * smax;
+    p->w_bound = (int64_t)bmax;
     return FH_OK;
 }
 
@@ -687,11 +743,12 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
         // the guard from the FFT times (the device checks of FH_CHECKS_DEVICE see the
         // rest); one that would not leave room for a tile falls back to the plan's
         // default, and the transform then takes its clamped walk if the drift is larger
-        int32_t gd = std::max(default_guard(p->d), host_guard(p->d, p->kt, pm->t_fft, n));
-        if (transform_smem_bytes(64, p->d.k_over, p->mode, p->block_warps, gd) >
+        unsigned long long dr = std::max(default_drift(p->d), host_drift(p->d, p->kt, pm->t_fft, n));
+        if (transform_smem_bytes(64, p->d.k_over, p->mode, p->block_warps, guard_for(dr)) >
             (size_t)max_optin_smem(p->device))
-            gd = default_guard(p->d);
-        p->guard = gd;
+            dr = default_drift(p->d);
+        p->drift = dr;
+        p->guard = guard_for(dr);
         t_src = t_m ? static_cast<const double *>(t_m) : p->t;
         f_src = f_m ? static_cast<const double *>(f_m) : p->freq;
         v_src = v_m ? static_cast<const double *>(v_m) : p->v;
@@ -700,6 +757,9 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     } else {
         if (!pm->offsets || (n > 0 && !pm->t_fft) || (np > 0 && !pm->freq))
             return set_error(FH_ERR_INVALID_ARG, "null device peakmap array");
+        // the FFT times are not seen on the host: the guards of the grid's own drift
+        p->drift = default_drift(p->d);
+        p->guard = default_guard(p->d);
         t_src = pm->t_fft;
         f_src = pm->freq;
         v_src = v_over_c;
@@ -745,12 +805,30 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     return FH_OK;
 }
 
+// Rows per slab for the plan's current peakmap: 64 (packed 16-bit counters)
+// for a plain START map whose stripe-start counts fit 16 bits by its size
+// (n_fft < 2^16; the window pre-pass checks the spacing of the peaks) and
+// whose counts keep the packed reduction key below 2^31 (K n_fft < 2^25), when
+// a tile still fits shared memory with the 63-row guard; else 32.
+static int32_t plan_slab_rows(fh_plan p, int32_t pref)
+{
+    if (pref == kRows || p->mode != FH_MODE_START || p->weighted) return kRows;
+    return packed_slab_rows(p->d, p->device, p->n_fft, p->drift);
+}
+
+static int32_t plan_guard(fh_plan p, int32_t rows)
+{
+    return rows == 2 * kRows ? guard_for(p->drift, 2 * kRows - 1) : p->guard;
+}
+
 static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
-                         int32_t tile, int32_t nwarps, int32_t schedule, cudaStream_t s)
+                         int32_t tile, int32_t nwarps, int32_t schedule, cudaStream_t s,
+                         int32_t slab_pref)
 {
     const fh_plan_desc &d = p->d;
     // keep the tile's counters within shared memory with this plan's guard cells
-    const int32_t guard = p->guard;
+    const int32_t rows = plan_slab_rows(p, slab_pref);
+    const int32_t guard = plan_guard(p, rows);
     const int32_t wmax = default_tile(d, p->device, p->mode, nwarps, guard);
     if (tile > wmax) tile = wmax;
     const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps, guard);
@@ -779,7 +857,9 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.n_fdot = d.n_fdot;
     job.k_over = d.k_over;
     job.tile_cells = tile;
-    job.n_slabs = (d.n_fdot + kRows - 1) / kRows;
+    job.slab_rows = rows;
+    job.dense = p->dense;
+    job.n_slabs = (d.n_fdot + rows - 1) / rows;
     job.n_tiles = (d.n_f0 + tile - 1) / tile;
     const int64_t per_dir = (int64_t)job.n_slabs * job.n_tiles;
     int bps = transform_blocks_per_sm(p->mode, nwarps, smem);
@@ -849,7 +929,7 @@ int fh_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
     if (rc) return rc;
     DeviceGuard g(p->device);
     return run_transform(p, dir_begin, n_dir, out_maps, p->tile_cells, p->block_warps,
-                         p->d.schedule, as_stream(stream));
+                         p->d.schedule, as_stream(stream), p->slab_pref);
 }
 
 int fh_copy_profile(fh_plan p, int32_t dir_begin, int32_t n_dir, uint64_t *out, void *stream)
@@ -921,6 +1001,82 @@ int fh_select_candidates(fh_plan p, int32_t dir_begin, int32_t n_dir, fh_candida
     return fh_sync(p, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Autotuner results: (tile width, block warps, rows per slab) per grid shape,
+// kept in memory for the process and, when FH_AUTOTUNE_CACHE names a file, in
+// that JSON file (one entry per line, rewritten atomically by rename) so that
+// later processes on the same GPU model reuse them.
+struct TuneChoice {
+    int32_t tile = 0, warps = 0, rows = 0;
+    double ms = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+const char *tune_path() { return std::getenv("FH_AUTOTUNE_CACHE"); }
+
+void tune_load_locked()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = tune_path();
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+        const char *k = std::strstr(line, "\"key\": \"");
+        if (!k) continue;
+        k += 8;
+        const char *ke = std::strchr(k, '"');
+        if (!ke) continue;
+        TuneChoice c;
+        const char *t = std::strstr(ke, "\"tile_cells\": ");
+        const char *w = std::strstr(ke, "\"block_warps\": ");
+        const char *r = std::strstr(ke, "\"slab_rows\": ");
+        const char *m = std::strstr(ke, "\"ms\": ");
+        if (!t || !w || !r || std::sscanf(t + 14, "%d", &c.tile) != 1 ||
+            std::sscanf(w + 15, "%d", &c.warps) != 1 || std::sscanf(r + 13, "%d", &c.rows) != 1)
+            continue;
+        if (m) std::sscanf(m + 6, "%lf", &c.ms);
+        if (c.tile < 32 || (c.warps != 16 && c.warps != 24 && c.warps != 32) ||
+            (c.rows != kRows && c.rows != 2 * kRows))
+            continue;  // not one of ours: ignored
+        g_tune[std::string(k, ke)] = c;
+    }
+    std::fclose(f);
+}
+
+void tune_store_locked()
+{
+    const char *path = tune_path();
+    if (!path || !*path) return;
+    const std::string tmp = std::string(path) + ".tmp." + std::to_string((long long)getpid());
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\"version\": 1, \"entries\": [\n");
+    size_t k = 0;
+    for (const auto &e : g_tune) {
+        std::fprintf(f,
+                     "{\"key\": \"%s\", \"tile_cells\": %d, \"block_warps\": %d, "
+                     "\"slab_rows\": %d, \"ms\": %.6f}%s\n",
+                     e.first.c_str(), e.second.tile, e.second.warps, e.second.rows, e.second.ms,
+                     ++k < g_tune.size() ? "," : "");
+    }
+    std::fprintf(f, "]}\n");
+    const bool ok = std::fclose(f) == 0;
+    if (ok) std::rename(tmp.c_str(), path);
+    else std::remove(tmp.c_str());
+}
+
+}  // namespace
+
+extern "C" {
+
 int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells,
                 int32_t *block_warps, void *stream)
 {
@@ -929,52 +1085,84 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     if (rc) return rc;
     DeviceGuard g(p->device);
     cudaStream_t s = as_stream(stream);
-    static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int64_t, int, int, int>, std::pair<int, int>> cache;
     const fh_plan_desc &d = p->d;
-    const auto key = std::make_tuple(d.n_f0, d.n_fdot, d.k_over, p->n_fft, p->n_peaks / 4096,
-                                     n_dir, p->mode, p->device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) {
+        cudaGetLastError();
+        std::strcpy(prop.name, "gpu");
+    }
+    for (char *c = prop.name; *c; ++c)
+        if (*c == '"' || *c == '\\' || *c == ' ') *c = '_';
+    // the grid shape: (n_f0, n_fdot, K, T_FFT, N_t, n_dir), with the counting
+    // mode, the weighting and the GPU model
+    char key[512];
+    std::snprintf(key, sizeof key, "%s|mode%d|w%d|n_f0=%d|n_fdot=%d|K=%d|T=%.17g|n_fft=%d|n_dir=%d",
+                  prop.name, p->mode, p->weighted ? 1 : 0, d.n_f0, d.n_fdot, d.k_over, d.t_fft,
+                  p->n_fft, n_dir);
+    auto apply = [&](const TuneChoice &c) {
+        p->tile_cells = c.tile;
+        p->block_warps = c.warps;
+        p->slab_pref = c.rows;
+        if (tile_cells) *tile_cells = p->tile_cells;
+        if (block_warps) *block_warps = p->block_warps;
+    };
     {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            p->tile_cells = it->second.first;
-            p->block_warps = it->second.second;
-            if (tile_cells) *tile_cells = p->tile_cells;
-            if (block_warps) *block_warps = p->block_warps;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            apply(it->second);
             return FH_OK;
         }
     }
+    // candidates: rows per slab (packed 64 where it applies, 32), block warps,
+    // tile widths up to the widest that fits with that slab's guard cells
     const int lim = max_optin_smem(p->device);
-    std::vector<std::pair<int, int>> cands;
-    for (int nw : {32, 24, 16}) {
-        if (nw == 24 && p->mode == FH_MODE_DIFF) continue;  // DIFF kernels: 512 / 1024 threads
-        const int32_t wmax = default_tile(d, p->device, p->mode, nw, p->guard);
-        for (int32_t w : {wmax, 1536, 1280, 1024, 768, 512}) {
-            if (w > wmax || w > d.n_f0) continue;
-            if (transform_smem_bytes(w, d.k_over, p->mode, nw, p->guard) > (size_t)lim) continue;
-            if (std::find(cands.begin(), cands.end(), std::make_pair((int)w, nw)) == cands.end())
-                cands.push_back({w, nw});
+    std::vector<TuneChoice> cands;
+    const int32_t rows_auto = plan_slab_rows(p, 0);
+    for (int32_t rows : {rows_auto, (int32_t)kRows}) {
+        if (rows == kRows && rows_auto == kRows && !cands.empty()) break;
+        const int32_t guard = plan_guard(p, rows);
+        for (int nw : {24, 32, 16}) {
+            if (nw == 24 && p->mode == FH_MODE_DIFF) continue;  // DIFF kernels: 512 / 1024 threads
+            const int32_t wmax = default_tile(d, p->device, p->mode, nw, guard);
+            for (int32_t w : {wmax, 1280, 1024, 768}) {
+                if (w > wmax || w > d.n_f0) continue;
+                if (transform_smem_bytes(w, d.k_over, p->mode, nw, guard) > (size_t)lim) continue;
+                bool dup = false;
+                for (const auto &c : cands) dup = dup || (c.tile == w && c.warps == nw && c.rows == rows);
+                if (!dup) cands.push_back({w, nw, rows, 0.0});
+            }
         }
     }
-    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps});
+    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps, kRows, 0.0});
+    // timed on at most 8 of the directions (one window group): the per-item
+    // work, and so the best tile, does not depend on how many there are
+    const int32_t nt = std::min<int32_t>(n_dir, 8);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    std::pair<int, int> pick = cands[0];
+    TuneChoice pick = cands[0];
     for (auto &c : cands) {
-        rc = run_transform(p, dir_begin, n_dir, nullptr, c.first, c.second, FH_SCHED_BATCHED, s);
+        const int32_t pref = c.rows == kRows ? kRows : 0;
+        rc = run_transform(p, dir_begin, nt, nullptr, c.tile, c.warps, FH_SCHED_BATCHED, s, pref);
         if (rc) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 2 && rc == FH_OK; ++r)
-            rc = run_transform(p, dir_begin, n_dir, nullptr, c.first, c.second, FH_SCHED_BATCHED, s);
-        cudaEventRecord(e1, s);
-        if (rc) break;
-        cudaEventSynchronize(e1);
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
+        for (int reps = 1; reps <= 4 && rc == FH_OK; reps *= 4) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == FH_OK; ++r)
+                rc = run_transform(p, dir_begin, nt, nullptr, c.tile, c.warps, FH_SCHED_BATCHED,
+                                   s, pref);
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms > 5.0f) break;  // long enough to time once
+        }
+        c.ms = ms;
+        if (rc == FH_OK && ms < best) {
             best = ms;
             pick = c;
         }
@@ -982,14 +1170,42 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    p->tile_cells = pick.first;
-    p->block_warps = pick.second;
+    apply(pick);
     {
-        std::lock_guard<std::mutex> lk(mu);
-        cache[key] = pick;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = pick;
+        tune_store_locked();
     }
-    if (tile_cells) *tile_cells = p->tile_cells;
-    if (block_warps) *block_warps = p->block_warps;
+    return FH_OK;
+}
+
+int fh_bench_fp64(int32_t iters, double *ops_per_s, double *ms, void *stream)
+{
+    if (!ops_per_s || iters < 1) return set_error(FH_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = as_stream(stream);
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    double *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(double));
+    if (e != cudaSuccess) return set_error(FH_ERR_NOMEM, "cudaMalloc(sink)");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int grid = n_sm * 4;  // 4 blocks of 512 threads per SM
+    e = launch_fp64_bench(std::max(1, iters / 8), grid, sink, s);  // warm-up
+    cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_fp64_bench(iters, grid, sink, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_error(e, "fp64 bench");
+    *ops_per_s = (double)grid * 512.0 * 16.0 * (double)iters / ((double)t * 1e-3);
+    if (ms) *ms = t;
     return FH_OK;
 }
 

@@ -39,6 +39,11 @@ struct TransformJob {
     int64_t count_bound;     // no count of the job's maps exceeds it
     const int2 *windows;     // nullable: precomputed peak windows (first, end) per
                              // [dir - dir_begin][slab][tile][fft]; else looked up
+    int32_t *dense;          // nullable: set by the window pre-pass when some FFT has two
+                             // peaks within one cell (the packed counters then do not
+                             // apply: the job's 64-row slabs run as two 32-row passes)
+    int32_t slab_rows;       // rows per slab: 32 (0 means 32), or 64 for the packed
+                             // layout (plain START map: every job of a launch alike)
     int64_t n_peaks;
     int64_t item_begin;      // first work item of this job in the launch
     int64_t n_items;         // n_dir * n_slabs * n_tiles
@@ -110,10 +115,11 @@ cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
                                           const double *sky, int32_t n_fft, int32_t n_dir,
                                           int32_t *err, cudaStream_t s);
 // Guard cells kept below and above a tile so that, in the fast path, no
-// update of a slab needs a bounds clamp: enough for a drift of 31 rows x
-// max|D| cells.  guard_for(dmax) is what a job needs; a launch allocates one
-// guard for all its jobs and jobs needing more take the clamped path.
-__host__ __device__ int32_t guard_for(unsigned long long dmax);
+// update of a slab needs a bounds clamp: enough for a drift of span_rows (the
+// slab's rows - 1) x max|D| cells.  guard_for(dmax, rows - 1) is what a job
+// needs; a launch allocates one guard for all its jobs and jobs needing more
+// take the clamped path.
+__host__ __device__ int32_t guard_for(unsigned long long dmax, int32_t span_rows = kRows - 1);
 // smem bytes the transform needs for tile width W (and mode)
 size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, int32_t nwarps,
                             int32_t guard);
@@ -126,6 +132,15 @@ int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem);
 // job.windows (the job's other fields as for the transform).
 cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, cudaStream_t s);
+// Adaptive map's count bound: bound[d] += sum_i W[d][i] c_{d,i}, c_{d,i} = the
+// most positions of FFT i (direction d) inside a half-open window of K cells
+// (bound: n_dir words, zeroed by the caller).
+cudaError_t launch_weight_bound(const int64_t *A, const int64_t *offsets, const int32_t *W,
+                                int32_t n_fft, int32_t n_dir, int64_t n_peaks, int32_t k_over,
+                                unsigned long long *bound, cudaStream_t s);
+// binary64 multiply + add chains, grid blocks of 512 threads, 16 operations
+// per thread per iteration
+cudaError_t launch_fp64_bench(int32_t iters, int32_t grid, double *sink, cudaStream_t s);
 cudaError_t launch_smem_atomic_bench(int32_t variant, int32_t iters, int32_t grid,
                                      unsigned long long *sink, cudaStream_t s);
 
@@ -168,6 +183,16 @@ int32_t default_tile(const fh_plan_desc &d, int device, int32_t mode, int32_t nw
 int32_t default_guard(const fh_plan_desc &d);
 // guard for FFT start times held in host memory (exact drift of the grid)
 int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft);
+// the drift bounds behind those guards: max |D_i| in 32.32 cells per row
+unsigned long long default_drift(const fh_plan_desc &d);
+unsigned long long host_drift(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft);
+// Rows per slab of a plain START map: 64 (packed 16-bit counters) when its
+// stripe-start counts fit 16 bits by its size (n_fft < 2^16; the window
+// pre-pass checks the peaks' spacing), its counts keep the packed reduction
+// key below 2^31 (K n_fft < 2^25) and a tile fits with the 63-row guard of
+// drift bound `drift`; else 32.
+int32_t packed_slab_rows(const fh_plan_desc &d, int device, int32_t n_fft,
+                         unsigned long long drift);
 int validate_desc(const fh_plan_desc &d);
 // host-memory inputs: CSR, ordering, finiteness and the 32.32 fixed-point range
 int validate_host_inputs(const fh_plan_desc &d, double kt, const fh_peakmap *pm, const double *v,

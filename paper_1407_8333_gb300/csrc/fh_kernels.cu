@@ -490,19 +490,34 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
             pr[k] = 0;
     }
     {
-        // warp w stages FFT w of the block
+        // warp w stages FFT w of the block; with J.dense it also flags two
+        // consecutive peaks whose cells differ by at most 1 (positions less
+        // than one cell apart imply that), which the packed transform's 16-bit
+        // counters cannot take
         const int is = blockIdx.x * 8 + warp;
         const bool ls = is < J.n_fft;
         const int64_t os = ls ? J.offsets[is] : 0;
         const int ns = ls ? (int)(J.offsets[is + 1] - os) : 0;
-        if (ns + 2 * kWinPad <= kWinPeaks) {
-            int32_t *c = &cell_s[warp][kWinPad];
-            const int64_t *As = Ad + os;
-            for (int k = lane; k < ns; k += 32) c[k] = global_cell(As, k);
-            if (lane < kWinPad) {
-                c[-1 - lane] = INT_MIN;
-                c[ns + lane] = INT_MAX;
+        const bool stage = ns + 2 * kWinPad <= kWinPeaks;
+        int32_t *c = &cell_s[warp][kWinPad];
+        const int64_t *As = Ad + os;
+        if (stage || J.dense != nullptr) {
+            bool close = false;
+            int carry = 0;
+            for (int k0 = 0; k0 < ns; k0 += 32) {
+                const int k = k0 + lane;
+                const int cur = k < ns ? global_cell(As, k) : 0;
+                if (stage && k < ns) c[k] = cur;
+                int prev = __shfl_up_sync(kFull, cur, 1);
+                if (lane == 0) prev = carry;
+                if (k > 0 && k < ns && (int64_t)cur - (int64_t)prev <= 1) close = true;
+                carry = __shfl_sync(kFull, cur, 31);
             }
+            if (J.dense != nullptr && __any_sync(kFull, close) && lane == 0) atomicOr(J.dense, 1);
+        }
+        if (stage && lane < kWinPad) {
+            c[-1 - lane] = INT_MIN;
+            c[ns + lane] = INT_MAX;
         }
     }
     __syncthreads();
@@ -539,18 +554,19 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
             qb[m] = 0;
             dst[m] = out + (int64_t)(t0 + tt) * nf + i;
         }
-        // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
+        // bounds of slab j0 = RS s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
         // ceil((S0 + j0 D + max(0, (R-1) D)) / 2^32) (+ the tile's terms), kept
-        // as 64-bit sums that advance by 32 D per full slab
-        const int64_t span32 = 31 * dv;
-        int64_t u = s0 + (span32 < 0 ? span32 : 0);
-        int64_t w = s0 + (span32 > 0 ? span32 : 0);
+        // as 64-bit sums that advance by RS D per full slab
+        const int RS = J.slab_rows == 2 * kRows ? 2 * kRows : kRows;
+        const int64_t span_full = (int64_t)(RS - 1) * dv;
+        int64_t u = s0 + (span_full < 0 ? span_full : 0);
+        int64_t w = s0 + (span_full > 0 ? span_full : 0);
         for (int slab = 0; slab < J.n_slabs; ++slab) {
             if (slab == J.n_slabs - 1) {
                 // the last slab may hold fewer rows
-                const int R = J.n_fdot - slab * kRows;
+                const int R = J.n_fdot - slab * RS;
                 const int64_t span = (int64_t)(R - 1) * dv;
-                const int64_t jd = (int64_t)slab * 32 * dv;
+                const int64_t jd = (int64_t)slab * RS * dv;
                 u = s0 + jd + (span < 0 ? span : 0);
                 w = s0 + jd + (span > 0 ? span : 0);
             }
@@ -599,8 +615,8 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
                 if (ok[m]) *dst[m] = make_int2((int)(o0 + qa[m]), (int)(o0 + max(qa[m], qb[m])));
                 dst[m] += slab_stride;
             }
-            u += 32 * dv;
-            w += 32 * dv;
+            u += RS * dv;
+            w += RS * dv;
         }
     }
 }
@@ -697,6 +713,54 @@ __device__ __forceinline__ void pair_steps(std::integer_sequence<int, Ts...>, ui
     (pair_step<CLAMP, WEIGHTED, Ts>(rbase, X1, X2, e, stride, E, w), ...);
 }
 
+// Step T of the packed walk (64-row slab, two 16-bit counters per word: row
+// r in the low half, row r + 32 in the high half of the same word): X1, X2 are
+// the lane's two peaks on row lane ^ g(T), Y1, Y2 the same peaks 32 rows
+// further (Y = X - 32 D), so all four share the row offset and the step; the
+// low-half updates add 1, the high-half ones 2^16.  Every lane is still on its
+// own bank.
+template <bool CLAMP, int T>
+__device__ __forceinline__ void quad_step(uint32_t rbase, int64_t &X1, int64_t &X2, int64_t &Y1,
+                                          int64_t &Y2, const int64_t (&e)[5], uint32_t stride,
+                                          uint32_t E)
+{
+    constexpr uint32_t gt = (uint32_t)(T ^ (T >> 1));
+    const uint32_t rb = rbase ^ (gt << 2);
+    uint32_t c1 = cell_of(X1), c2 = cell_of(X2), c3 = cell_of(Y1), c4 = cell_of(Y2);
+    if (CLAMP) {
+        c1 = min(c1, E);
+        c2 = min(c2, E);
+        c3 = min(c3, E);
+        c4 = min(c4, E);
+    }
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(c1 * stride + rb) : "memory");
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(c2 * stride + rb) : "memory");
+    asm volatile("red.shared.add.u32 [%0], 65536;" ::"r"(c3 * stride + rb) : "memory");
+    asm volatile("red.shared.add.u32 [%0], 65536;" ::"r"(c4 * stride + rb) : "memory");
+    if constexpr (T < 31) {
+        constexpr int b = ctz5(T + 1);
+        if constexpr ((gt >> b) & 1) {
+            X1 -= e[b];
+            X2 -= e[b];
+            Y1 -= e[b];
+            Y2 -= e[b];
+        } else {
+            X1 += e[b];
+            X2 += e[b];
+            Y1 += e[b];
+            Y2 += e[b];
+        }
+    }
+}
+
+template <bool CLAMP, int... Ts>
+__device__ __forceinline__ void quad_steps(std::integer_sequence<int, Ts...>, uint32_t rbase,
+                                           int64_t X1, int64_t X2, int64_t Y1, int64_t Y2,
+                                           const int64_t (&e)[5], uint32_t stride, uint32_t E)
+{
+    (quad_step<CLAMP, Ts>(rbase, X1, X2, Y1, Y2, e, stride, E), ...);
+}
+
 template <int... Ts>
 __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, int32_t *H0, int lane,
                                            int64_t X, const int64_t (&e)[5], int E, int Wt, int K,
@@ -705,7 +769,7 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
     (diff_step<Ts>(H0, lane, X, e, E, Wt, K, w), ...);
 }
 
-// One block per work item (direction, slab of 32 spin-down rows, tile of W
+// One block per work item (direction, slab of spin-down rows, tile of W
 // frequency cells); a persistent grid strides over the items of all jobs.
 //
 // Shared memory holds the tile's counters H[L][row], L = s - (b0 - K + 1) for
@@ -719,21 +783,31 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // of the per-FFT slot counts; each lane finds the FFT owning its slot from the
 // round's start bits); START mode puts two peaks of one FFT in a slot.  The
 // next round's positions are loaded while the current round is added, and
-// every lane adds its peaks' 32 row updates along the Gray-code row order
-// (pair_step / diff_step), so the 32 atomics of one warp
+// every lane adds its peaks' row updates along the Gray-code row order
+// (pair_step / quad_step / diff_step), so the 32 atomics of one warp
 // instruction always go to 32 different banks.
 //
+// PACK (START mode, plain map): a slab has 64 rows and each counter word holds
+// two 16-bit counts, row r in the low half and row r + 32 in the high half, so
+// one dealt pair of peaks feeds 128 updates (quad_step).  A stripe-start count
+// stays below 2^16 when no FFT has two peaks within one cell (each FFT then
+// starts at most one stripe per cell and row) and n_fft < 2^16; the window
+// pre-pass flags the first condition per job (`dense`) and a flagged job runs
+// its 64-row slabs as two 32-row passes with whole-word counts instead.
+//
 // Emit: warps take 16-cell groups along f0 (START, packed counts) or segments
-// (DIFF, or counts too large to pack); lane l walks row l: START sums a K-cell
-// window of starts, DIFF takes a running sum with the other segments' totals
-// as carry-in.  The count goes to the map (optional) and the warp's max over
-// rows (smallest row on ties) to the direction's profile by a 64-bit
-// atomicMax, which is order-independent.
-template <int MODE, int MAXT, bool WEIGHTED>
+// (DIFF, or counts too large to pack); lane l walks row l (and, packed, row
+// l + 32): START sums a K-cell window of starts, DIFF takes a running sum with
+// the other segments' totals as carry-in.  The count goes to the map
+// (optional) and the warp's max over rows (smallest row on ties) to the
+// direction's profile by a 64-bit atomicMax, which is order-independent.
+template <int MODE, int MAXT, bool WEIGHTED, bool PACK>
 __global__ void __launch_bounds__(MAXT, 1)
 transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words,
                  int32_t guard, uint32_t cell_stride)
 {
+    static_assert(!PACK || (MODE == FH_MODE_START && !WEIGHTED), "packed counters: plain START");
+    constexpr int RS = PACK ? 2 * kRows : kRows;  // rows per slab
     extern __shared__ __align__(16) int32_t smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -752,18 +826,21 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                                 (MODE == FH_MODE_DIFF ? nwarps * 32 : 0);
     const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    // Per job: the unclamped walk runs when the job's largest drift over 32 rows
+    // Per job: the unclamped walk runs when the job's largest drift over a slab
     // stays inside the guards and no input check has failed.  Its windows then
     // hold sorted positions, so every row of every windowed peak lands in the
     // guard cells or the tile; after a failed check (unsorted or non-finite
     // input) the windows can hold anything and the clamped walk, which keeps
-    // every update in [0, E], runs instead.
-    unsigned job_fast = 0;  // bit j: job j may take the unclamped walk
+    // every update in [0, E], runs instead.  (PACK) the packed counters are
+    // used while the window pre-pass found no FFT with two peaks in one cell.
+    unsigned job_fast = 0;    // bit j: job j may take the unclamped walk
+    unsigned job_packed = 0;  // bit j: job j's stripe-start counts fit 16 bits
     for (int j = 0; j < tbl.n_jobs; ++j) {
         const TransformJob &Jt = tbl.job[j];
         if (Jt.dmax != nullptr && Jt.err != nullptr && *Jt.err == 0 &&
-            guard_for(*Jt.dmax) <= guard)
+            guard_for(*Jt.dmax, RS - 1) <= guard)
             job_fast |= 1u << j;
+        if (PACK && Jt.dense != nullptr && *Jt.dense == 0) job_packed |= 1u << j;
     }
 
     for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
@@ -778,8 +855,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int tile = r2 - slab * J->n_tiles;
         const int K = J->k_over, W = J->tile_cells, n_f0 = J->n_f0, n_fdot = J->n_fdot;
         const int n_fft = J->n_fft;
-        const int j0 = slab * kRows;
-        const int R = min(kRows, n_fdot - j0);
+        const int js = slab * RS;
+        const int R_slab = min(RS, n_fdot - js);
         const int b0 = tile * W;
         const int Wt = min(W, n_f0 - b0);
         const int E = Wt + K - 1;
@@ -794,321 +871,477 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                        : nullptr;
         const int32_t *__restrict__ wts =
             J->weights ? J->weights + (int64_t)d_abs * n_fft : nullptr;
-        const bool row_ok = lane < R;
         const bool fast = MODE == FH_MODE_START && ((job_fast >> jb) & 1u);
-
-        // zero the counters (with the guard cells in the fast path); reset the chunk counter
-        {
-            int4 *h4 = reinterpret_cast<int4 *>(fast ? Hlo : H);
-            const int n4 = ((fast ? E + 2 * guard : E) * kRows) >> 2;
-            for (int w = threadIdx.x; w < n4; w += blockDim.x) h4[w] = make_int4(0, 0, 0, 0);
-            if (threadIdx.x == 0) *next_chunk = nwarps;
-        }
-        __syncthreads();
-
-        // accumulate
         const int64_t base_shift = (int64_t)(b0 - K + 1) * 4294967296LL;
         const int64_t e_fixed = (int64_t)E * 4294967296LL;
         const int nchunks = (n_fft + 31) >> 5;
-        // chunks of 32 FFTs (lane <-> FFT): the first round one per warp, then
-        // whoever is free
-        for (int c = warp; c < nchunks;) {
-            int64_t cb, dv, q0;
-            int n;
-            // the FFT's weight on this direction (adaptive map), 1 for the plain map
-            int32_t wt = 1;
-            if constexpr (WEIGHTED)
-                if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
-            if (wrow != nullptr) {
-                // precomputed window: one coalesced load; trusted on the unclamped walk
-                // (the input checks passed and the table was built from the sanitised
-                // CSR), else clamped into the FFT's CSR range
-                const int i = (c << 5) + lane;
-                cb = 0;
-                dv = 0;
-                q0 = 0;
-                n = 0;
-                if (i < n_fft) {
-                    const int2 wv = wrow[i];
-                    dv = __ldg(Dt + i);
-                    cb = __ldg(S0 + i) + (int64_t)j0 * dv + base_shift;
-                    if (fast) {
-                        q0 = wv.x;
-                        n = wv.y - wv.x;
-                    } else {
-                        const int64_t o0 = __ldg(offs + i), o1 = __ldg(offs + i + 1);
-                        const int64_t a = wv.x < o0 ? o0 : (wv.x > o1 ? o1 : wv.x);
-                        const int64_t b = wv.y < a ? a : (wv.y > o1 ? o1 : wv.y);
-                        q0 = a;
-                        n = (int)(b - a);
-                    }
-                }
-            } else {
-                lookup_window(Ad, offs, S0, Dt, n_fft, (c << 5) + lane, j0, R, base_shift,
-                              e_fixed, cb, dv, q0, n);
-            }
-            // START mode deals the peaks out in pairs of one FFT (one slot = two
-            // consecutive peaks of the window; an odd count leaves the last slot's
-            // second peak empty), DIFF mode one peak per slot
-            constexpr bool kPairs = MODE == FH_MODE_START;
-            const int m = kPairs ? (n + 1) >> 1 : n;
-            // exclusive scan of the per-FFT slot counts, owner table of non-empty FFTs
-            int P = m;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, P, o);
-                if (lane >= o) P += y;
-            }
-            const int T = __shfl_sync(kFull, P, 31);
-            P -= m;
-            const bool has = m > 0;
-            // the slot's first peak is kq + (pairs ? 2 : 1) g; the window ends at qe
-            const int kq = (int)q0 - (kPairs ? 2 * P : P);
-            const int qe = (int)q0 + n;
-            const unsigned nonempty = __ballot_sync(kFull, has);
-            if (has) tab[__popc(nonempty & lanemask_lt)] = lane;
-            __syncwarp();
 
-            // Slot g = base + lane of a round belongs to the non-empty FFT whose
-            // range [P, P + m) holds it.  `before` counts the non-empty FFTs
-            // starting below the base; bases are fetched in increasing order, 32
-            // apart.  The slot's peaks are positions q0 + k, k = (pairs) 2 (g - P)
-            // and 2 (g - P) + 1 (if below q0 + n), or (singles) g - P: the owner
-            // publishes kq = q0 - 2 P (q0 - P) and its window end qe.
-            int before = 0;
-            auto fetch = [&](int base, int64_t &a1, int64_t &a2, bool &two, int &owner) {
-                const unsigned rel = (unsigned)(P - base);
-                const unsigned bits = __reduce_or_sync(kFull, (has && rel < 32u) ? (1u << rel) : 0u);
-                const int oc = before + __popc(bits & lanemask_le) - 1;
-                before += __popc(bits);
-                owner = tab[oc < 0 ? 0 : oc];
-                const int okq = __shfl_sync(kFull, kq, owner);
-                const int g = base + lane;
-                const bool live = g < T;
-                if (kPairs) {
-                    const int oqe = __shfl_sync(kFull, qe, owner);
-                    const int k = okq + 2 * g;
-                    two = live && k + 1 < oqe;
-                    a1 = live ? __ldg(Ad + k) : 0;
-                    a2 = two ? __ldg(Ad + k + 1) : 0;
-                } else {
-                    two = false;
-                    a1 = live ? __ldg(Ad + (okq + g)) : 0;
-                    a2 = 0;
-                }
-            };
-            // X of the lane's row for the slot's peaks and their step table.  An
-            // empty slot (g >= T) is parked in guard cell -1 with zero steps.  An
-            // empty second peak walks with the first one's steps from a start
-            // that keeps all 32 rows in guard cells -guard .. -1 on the unclamped
-            // walk (|31 D| is below guard - 1 cells there), and far below cell 0
-            // on the clamped walk (which sends it to the dump cell).  Never read.
-            // On the unclamped walk every windowed peak's 32 rows stay inside the
-            // guard cells: the window holds the peaks with A - cb in
-            // [min(0, (R-1) D), max(0, (R-1) D) + E 2^32) (to one cell), and
-            // |31 D| stays below guard - 2 cells.
-            auto setup = [&](int g, int64_t a1, int64_t a2, bool two, int owner, int64_t &X1,
-                             int64_t &X2, int64_t (&e)[5], int32_t &ow) {
+        // One pass over the tile: zero the counters, accumulate rows j0 .. j0 +
+        // R - 1 (QUAD: rows j0 .. j0 + 31 in the low halves and j0 + 32 .. j0 +
+        // R - 1 in the high halves), emit.  The windows (table or lookup) cover
+        // the whole slab, a superset of the pass's rows when a packed slab runs
+        // as two passes.
+        auto pass = [&](const int j0, const int R, auto quad_tag) {
+            constexpr bool QUAD = decltype(quad_tag)::value;
+            const bool row_ok = lane < R;
+
+            // zero the counters (with the guard cells in the fast path); reset the chunk counter
+            {
+                int4 *h4 = reinterpret_cast<int4 *>(fast ? Hlo : H);
+                const int n4 = ((fast ? E + 2 * guard : E) * kRows) >> 2;
+                for (int w = threadIdx.x; w < n4; w += blockDim.x) h4[w] = make_int4(0, 0, 0, 0);
+                if (threadIdx.x == 0) *next_chunk = nwarps;
+            }
+            __syncthreads();
+
+            // accumulate
+            // chunks of 32 FFTs (lane <-> FFT): the first round one per warp, then
+            // whoever is free
+            for (int c = warp; c < nchunks;) {
+                int64_t cb, dv, q0;
+                int n;
+                // the FFT's weight on this direction (adaptive map), 1 for the plain map
+                int32_t wt = 1;
                 if constexpr (WEIGHTED)
-                    ow = __shfl_sync(kFull, wt, owner);
-                else
-                    ow = 1;
-                const int64_t ocb = __shfl_sync(kFull, cb, owner);
-                const int64_t odv0 = __shfl_sync(kFull, dv, owner);
-                const bool live = g < T;
-                const int64_t odv = live ? odv0 : 0;
-                // e[b] = +-(D << b), + when bit b of the lane is set
-                const int64_t ndv = -odv;
+                    if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
+                if (wrow != nullptr) {
+                    // precomputed window: one coalesced load; trusted on the unclamped walk
+                    // (the input checks passed and the table was built from the sanitised
+                    // CSR), else clamped into the FFT's CSR range
+                    const int i = (c << 5) + lane;
+                    cb = 0;
+                    dv = 0;
+                    q0 = 0;
+                    n = 0;
+                    if (i < n_fft) {
+                        const int2 wv = wrow[i];
+                        dv = __ldg(Dt + i);
+                        cb = __ldg(S0 + i) + (int64_t)j0 * dv + base_shift;
+                        if (fast) {
+                            q0 = wv.x;
+                            n = wv.y - wv.x;
+                        } else {
+                            const int64_t o0 = __ldg(offs + i), o1 = __ldg(offs + i + 1);
+                            const int64_t a = wv.x < o0 ? o0 : (wv.x > o1 ? o1 : wv.x);
+                            const int64_t b = wv.y < a ? a : (wv.y > o1 ? o1 : wv.y);
+                            q0 = a;
+                            n = (int)(b - a);
+                        }
+                    }
+                } else {
+                    int64_t cbs;
+                    lookup_window(Ad, offs, S0, Dt, n_fft, (c << 5) + lane, js, R_slab, base_shift,
+                                  e_fixed, cbs, dv, q0, n);
+                    cb = cbs + (int64_t)(j0 - js) * dv;
+                }
+                // START mode deals the peaks out in pairs of one FFT (one slot = two
+                // consecutive peaks of the window; an odd count leaves the last slot's
+                // second peak empty), DIFF mode one peak per slot
+                constexpr bool kPairs = MODE == FH_MODE_START;
+                const int m = kPairs ? (n + 1) >> 1 : n;
+                // exclusive scan of the per-FFT slot counts, owner table of non-empty FFTs
+                int P = m;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) e[b] = (((lane >> b) & 1) ? odv : ndv) * (int64_t)(1 << b);
-                const int64_t lane_dv = (int64_t)lane * odv;
-                X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
-                if (kPairs) {
-                    const int64_t park =
-                        fast ? (odv > 0 ? -(int64_t(1) << 32) : -((int64_t)guard << 32)) - lane_dv
-                             : -(int64_t(1) << 62);
-                    X2 = two ? a2 - ocb - lane_dv : park;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, P, o);
+                    if (lane >= o) P += y;
                 }
-            };
-            int64_t a1_nx = 0, a2_nx = 0;
-            bool two_nx = false;
-            int own_nx = 0;
-            if (T > 0) fetch(0, a1_nx, a2_nx, two_nx, own_nx);
-            for (int base = 0; base < T; base += 32) {
-                int64_t a1 = a1_nx, a2 = a2_nx;
-                bool two = two_nx;
-                int owner = own_nx;
-                if (base + 32 < T) fetch(base + 32, a1_nx, a2_nx, two_nx, own_nx);
-                // A last round of L <= 16 slots (unclamped START walk): S = the
-                // power of two >= L; slot q = lane mod S is walked by the 32 / S
-                // lanes lane = q + S p, lane p taking rows S p .. S p + S - 1 in
-                // S Gray-code steps (row = lane ^ g(t), t < S).  Every (slot, row)
-                // is added once, the 32 lanes stay on 32 banks, and the start
-                // X = A - cb - lane D and the step table are those of a full round.
-                int S = 32;
-                if (MODE == FH_MODE_START && fast && T - base <= 16) {
-                    const int L = T - base;
-                    S = L <= 1 ? 1 : (L <= 2 ? 2 : (L <= 4 ? 4 : (L <= 8 ? 8 : 16)));
-                    const int src = lane & (S - 1);
-                    a1 = __shfl_sync(kFull, a1, src);
-                    a2 = __shfl_sync(kFull, a2, src);
-                    two = __shfl_sync(kFull, (int)two, src) != 0;
-                    owner = __shfl_sync(kFull, owner, src);
-                }
-                int64_t X1, X2 = 0, e[5];
-                int32_t ow;
-                setup(base + (lane & (S - 1)), a1, a2, two, owner, X1, X2, e, ow);
-                if (MODE == FH_MODE_START) {
-                    if (fast) {
+                const int T = __shfl_sync(kFull, P, 31);
+                P -= m;
+                const bool has = m > 0;
+                // the slot's first peak is kq + (pairs ? 2 : 1) g; the window ends at qe
+                const int kq = (int)q0 - (kPairs ? 2 * P : P);
+                const int qe = (int)q0 + n;
+                const unsigned nonempty = __ballot_sync(kFull, has);
+                if (has) tab[__popc(nonempty & lanemask_lt)] = lane;
+                __syncwarp();
+
+                // Slot g = base + lane of a round belongs to the non-empty FFT whose
+                // range [P, P + m) holds it.  `before` counts the non-empty FFTs
+                // starting below the base; bases are fetched in increasing order, 32
+                // apart.  The slot's peaks are positions q0 + k, k = (pairs) 2 (g - P)
+                // and 2 (g - P) + 1 (if below q0 + n), or (singles) g - P: the owner
+                // publishes kq = q0 - 2 P (q0 - P) and its window end qe.
+                int before = 0;
+                auto fetch = [&](int base, int64_t &a1, int64_t &a2, bool &two, int &owner) {
+                    const unsigned rel = (unsigned)(P - base);
+                    const unsigned bits =
+                        __reduce_or_sync(kFull, (has && rel < 32u) ? (1u << rel) : 0u);
+                    const int oc = before + __popc(bits & lanemask_le) - 1;
+                    before += __popc(bits);
+                    owner = tab[oc < 0 ? 0 : oc];
+                    const int okq = __shfl_sync(kFull, kq, owner);
+                    const int g = base + lane;
+                    const bool live = g < T;
+                    if (kPairs) {
+                        const int oqe = __shfl_sync(kFull, qe, owner);
+                        const int k = okq + 2 * g;
+                        two = live && k + 1 < oqe;
+                        a1 = live ? __ldg(Ad + k) : 0;
+                        a2 = two ? __ldg(Ad + k + 1) : 0;
+                    } else {
+                        two = false;
+                        a1 = live ? __ldg(Ad + (okq + g)) : 0;
+                        a2 = 0;
+                    }
+                };
+                // X of the lane's row for the slot's peaks and their step table.  An
+                // empty slot (g >= T) is parked in guard cell -1 with zero steps.  An
+                // empty second peak walks with the first one's steps from a start
+                // that keeps all the pass's rows in guard cells -guard .. -1 on the
+                // unclamped walk (|(RS - 1) D| is below guard - 1 cells there), and far
+                // below cell 0 on the clamped walk (which sends it to the dump cell).
+                // Never read.  On the unclamped walk every windowed peak's rows stay
+                // inside the guard cells: the window holds the peaks with A - cb_slab
+                // in [min(0, (R_slab-1) D), max(0, (R_slab-1) D) + E 2^32) (to one
+                // cell), and |(RS - 1) D| stays below guard - 2 cells.  QUAD: Y1, Y2
+                // are the same peaks 32 rows further.
+                auto setup = [&](int g, int64_t a1, int64_t a2, bool two, int owner, int64_t &X1,
+                                 int64_t &X2, int64_t (&e)[5], int32_t &ow, int64_t &dv_slot) {
+                    if constexpr (WEIGHTED)
+                        ow = __shfl_sync(kFull, wt, owner);
+                    else
+                        ow = 1;
+                    const int64_t ocb = __shfl_sync(kFull, cb, owner);
+                    const int64_t odv0 = __shfl_sync(kFull, dv, owner);
+                    const bool live = g < T;
+                    const int64_t odv = live ? odv0 : 0;
+                    dv_slot = odv;
+                    // e[b] = +-(D << b), + when bit b of the lane is set
+                    const int64_t ndv = -odv;
+#pragma unroll
+                    for (int b = 0; b < 5; ++b)
+                        e[b] = (((lane >> b) & 1) ? odv : ndv) * (int64_t)(1 << b);
+                    const int64_t lane_dv = (int64_t)lane * odv;
+                    X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
+                    if (kPairs) {
+                        const int64_t park =
+                            fast ? (odv > 0 ? -(int64_t(1) << 32) : -((int64_t)guard << 32)) -
+                                       lane_dv
+                                 : -(int64_t(1) << 62);
+                        X2 = two ? a2 - ocb - lane_dv : park;
+                    }
+                };
+                int64_t a1_nx = 0, a2_nx = 0;
+                bool two_nx = false;
+                int own_nx = 0;
+                if (T > 0) fetch(0, a1_nx, a2_nx, two_nx, own_nx);
+                for (int base = 0; base < T; base += 32) {
+                    int64_t a1 = a1_nx, a2 = a2_nx;
+                    bool two = two_nx;
+                    int owner = own_nx;
+                    if (base + 32 < T) fetch(base + 32, a1_nx, a2_nx, two_nx, own_nx);
+                    // A last round of L <= 16 slots (unclamped START walk): S = the
+                    // power of two >= L; slot q = lane mod S is walked by the 32 / S
+                    // lanes lane = q + S p, lane p taking rows S p .. S p + S - 1 in
+                    // S Gray-code steps (row = lane ^ g(t), t < S).  Every (slot, row)
+                    // is added once, the 32 lanes stay on 32 banks, and the start
+                    // X = A - cb - lane D and the step table are those of a full round.
+                    int S = 32;
+                    if (MODE == FH_MODE_START && fast && T - base <= 16) {
+                        const int L = T - base;
+                        S = L <= 1 ? 1 : (L <= 2 ? 2 : (L <= 4 ? 4 : (L <= 8 ? 8 : 16)));
+                        const int src = lane & (S - 1);
+                        a1 = __shfl_sync(kFull, a1, src);
+                        a2 = __shfl_sync(kFull, a2, src);
+                        two = __shfl_sync(kFull, (int)two, src) != 0;
+                        owner = __shfl_sync(kFull, owner, src);
+                    }
+                    int64_t X1, X2 = 0, e[5], dv_slot;
+                    int32_t ow;
+                    setup(base + (lane & (S - 1)), a1, a2, two, owner, X1, X2, e, ow, dv_slot);
+                    if (MODE == FH_MODE_START) {
                         using std::make_integer_sequence;
                         const uint32_t st = cell_stride, ee = (uint32_t)E, ww = (uint32_t)ow;
-                        switch (S) {
-                        case 1:
-                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 1>{}, rbase, X1, X2, e, st, ee, ww);
-                            break;
-                        case 2:
-                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 2>{}, rbase, X1, X2, e, st, ee, ww);
-                            break;
-                        case 4:
-                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 4>{}, rbase, X1, X2, e, st, ee, ww);
-                            break;
-                        case 8:
-                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 8>{}, rbase, X1, X2, e, st, ee, ww);
-                            break;
-                        case 16:
-                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 16>{}, rbase, X1, X2, e, st, ee, ww);
-                            break;
-                        default:
-                            pair_steps<false, WEIGHTED>(make_integer_sequence<int, 32>{}, rbase, X1, X2, e, st, ee, ww);
-                        }
-                    } else
-                        pair_steps<true, WEIGHTED>(std::make_integer_sequence<int, 32>{}, rbase, X1,
-                                                   X2, e, cell_stride, (uint32_t)E, (uint32_t)ow);
-                } else if (base + lane < T) {
-                    diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X1, e, E, Wt, K, ow);
+                        if constexpr (QUAD) {
+                            // the same peaks 32 rows further, in the high halves
+                            const int64_t Y1 = X1 - 32 * dv_slot, Y2 = X2 - 32 * dv_slot;
+                            if (fast) {
+                                switch (S) {
+                                case 1:
+                                    quad_steps<false>(make_integer_sequence<int, 1>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
+                                    break;
+                                case 2:
+                                    quad_steps<false>(make_integer_sequence<int, 2>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
+                                    break;
+                                case 4:
+                                    quad_steps<false>(make_integer_sequence<int, 4>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
+                                    break;
+                                case 8:
+                                    quad_steps<false>(make_integer_sequence<int, 8>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
+                                    break;
+                                case 16:
+                                    quad_steps<false>(make_integer_sequence<int, 16>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
+                                    break;
+                                default:
+                                    quad_steps<false>(make_integer_sequence<int, 32>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
+                                }
+                            } else
+                                quad_steps<true>(make_integer_sequence<int, 32>{}, rbase, X1, X2,
+                                                 Y1, Y2, e, st, ee);
+                        } else if (fast) {
+                            switch (S) {
+                            case 1:
+                                pair_steps<false, WEIGHTED>(make_integer_sequence<int, 1>{}, rbase, X1, X2, e, st, ee, ww);
+                                break;
+                            case 2:
+                                pair_steps<false, WEIGHTED>(make_integer_sequence<int, 2>{}, rbase, X1, X2, e, st, ee, ww);
+                                break;
+                            case 4:
+                                pair_steps<false, WEIGHTED>(make_integer_sequence<int, 4>{}, rbase, X1, X2, e, st, ee, ww);
+                                break;
+                            case 8:
+                                pair_steps<false, WEIGHTED>(make_integer_sequence<int, 8>{}, rbase, X1, X2, e, st, ee, ww);
+                                break;
+                            case 16:
+                                pair_steps<false, WEIGHTED>(make_integer_sequence<int, 16>{}, rbase, X1, X2, e, st, ee, ww);
+                                break;
+                            default:
+                                pair_steps<false, WEIGHTED>(make_integer_sequence<int, 32>{}, rbase, X1, X2, e, st, ee, ww);
+                            }
+                        } else
+                            pair_steps<true, WEIGHTED>(make_integer_sequence<int, 32>{}, rbase, X1,
+                                                       X2, e, st, ee, ww);
+                    } else if (base + lane < T) {
+                        diff_steps(std::make_integer_sequence<int, 32>{}, H, lane, X1, e, E, Wt, K,
+                                   ow);
+                    }
                 }
+                __syncwarp();
+                int nc = 0;
+                if (lane == 0) nc = atomicAdd(next_chunk, 1);
+                c = __shfl_sync(kFull, nc, 0);
             }
-            __syncwarp();
-            int nc = 0;
-            if (lane == 0) nc = atomicAdd(next_chunk, 1);
-            c = __shfl_sync(kFull, nc, 0);
-        }
-        __syncthreads();
+            __syncthreads();
 
-        // emit counts, map and profile
-        int32_t *maprow = nullptr;
-        if (J->maps != nullptr && row_ok)
-            maprow = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
-        unsigned long long *prof =
-            reinterpret_cast<unsigned long long *>(J->profile) + (int64_t)d_abs * n_f0 + b0;
-        // Per cell the profile takes the warp's max over its rows, smallest row
-        // on ties.  Counts below 2^26 fit one packed signed reduction
-        // 32 count + (31 - lane); rows beyond the slab start their window at
-        // -2^26, so they stay negative and never win.
-        const bool packed = J->count_bound < (int64_t(1) << 26);
-        const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 31u;
-        auto key_of = [&](int v) {
-            return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
-                   (unsigned long long)(key_lo + (uint32_t)(v & 31));
-        };
-        if (MODE == FH_MODE_START && packed) {
-            // a K-cell window slides along the warp's segment (count of cell c =
-            // sum of the starts in cells c .. c + K - 1), 16 cells per group:
-            // lane m keeps cell m's reduction and the group's 16 profile atomics
-            // go out together
-            const int seg = (((Wt + nwarps - 1) / nwarps) + 15) & ~15;
-            const int c0 = min(Wt, warp * seg);
-            const int c1 = min(Wt, c0 + seg);
-            const int c31 = 31 - lane;
-            int win = row_ok ? 0 : -(1 << 26);
-            if (c0 < c1)
-                for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
-            // a lane's map row is written 16 cells (64 bytes) at a time, as four
-            // 16-byte stores where the row is 16-byte aligned (the group's cells
-            // start at a multiple of 16 of the tile), else one cell at a time
-            const bool vec_map = maprow != nullptr && (((uintptr_t)maprow & 15u) == 0);
-            auto run = [&](auto map_tag) {
-                constexpr bool kMap = decltype(map_tag)::value;
-                int c = c0;
-                for (; c + 16 <= c1; c += 16) {
-                    const int32_t *h0 = H + c * kRows + lane;
-                    const int32_t *h1 = h0 + K * kRows;
-                    int myv = 0;
-                    int cnts[kMap ? 16 : 1];
-#pragma unroll
-                    for (int m = 0; m < 16; ++m) {
-                        const int cnt = win;
-                        win += h1[m * kRows] - h0[m * kRows];
-                        if constexpr (kMap) cnts[m] = cnt;
-                        const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
-                        if (lane == m) myv = v;
+            // emit counts, map and profile
+            unsigned long long *prof =
+                reinterpret_cast<unsigned long long *>(J->profile) + (int64_t)d_abs * n_f0 + b0;
+            if constexpr (QUAD) {
+                // Packed words: row lane in the low half, row lane + 32 in the high
+                // half.  Per cell the lane forms both counts (K-cell windows of
+                // starts), keys them as 64 count + (63 - row in the slab) and one
+                // signed reduction gives the warp's (max count, smallest row) over
+                // the 64 rows; rows beyond the slab start their windows at -2^25 and
+                // never win (counts stay below 2^25 on this path).
+                const bool hi_ok = lane + kRows < R;
+                int32_t *maplo = nullptr, *maphi = nullptr;
+                if (J->maps != nullptr) {
+                    int32_t *m0 = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
+                    maplo = row_ok ? m0 : nullptr;
+                    maphi = hi_ok ? m0 + (int64_t)kRows * n_f0 : nullptr;
+                }
+                const int seg = (((Wt + nwarps - 1) / nwarps) + 15) & ~15;
+                const int c0 = min(Wt, warp * seg);
+                const int c1 = min(Wt, c0 + seg);
+                const int klo = 63 - lane, khi = 31 - lane;
+                int winlo = row_ok ? 0 : -(1 << 25);
+                int winhi = hi_ok ? 0 : -(1 << 25);
+                if (c0 < c1)
+                    for (int L = c0; L < c0 + K; ++L) {
+                        const uint32_t h = (uint32_t)H[L * kRows + lane];
+                        winlo += (int)(h & 0xFFFFu);
+                        winhi += (int)(h >> 16);
                     }
-                    if constexpr (kMap) {
-                        if (vec_map) {
-                            int4 *d4 = reinterpret_cast<int4 *>(maprow + c);
+                const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 63u;
+                auto key_of = [&](int v) {
+                    return ((unsigned long long)(uint32_t)(v >> 6) << 32) |
+                           (unsigned long long)(key_lo + (uint32_t)(v & 63));
+                };
+                // the high row is 32 n_f0 words after the low one: same alignment
+                const int32_t *mrow = maplo ? maplo : maphi;
+                const bool vec_map = mrow != nullptr && (((uintptr_t)mrow & 15u) == 0);
+                auto run = [&](auto map_tag) {
+                    constexpr bool kMap = decltype(map_tag)::value;
+                    int c = c0;
+                    for (; c + 16 <= c1; c += 16) {
+                        const int32_t *h0 = H + c * kRows + lane;
+                        const int32_t *h1 = h0 + K * kRows;
+                        int myv = 0;
+                        int cl[kMap ? 16 : 1], ch[kMap ? 16 : 1];
 #pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                d4[q] = make_int4(cnts[4 * q], cnts[4 * q + 1], cnts[4 * q + 2],
-                                                  cnts[4 * q + 3]);
-                        } else if (row_ok) {
+                        for (int m = 0; m < 16; ++m) {
+                            const int lo = winlo, hi = winhi;
+                            const uint32_t a = (uint32_t)h1[m * kRows], b = (uint32_t)h0[m * kRows];
+                            winlo += (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
+                            winhi += (int)(a >> 16) - (int)(b >> 16);
+                            if constexpr (kMap) {
+                                cl[m] = lo;
+                                ch[m] = hi;
+                            }
+                            const int v = max(lo * 64 + klo, hi * 64 + khi);
+                            const int r = __reduce_max_sync(kFull, v);
+                            if (lane == m) myv = r;
+                        }
+                        if constexpr (kMap) {
+                            if (vec_map) {
+                                if (maplo) {
+                                    int4 *d4 = reinterpret_cast<int4 *>(maplo + c);
 #pragma unroll
-                            for (int m = 0; m < 16; ++m) maprow[c + m] = cnts[m];
+                                    for (int q = 0; q < 4; ++q)
+                                        d4[q] = make_int4(cl[4 * q], cl[4 * q + 1], cl[4 * q + 2], cl[4 * q + 3]);
+                                }
+                                if (maphi) {
+                                    int4 *d4 = reinterpret_cast<int4 *>(maphi + c);
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        d4[q] = make_int4(ch[4 * q], ch[4 * q + 1], ch[4 * q + 2], ch[4 * q + 3]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int m = 0; m < 16; ++m) {
+                                    if (maplo) maplo[c + m] = cl[m];
+                                    if (maphi) maphi[c + m] = ch[m];
+                                }
+                            }
+                        }
+                        if (lane < 16) atomicMax(prof + c + lane, key_of(myv));
+                    }
+                    for (; c < c1; ++c) {
+                        const int lo = winlo, hi = winhi;
+                        // the segment's last step may read cell E (the dump cell); that value is unused
+                        const uint32_t a = (uint32_t)H[(c + K) * kRows + lane];
+                        const uint32_t b = (uint32_t)H[c * kRows + lane];
+                        winlo += (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
+                        winhi += (int)(a >> 16) - (int)(b >> 16);
+                        if (kMap && maplo) maplo[c] = lo;
+                        if (kMap && maphi) maphi[c] = hi;
+                        const int v = __reduce_max_sync(kFull, max(lo * 64 + klo, hi * 64 + khi));
+                        if (lane == 0) atomicMax(prof + c, key_of(v));
+                    }
+                };
+                if (J->maps != nullptr)
+                    run(std::true_type{});
+                else
+                    run(std::false_type{});
+            } else {
+                int32_t *maprow = nullptr;
+                if (J->maps != nullptr && row_ok)
+                    maprow = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
+                // Per cell the profile takes the warp's max over its rows, smallest row
+                // on ties.  Counts below 2^26 fit one packed signed reduction
+                // 32 count + (31 - lane); rows beyond the pass start their window at
+                // -2^26, so they stay negative and never win.
+                const bool packed = J->count_bound < (int64_t(1) << 26);
+                const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 31u;
+                auto key_of = [&](int v) {
+                    return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
+                           (unsigned long long)(key_lo + (uint32_t)(v & 31));
+                };
+                if (MODE == FH_MODE_START && packed) {
+                    // a K-cell window slides along the warp's segment (count of cell c =
+                    // sum of the starts in cells c .. c + K - 1), 16 cells per group:
+                    // lane m keeps cell m's reduction and the group's 16 profile atomics
+                    // go out together
+                    const int seg = (((Wt + nwarps - 1) / nwarps) + 15) & ~15;
+                    const int c0 = min(Wt, warp * seg);
+                    const int c1 = min(Wt, c0 + seg);
+                    const int c31 = 31 - lane;
+                    int win = row_ok ? 0 : -(1 << 26);
+                    if (c0 < c1)
+                        for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
+                    // a lane's map row is written 16 cells (64 bytes) at a time, as four
+                    // 16-byte stores where the row is 16-byte aligned (the group's cells
+                    // start at a multiple of 16 of the tile), else one cell at a time
+                    const bool vec_map = maprow != nullptr && (((uintptr_t)maprow & 15u) == 0);
+                    auto run = [&](auto map_tag) {
+                        constexpr bool kMap = decltype(map_tag)::value;
+                        int c = c0;
+                        for (; c + 16 <= c1; c += 16) {
+                            const int32_t *h0 = H + c * kRows + lane;
+                            const int32_t *h1 = h0 + K * kRows;
+                            int myv = 0;
+                            int cnts[kMap ? 16 : 1];
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) {
+                                const int cnt = win;
+                                win += h1[m * kRows] - h0[m * kRows];
+                                if constexpr (kMap) cnts[m] = cnt;
+                                const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
+                                if (lane == m) myv = v;
+                            }
+                            if constexpr (kMap) {
+                                if (vec_map) {
+                                    int4 *d4 = reinterpret_cast<int4 *>(maprow + c);
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        d4[q] = make_int4(cnts[4 * q], cnts[4 * q + 1],
+                                                          cnts[4 * q + 2], cnts[4 * q + 3]);
+                                } else if (row_ok) {
+#pragma unroll
+                                    for (int m = 0; m < 16; ++m) maprow[c + m] = cnts[m];
+                                }
+                            }
+                            if (lane < 16) atomicMax(prof + c + lane, key_of(myv));
+                        }
+                        for (; c < c1; ++c) {
+                            const int cnt = win;
+                            // the segment's last step may read cell E (the dump cell); that value is unused
+                            win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
+                            if (kMap && row_ok) maprow[c] = cnt;
+                            const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
+                            if (lane == 0) atomicMax(prof + c, key_of(v));
+                        }
+                    };
+                    if (J->maps != nullptr)
+                        run(std::true_type{});
+                    else
+                        run(std::false_type{});
+                } else {
+                    // generic path (DIFF mode, or counts too large to pack): one cell at a
+                    // time, lane 0 takes the profile atomic
+                    const int seg = (Wt + nwarps - 1) / nwarps;
+                    const int c0 = min(Wt, warp * seg);
+                    const int c1 = min(Wt, c0 + seg);
+                    auto emit = [&](int c, int count) {
+                        if (maprow) maprow[c] = count;
+                        const int m = __reduce_max_sync(kFull, row_ok ? count : INT_MIN);
+                        const unsigned rm =
+                            __reduce_min_sync(kFull, (row_ok && count == m) ? (unsigned)lane : 32u);
+                        const unsigned long long key =
+                            ((unsigned long long)(unsigned)m << 32) |
+                            (0xFFFFFFFFull - (unsigned long long)(unsigned)(j0 + rm));
+                        if (lane == 0) atomicMax(prof + c, key);
+                    };
+                    if (MODE == FH_MODE_START) {
+                        int win = 0;
+                        if (c0 < c1)
+                            for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
+                        for (int c = c0; c < c1; ++c) {
+                            emit(c, win);
+                            win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
+                        }
+                    } else {
+                        int32_t *segtot = Hlo + hist_words + nwarps * 32;
+                        int tot = 0;
+                        for (int c = c0; c < c1; ++c) tot += H[c * kRows + lane];
+                        segtot[warp * 32 + lane] = tot;
+                        __syncthreads();
+                        int acc = 0;
+                        for (int w = 0; w < warp; ++w) acc += segtot[w * 32 + lane];
+                        for (int c = c0; c < c1; ++c) {
+                            acc += H[c * kRows + lane];
+                            emit(c, acc);
                         }
                     }
-                    if (lane < 16) atomicMax(prof + c + lane, key_of(myv));
-                }
-                for (; c < c1; ++c) {
-                    const int cnt = win;
-                    // the segment's last step may read cell E (the dump cell); that value is unused
-                    win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
-                    if (kMap && row_ok) maprow[c] = cnt;
-                    const int v = __reduce_max_sync(kFull, cnt * 32 + c31);
-                    if (lane == 0) atomicMax(prof + c, key_of(v));
-                }
-            };
-            if (J->maps != nullptr)
-                run(std::true_type{});
-            else
-                run(std::false_type{});
-        } else {
-            // generic path (DIFF mode, or counts too large to pack): one cell at a
-            // time, lane 0 takes the profile atomic
-            const int seg = (Wt + nwarps - 1) / nwarps;
-            const int c0 = min(Wt, warp * seg);
-            const int c1 = min(Wt, c0 + seg);
-            auto emit = [&](int c, int count) {
-                if (maprow) maprow[c] = count;
-                const int m = __reduce_max_sync(kFull, row_ok ? count : INT_MIN);
-                const unsigned rm =
-                    __reduce_min_sync(kFull, (row_ok && count == m) ? (unsigned)lane : 32u);
-                const unsigned long long key =
-                    ((unsigned long long)(unsigned)m << 32) |
-                    (0xFFFFFFFFull - (unsigned long long)(unsigned)(j0 + rm));
-                if (lane == 0) atomicMax(prof + c, key);
-            };
-            if (MODE == FH_MODE_START) {
-                int win = 0;
-                if (c0 < c1)
-                    for (int L = c0; L < c0 + K; ++L) win += H[L * kRows + lane];
-                for (int c = c0; c < c1; ++c) {
-                    emit(c, win);
-                    win += H[(c + K) * kRows + lane] - H[c * kRows + lane];
-                }
-            } else {
-                int32_t *segtot = Hlo + hist_words + nwarps * 32;
-                int tot = 0;
-                for (int c = c0; c < c1; ++c) tot += H[c * kRows + lane];
-                segtot[warp * 32 + lane] = tot;
-                __syncthreads();
-                int acc = 0;
-                for (int w = 0; w < warp; ++w) acc += segtot[w * 32 + lane];
-                for (int c = c0; c < c1; ++c) {
-                    acc += H[c * kRows + lane];
-                    emit(c, acc);
                 }
             }
+            __syncthreads();
+        };
+
+        if constexpr (PACK) {
+            if (((job_packed >> jb) & 1u) && R_slab > kRows) {
+                pass(js, R_slab, std::true_type{});
+            } else {
+                // 32 rows or fewer (the counts stay in the low halves, whole-word
+                // counts equal them), or a job whose counts need whole words: the
+                // slab as one or two 32-row passes
+                pass(js, min(kRows, R_slab), std::false_type{});
+                if (R_slab > kRows) pass(js + kRows, R_slab - kRows, std::false_type{});
+            }
+        } else {
+            pass(js, R_slab, std::false_type{});
         }
-        __syncthreads();
     }
 }
 
@@ -1252,6 +1485,47 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectArgs a)
     }
 }
 
+// ---------------------------------------------------------------- adaptive count bound
+// Eq. ncountadap adds W_i per stripe of FFT i, so a count is at most
+// sum_i W_i c_i, c_i = the most stripes of FFT i on one cell.  Two stripes of
+// FFT i share a cell on some row only if their positions differ by less than K
+// cells (s_q - s_p <= K - 1 with s = floor((A - shift) / 2^32) forces
+// A_q - A_p < K 2^32), so c_i <= the most positions of FFT i inside a
+// half-open window of K cells, found here by two pointers over the FFT's
+// ascending positions.  One thread per (direction, FFT); bound[d] receives
+// sum_i W_{d,i} c_{d,i} (each product capped at 2^40, which already exceeds
+// any admissible bound).  Every index stays inside the FFT's CSR range (a
+// valid CSR); unsorted positions only loosen the bound, and such inputs are
+// reported by the device checks.
+__global__ void __launch_bounds__(256)
+weight_bound_kernel(const int64_t *__restrict__ A, const int64_t *__restrict__ offsets,
+                    const int32_t *__restrict__ W, int32_t n_fft, int64_t n_peaks,
+                    int32_t k_over, unsigned long long *__restrict__ bound)
+{
+    const int d = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n_fft) {
+        const int64_t *Ad = A + (int64_t)d * n_peaks;
+        const int64_t o0 = offsets[i], o1 = offsets[i + 1];
+        const unsigned long long width = (unsigned long long)k_over << 32;
+        int64_t q = o0, c = 0;
+        for (int64_t p = o0; p < o1; ++p) {
+            if (q < p + 1) q = p + 1;
+            // positions within K cells of A_p (unsigned difference: a wrap from
+            // unsorted input ends the window instead of overflowing)
+            while (q < o1 && (unsigned long long)(Ad[q] - Ad[p]) < width) ++q;
+            if (q - p > c) c = q - p;
+        }
+        const unsigned long long w = (unsigned long long)(uint32_t)W[(int64_t)d * n_fft + i];
+        const unsigned long long cap = 1ull << 40;
+        v = (c >= (int64_t)(cap >> 1) || w * (unsigned long long)c > cap) ? cap
+                                                                          : w * (unsigned long long)c;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(bound + d, v);
+}
+
 // ---------------------------------------------------------------- measurement
 // Shared-memory atomicAdd throughput.  Variant 0: lane l always hits bank l
 // (8 independent words per thread, immediate offsets, no address math in the
@@ -1283,6 +1557,26 @@ smem_atomic_bench_kernel(int32_t variant, int32_t iters, unsigned long long *sin
     unsigned long long acc = 0;
     for (int w = threadIdx.x; w < kWords; w += blockDim.x) acc += (unsigned)s[w];
     atomicAdd(sink, acc);
+}
+
+// Binary64 throughput: every thread keeps 8 independent chains, each step one
+// __dmul_rn and one __dadd_rn (never contracted into an FMA, like the
+// positions' arithmetic); the sum of all chains goes to *sink so nothing is
+// dead.  8 x 2 operations per thread per iteration.
+__global__ void __launch_bounds__(512)
+fp64_bench_kernel(int32_t iters, double a, double b, double *sink)
+{
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1.0 + 1e-3 * (double)(threadIdx.x + 37 * k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __dadd_rn(__dmul_rn(x[k], a), b);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc += x[k];
+    if (acc == 12345.678) sink[0] = acc;  // almost never taken; keeps the chains live
 }
 
 }  // namespace
@@ -1343,10 +1637,10 @@ cudaError_t launch_validate_device_inputs(const double *t, const double *freq,
     return cudaGetLastError();
 }
 
-__host__ __device__ int32_t guard_for(unsigned long long dmax)
+__host__ __device__ int32_t guard_for(unsigned long long dmax, int32_t span_rows)
 {
-    // 31 rows of drift, rounded up to whole cells, plus 2 cells of margin
-    const unsigned long long drift = 31ull * dmax;
+    // span_rows rows of drift, rounded up to whole cells, plus 2 cells of margin
+    const unsigned long long drift = (unsigned long long)span_rows * dmax;
     return (int32_t)((drift + 0xFFFFFFFFull) >> 32) + 2;
 }
 
@@ -1364,30 +1658,36 @@ size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, in
 // Kernel instantiation for a counting mode and block size: blocks of up to 512
 // threads get up to 128 registers per thread, of up to 768 threads (START
 // mode) 80, of 1024 threads 64.
-template <bool WEIGHTED, typename F>
+template <bool WEIGHTED, bool PACK, typename F>
 static auto with_transform_kernel_w(int32_t mode, int32_t nwarps, F &&f)
 {
-    if (mode == FH_MODE_DIFF)
-        return nwarps > 16 ? f(transform_kernel<FH_MODE_DIFF, 1024, WEIGHTED>)
-                           : f(transform_kernel<FH_MODE_DIFF, 512, WEIGHTED>);
-    return nwarps > 24   ? f(transform_kernel<FH_MODE_START, 1024, WEIGHTED>)
-           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 768, WEIGHTED>)
-                         : f(transform_kernel<FH_MODE_START, 512, WEIGHTED>);
+    if constexpr (!PACK) {
+        if (mode == FH_MODE_DIFF)
+            return nwarps > 16 ? f(transform_kernel<FH_MODE_DIFF, 1024, WEIGHTED, false>)
+                               : f(transform_kernel<FH_MODE_DIFF, 512, WEIGHTED, false>);
+    }
+    return nwarps > 24   ? f(transform_kernel<FH_MODE_START, 1024, WEIGHTED, PACK>)
+           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 768, WEIGHTED, PACK>)
+                         : f(transform_kernel<FH_MODE_START, 512, WEIGHTED, PACK>);
 }
-// weighted: instantiation that adds per-FFT weights (adaptive map); plain: +1
+// weighted: instantiation that adds per-FFT weights (adaptive map); plain: +1;
+// pack: 64-row slabs with two 16-bit counts per word (plain START map only)
 template <typename F>
-static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, F &&f)
+static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, bool pack, F &&f)
 {
-    return weighted ? with_transform_kernel_w<true>(mode, nwarps, f)
-                    : with_transform_kernel_w<false>(mode, nwarps, f);
+    if (pack) return with_transform_kernel_w<false, true>(FH_MODE_START, nwarps, f);
+    return weighted ? with_transform_kernel_w<true, false>(mode, nwarps, f)
+                    : with_transform_kernel_w<false, false>(mode, nwarps, f);
 }
 
 cudaError_t transform_prepare(int32_t mode, size_t smem)
 {
     cudaError_t e = cudaSuccess;
     for (int nw : {16, 24, 32})
-        for (bool wt : {false, true}) {
-            const cudaError_t r = with_transform_kernel(mode, nw, wt, [&](auto k) {
+        for (int v = 0; v < 3; ++v) {
+            const bool wt = v == 1, pk = v == 2;
+            if (pk && mode != FH_MODE_START) continue;
+            const cudaError_t r = with_transform_kernel(mode, nw, wt, pk, [&](auto k) {
                 return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem);
             });
@@ -1401,7 +1701,7 @@ int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem)
     int n = 0;
     // (both instantiations are bounded to one block of nwarps warps per SM by
     // their launch bounds; shared memory decides the rest)
-    const cudaError_t e = with_transform_kernel(mode, nwarps, false, [&](auto k) {
+    const cudaError_t e = with_transform_kernel(mode, nwarps, false, false, [&](auto k) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, nwarps * 32, smem);
     });
     return e == cudaSuccess ? n : 0;
@@ -1418,9 +1718,13 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
         const int32_t w = (tbl.job[j].tile_cells + tbl.job[j].k_over + 2 * guard) * kRows;
         hist_words = w > hist_words ? w : hist_words;
     }
-    bool weighted = false;
-    for (int j = 0; j < tbl.n_jobs; ++j) weighted = weighted || tbl.job[j].weights != nullptr;
-    with_transform_kernel(mode, nwarps, weighted, [&](auto k) {
+    bool weighted = false, pack = mode == FH_MODE_START && tbl.n_jobs > 0;
+    for (int j = 0; j < tbl.n_jobs; ++j) {
+        weighted = weighted || tbl.job[j].weights != nullptr;
+        pack = pack && tbl.job[j].slab_rows == 2 * kRows;
+    }
+    if (weighted && pack) return cudaErrorInvalidValue;  // packed counters hold plain counts only
+    with_transform_kernel(mode, nwarps, weighted, pack, [&](auto k) {
         k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u);
         return cudaSuccess;
     });
@@ -1447,6 +1751,22 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t s)
     if (a.n_dir <= 0 || a.n_sb <= 0) return cudaSuccess;
     dim3 grid(a.n_sb, a.n_dir);
     select_kernel<<<grid, kSelThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weight_bound(const int64_t *A, const int64_t *offsets, const int32_t *W,
+                                int32_t n_fft, int32_t n_dir, int64_t n_peaks, int32_t k_over,
+                                unsigned long long *bound, cudaStream_t s)
+{
+    if (n_fft <= 0 || n_dir <= 0) return cudaSuccess;
+    dim3 grid((n_fft + 255) / 256, n_dir);
+    weight_bound_kernel<<<grid, 256, 0, s>>>(A, offsets, W, n_fft, n_peaks, k_over, bound);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_bench(int32_t iters, int32_t grid, double *sink, cudaStream_t s)
+{
+    fp64_bench_kernel<<<grid, 512, 0, s>>>(iters, 0.999999, 1e-6, sink);
     return cudaGetLastError();
 }
 

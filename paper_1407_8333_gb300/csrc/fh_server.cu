@@ -65,12 +65,13 @@ struct Job {
     int32_t *d_err = nullptr;
     unsigned long long *d_dmax = nullptr;
     int32_t guard = 0;
+    int32_t rows = kRows;   // rows per slab: 64 with packed 16-bit counters, else 32
     int2 *d_win = nullptr;  // peak windows [dir][slab][tile][fft] at the job's tile
     size_t pin_off = 0;  // offset of its candidates in the batch's pinned buffer
     size_t err_off = 0;
 
     int64_t cand_count() const { return (int64_t)n_dir * n_sb * d.top_k; }
-    int32_t n_slabs() const { return (d.n_fdot + kRows - 1) / kRows; }
+    int32_t n_slabs() const { return (d.n_fdot + rows - 1) / rows; }
     int32_t n_tiles() const { return tile > 0 ? (d.n_f0 + tile - 1) / tile : 0; }
 
     // layout of the job's single device allocation
@@ -226,23 +227,25 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             e = cudaMemsetAsync(j->d_prof, 0, 8 * (size_t)j->n_dir * d.n_f0, s);
         if (e != cudaSuccess) return cuda_error(e, "job set-up");
     }
-    // One persistent transform launch per group of up to kMaxBatchJobs jobs.
-    // A launch has one guard width (the largest its jobs need) and each job
-    // keeps the tile its window table was sized for, so jobs (in order of
-    // guard) join a group only while every member's tile still fits in shared
-    // memory with the group's guard.
+    // One persistent transform launch per group of up to kMaxBatchJobs jobs of
+    // one slab height.  A launch has one guard width (the largest its jobs
+    // need) and each job keeps the tile its window table was sized for, so jobs
+    // (in order of slab height, then guard) join a group only while every
+    // member's tile still fits in shared memory with the group's guard.
     const int nwarps = kServeWarps;
     const size_t lim = (size_t)max_optin_smem(device);
     std::vector<Job *> order(batch.begin(), batch.end());
-    std::stable_sort(order.begin(), order.end(),
-                     [](const Job *x, const Job *y) { return x->guard < y->guard; });
+    std::stable_sort(order.begin(), order.end(), [](const Job *x, const Job *y) {
+        return x->rows != y->rows ? x->rows < y->rows : x->guard < y->guard;
+    });
     auto fits = [&](const Job *j, int32_t guard) {
         return transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps, guard) <= lim;
     };
     for (size_t g = 0; g < order.size();) {
         size_t g_end = g + 1;
         int32_t guard = std::max<int32_t>(2, order[g]->guard);
-        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs) {
+        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs &&
+               order[g_end]->rows == order[g]->rows) {
             const int32_t gn = std::max(guard, order[g_end]->guard);
             bool ok = true;
             for (size_t k = g; k <= g_end && ok; ++k) ok = fits(order[k], gn);
@@ -277,6 +280,8 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.dir_begin = 0;
             t.n_dir = j->n_dir;
             t.windows = j->d_win;
+            t.slab_rows = j->rows;
+            t.dense = reinterpret_cast<int32_t *>(j->d_dmax + 1);  // beside dmax, cleared with it
             t.item_begin = items;
             t.n_items = (int64_t)t.n_slabs * t.n_tiles * j->n_dir;
             items += t.n_items;
@@ -486,8 +491,12 @@ int copy_job(const fh_job_desc *jd, Job &j, int device)
     j.freq.assign(pm.freq, pm.freq + pm.n_peaks);
     j.v.assign(jd->v_over_c, jd->v_over_c + 3 * (size_t)pm.n_fft);
     j.sky.assign(jd->sky_n, jd->sky_n + 3 * (size_t)jd->n_dir);
-    // the job runs with the library's default tile for its own guard cells
-    j.guard = std::max(default_guard(j.d), host_guard(j.d, j.kt, j.t.data(), j.n_fft));
+    // the job runs with packed 64-row slabs where they apply, and the
+    // library's default tile for its own guard cells
+    const unsigned long long drift =
+        std::max(default_drift(j.d), host_drift(j.d, j.kt, j.t.data(), j.n_fft));
+    j.rows = packed_slab_rows(j.d, device, j.n_fft, drift);
+    j.guard = guard_for(drift, j.rows - 1);
     j.tile = default_tile(j.d, device, FH_MODE_START, kServeWarps, j.guard);
     j.bytes = j.layout(false);
     return FH_OK;

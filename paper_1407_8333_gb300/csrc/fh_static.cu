@@ -14,7 +14,11 @@
 //
 // The array's host-side name is only a handle: host code never passes it to a
 // kernel.  The device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and cached.
+// cudaGetSymbolAddress (with that device current) and cached for the life of
+// the process (the primary context is assumed to live as long).  This file
+// has no kernels, so it is a module of its own: under lazy module loading the
+// first lookup on a device is when the driver loads it and commits the array's
+// device memory; later calls take none.
 #include <cstring>
 #include <mutex>
 

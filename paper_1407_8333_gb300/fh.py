@@ -123,6 +123,7 @@ _SIGS = {
     "fh_search_static": ([ctypes.POINTER(fh_plan_desc), ctypes.POINTER(fh_peakmap), _P, _P, _P, _i64,
                           ctypes.POINTER(_i64), _P, _P], ctypes.c_int),
     "fh_bench_smem_atomics": ([_i32, _i32, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _P], ctypes.c_int),
+    "fh_bench_fp64": ([_i32, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _P], ctypes.c_int),
     "fh_last_error": ([], ctypes.c_char_p),
     "fh_version": ([], ctypes.c_char_p),
 }
@@ -531,6 +532,14 @@ def fh_bench_smem_atomics(variant: int = 0, iters: int = 4096, stream=None) -> t
     r, ms = _f64(0), _f64(0)
     _check(load().fh_bench_smem_atomics(int(variant), int(iters), ctypes.byref(r), ctypes.byref(ms),
                                         _stream(stream)), "fh_bench_smem_atomics")
+    return float(r.value), float(ms.value)
+
+
+def fh_bench_fp64(iters: int = 4096, stream=None) -> tuple:
+    """(binary64 operations per second, ms) of the multiply + add chains."""
+    r, ms = _f64(0), _f64(0)
+    _check(load().fh_bench_fp64(int(iters), ctypes.byref(r), ctypes.byref(ms), _stream(stream)),
+           "fh_bench_fp64")
     return float(r.value), float(ms.value)
 
 

@@ -488,6 +488,31 @@ def random_case(seed: int, n_fft: int = 20, n_bins: int = 40, k_over: int = 10,
     return inp, params
 
 
+def dense_case(seed: int, dense_ffts=(1,), n_dense: int = 12, spacing_bins: float = 0.2,
+               **kw) -> tuple:
+    """``random_case`` with the peaks of the FFTs ``dense_ffts`` replaced by
+    ``n_dense`` off-grid peaks ``spacing_bins`` apart (ascending, inside the
+    band): an accepted but non-bin-grid peakmap on which several stripes of
+    one FFT cover the same cell (the adaptive map's count bound must hold)."""
+    inp, params = random_case(seed, **kw)
+    t_fft = params["t_fft"]
+    k0 = int(round(inp.w.f_lo * t_fft))
+    parts, counts = [], []
+    for i in range(inp.t.shape[0]):
+        if i in dense_ffts:
+            start = k0 + 2.0 + 0.37 * (i % 3)
+            f = (start + spacing_bins * np.arange(n_dense)) / t_fft
+        else:
+            f = inp.freq[int(inp.offsets[i]):int(inp.offsets[i + 1])]
+        parts.append(f)
+        counts.append(f.shape[0])
+    offsets = np.zeros(inp.t.shape[0] + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    out = Inputs(w=inp.w, t=inp.t, offsets=offsets,
+                 freq=np.ascontiguousarray(np.concatenate(parts)), v=inp.v, sky=inp.sky)
+    return out, params
+
+
 # --------------------------------------------------------------------------
 # Spectra for peakmap construction (periodogram and AR average spectrum)
 # --------------------------------------------------------------------------

@@ -70,7 +70,7 @@ def check(g, o, pp, maps=True):
 CASES = [
     # seed, n_fft, n_bins, n_fdot, n_dir, frac_bits, weight scale, mode, tile, warps
     (51, 30, 80, 37, 2, 4, 2.0, 0, 96, 8),        # packed emit
-    (52, 41, 96, 45, 3, 20, 3.0, 0, 128, 16),     # counts above 2^26: unpacked emit
+    (52, 41, 96, 45, 3, 20, 6.0, 0, 128, 16),     # count bound above 2^26: unpacked emit
     (53, 25, 64, 33, 2, 8, 3.0, 1, 100, 8),       # DIFF mode
     (54, 64, 200, 64, 1, 10, 1.0, 0, 0, 0),       # library default tile
 ]
@@ -85,7 +85,9 @@ def test_weighted_maps_and_candidates_bit_exact(fh, oracle_mod, case):
     w[:, ::7] = 0.0                       # some FFTs switched off
     o = oracle_mod.search(inp, pp, want_maps=True, weights=w, frac_bits=F)
     if F == 20:
-        assert 2 * int(o["s1"].max()) >= (1 << 26)
+        bounds = [oracle_mod.count_bound(inp.offsets, o["A"][d], pp["k_over"], o["W"][d])
+                  for d in range(n_dir)]
+        assert max(bounds) >= (1 << 26)
     g = run_weighted(fh, inp, pp, w, F, mode=mode, tile=tile, warps=warps)
     check(g, o, pp)
 
@@ -155,3 +157,56 @@ def test_weighted_bench_workload_profile_and_candidates(fh, oracle_mod):
     finally:
         fh.fh_destroy_plan(plan)
     check(g, o, pp, maps=False)
+
+
+def _dense(seed):
+    return synth.dense_case(seed, dense_ffts=(1, 5), n_dense=12, spacing_bins=0.2, n_fft=24,
+                            n_bins=60, n_fdot=40, n_dir=2, p=0.3)
+
+
+@pytest.mark.parametrize("mode,F,big", [(0, 4, 1.0), (0, 16, 1000.0), (1, 8, 40.0)])
+def test_dense_off_grid_peaks_weighted_bit_exact(fh, oracle_mod, mode, F, big):
+    """Dense off-grid peaks put several stripes of one FFT on a cell, so a count
+    can exceed 2 sum(W); with a count bound below 2^31 both sides compute the
+    map, equal bit for bit (packed emit, unpacked emit above 2^26, DIFF)."""
+    inp, pp = _dense(61)
+    n_fft = inp.t.shape[0]
+    w = 1.0 + synth.uniform(61, 78, np.arange(2 * n_fft)).reshape(2, n_fft)
+    w[:, 1] = big
+    w[:, 5] = big
+    o = oracle_mod.search(inp, pp, want_maps=True, weights=w, frac_bits=F)
+    c = oracle_mod.stripe_overlap(inp.offsets, o["A"][0], pp["k_over"])
+    assert c[1] >= 5 and c[5] >= 5
+    assert int(o["maps"].max()) > 2 * int(o["W"][:, 1].max())   # more than two stripes
+    g = run_weighted(fh, inp, pp, w, F, mode=mode, tile=96, warps=8)
+    check(g, o, pp)
+
+
+def test_dense_off_grid_peaks_large_weights_refused_on_both_sides(fh, oracle_mod):
+    """The same peakmap with weights summing below 2^30 whose count bound
+    reaches 2^31: the oracle raises and fh_set_weights returns FH_ERR_RANGE,
+    and the plan still searches the same peakmap with admissible weights."""
+    import torch
+    inp, pp = _dense(62)
+    n_fft = inp.t.shape[0]
+    w = np.ones((2, n_fft))
+    w[:, 1] = float(2 ** 29 - 4096)
+    with pytest.raises(ValueError):
+        oracle_mod.search(inp, pp, weights=w, frac_bits=0)
+    plan = fh.fh_create_plan(fh.make_desc(pp, n_fft, 2, inp.n_peaks))
+    try:
+        dev = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
+        fh.fh_correct_doppler(plan, *dev)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_set_weights(plan, w, 0)
+        assert ei.value.code == fh.FH_ERR_RANGE
+        w2 = np.ones((2, n_fft))
+        w2[:, 1] = 3.0
+        fh.fh_set_weights(plan, w2, 0)
+        m = torch.empty((2, pp["n_fdot"], pp["n_f0"]), dtype=torch.int32, device="cuda")
+        fh.fh_transform(plan, 0, 2, m)
+        torch.cuda.synchronize()
+        o = oracle_mod.search(inp, pp, want_maps=True, weights=w2, frac_bits=0)
+        assert np.array_equal(m.cpu().numpy(), o["maps"])
+    finally:
+        fh.fh_destroy_plan(plan)

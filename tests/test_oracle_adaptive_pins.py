@@ -153,3 +153,58 @@ def test_search_with_unit_weights_equals_plain_search(oracle_mod):
     for k in ("maps", "pcount", "prow", "cell", "row", "count"):
         assert np.array_equal(a[k], b[k]), k
     assert np.array_equal(a["cr"].view(np.uint64), b["cr"].view(np.uint64))
+
+
+def test_stripe_overlap_by_brute_force(oracle_mod):
+    """stripe_overlap (the count bound's per-FFT factor) against its definition
+    evaluated pair by pair: the most positions of one FFT inside a half-open
+    window of K cells."""
+    inp, pp = synth.dense_case(45, dense_ffts=(1, 4), n_dense=9, spacing_bins=0.23, n_fft=7,
+                               n_bins=30, n_fdot=9, n_dir=1, p=0.4)
+    kt, A, S0, D = _steps(oracle_mod, inp, pp)
+    c = oracle_mod.stripe_overlap(inp.offsets, A[0], pp["k_over"])
+    width = pp["k_over"] << 32
+    for i in range(inp.t.shape[0]):
+        a = [int(x) for x in A[0][inp.offsets[i]:inp.offsets[i + 1]]]
+        best = max([sum(1 for y in a if x <= y < x + width) for x in a] or [0])
+        assert c[i] == best
+    assert c[1] >= 4 and c[4] >= 4          # the dense FFTs put >= 4 stripes on a cell
+
+
+def test_count_bound_holds_on_dense_off_grid_peaks(oracle_mod):
+    """Dense off-grid peaks: a cell takes more than two stripes of one FFT, yet
+    no weighted count of the direct map exceeds count_bound, and one FFT alone
+    reaches more than 2 W on some cell (so 2 sum(W) would not be a bound)."""
+    inp, pp = synth.dense_case(46, dense_ffts=(2,), n_dense=10, spacing_bins=0.25, n_fft=6,
+                               n_bins=30, n_fdot=9, n_dir=1, p=0.4)
+    kt, A, S0, D = _steps(oracle_mod, inp, pp)
+    w = (np.arange(inp.t.shape[0], dtype=np.int32) % 5 + 1) * 1000
+    m = _map(oracle_mod, inp, pp, A[0], S0, D, w, direct=True)
+    assert m.max() <= oracle_mod.count_bound(inp.offsets, A[0], pp["k_over"], w)
+    only = np.zeros_like(w)
+    only[2] = w[2]
+    m2 = _map(oracle_mod, inp, pp, A[0], S0, D, only, direct=True)
+    assert m2.max() > 2 * w[2]
+
+
+def test_search_refuses_weights_whose_count_bound_reaches_2_31(oracle_mod):
+    """Weights summing below 2^30 are refused when dense peaks of one FFT could
+    carry a count to 2^31 (the same rule as the library's fh_set_weights); the
+    same peakmap with smaller weights is searched, and its map equals direct
+    counting."""
+    inp, pp = synth.dense_case(47, dense_ffts=(1,), n_dense=12, spacing_bins=0.2, n_fft=5,
+                               n_bins=30, n_fdot=9, n_dir=1, p=0.4)
+    kt, A, S0, D = _steps(oracle_mod, inp, pp)
+    c = oracle_mod.stripe_overlap(inp.offsets, A[0], pp["k_over"])
+    assert c[1] >= 5
+    n = inp.t.shape[0]
+    big = np.ones((1, n))
+    big[0, 1] = float(2 ** 29 - 16)           # sum < 2^30, but c[1] W[1] >= 2^31
+    with pytest.raises(ValueError):
+        oracle_mod.search(inp, pp, weights=big, frac_bits=0)
+    ok = np.ones((1, n))
+    ok[0, 1] = float((2 ** 31 - 1 - 64) // int(c[1]))
+    o = oracle_mod.search(inp, pp, weights=ok, frac_bits=0, want_maps=True)
+    W = oracle_mod.quantize_weights(ok, 0)
+    assert np.array_equal(o["maps"][0], _map(oracle_mod, inp, pp, A[0], S0, D,
+                                             W[0].astype(np.int32), direct=True))

@@ -164,3 +164,53 @@ def test_destroy_with_queued_jobs(fh):
     for _ in range(3):
         _submit(fh, sv, inp, pp)
     fh.fh_server_destroy(sv)                 # cancels the queue, returns promptly
+
+
+def test_served_jobs_of_the_stream_shapes_alone_mix_oracle(fh, oracle_mod):
+    """One job of every shape the served stream draws (T_FFT 8192/4096/2048/1024 s
+    x band 0.25/0.5/1/2 Hz, K = 10, the spin-down grid of 150 days: 1169 / 585 /
+    293 / 147 rows) with 5 % of the FFTs and 1..32 directions: each job's
+    candidates are the same bytes alone and in the concurrent mix, and equal the
+    oracle's on a sampled direction (Sec. VIII: bands are searched
+    independently)."""
+    import math
+    from paper_1407_8333_gb300 import serve
+    pool = serve.make_job_pool(4, scale_fft=0.05)
+    jobs = []
+    for k, (shape, inp) in enumerate(sorted(pool.items())):
+        w = inp.w
+        n_dir = [1, 3, 7, 12, 19, 32, 5, 2][k % 8]
+        grid = synth.ecliptic_grid(max(2.0, min(synth.doppler_number(w.f_hi, w.t_fft), 60.0)))
+        idx = (7 * k + np.arange(n_dir)) % len(grid)
+        jobs.append((shape, synth.Inputs(w=w, t=inp.t, offsets=inp.offsets, freq=inp.freq,
+                                         v=inp.v, sky=np.ascontiguousarray(grid[idx]))))
+    rows = {t: jobs_pp["n_fdot"] for t, jobs_pp in
+            ((s[0], i.w.plan_params()) for s, i in jobs)}
+    assert rows == {8192.0: 1169, 4096.0: 585, 2048.0: 293, 1024.0: 147}
+    sv = fh.fh_server_create(8 << 30, 1)
+    try:
+        alone = [_wait(fh, sv, _submit(fh, sv, inp, inp.w.plan_params()), timeout=300.0)
+                 for _, inp in jobs]
+    finally:
+        fh.fh_server_destroy(sv)
+    sv = fh.fh_server_create(8 << 30, 4)
+    try:
+        ids = [_submit(fh, sv, inp, inp.w.plan_params()) for _, inp in jobs]
+        fh.fh_server_drain(sv, 300.0)
+        mix = [fh.fh_poll(sv, i)[1] for i in ids]
+        stats = [fh.fh_job_get_stats(sv, i) for i in ids]
+    finally:
+        fh.fh_server_destroy(sv)
+    assert max(s["batch_jobs"] for s in stats) >= 2    # batching happened
+    for k, ((shape, inp), a, m) in enumerate(zip(jobs, alone, mix)):
+        assert a.tobytes() == m.tobytes(), shape
+        pp = inp.w.plan_params()
+        n_dir = inp.sky.shape[0]
+        d = (3 * k) % n_dir
+        one = synth.Inputs(w=inp.w, t=inp.t, offsets=inp.offsets, freq=inp.freq, v=inp.v,
+                           sky=np.ascontiguousarray(inp.sky[[d]]))
+        o = oracle_mod.search(one, pp)
+        c = m.reshape(n_dir, -1, pp["top_k"])[d]
+        for key in ("cell", "row", "count"):
+            assert np.array_equal(c[key], o[key][0]), (shape, key)
+        assert not math.isnan(float(c["f0"][0, 0]))
