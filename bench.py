@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--dirs", type=int, default=0,
+                    help="use only the workload's first N sky directions (profiling slices)")
     ap.add_argument("--no-extras", action="store_true", help="skip batched/serving/cpu legs")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--legs", default="single_sky,maps,adaptive,batched,serving,refine,peakmap,"
@@ -69,7 +71,7 @@ def dist_env():
     return rank, world, local
 
 
-def config_of(w, extra=None):
+def config_of(w, extra=None, n_dir=None):
     pp = w.plan_params()
     cfg = {"workload": w.name,
            "description": ("T_FFT=%g s, %d FFTs (start spacing %g s), band %.2f-%.2f Hz, K=%d "
@@ -78,7 +80,7 @@ def config_of(w, extra=None):
                            (w.t_fft, w.n_fft, w.t_step, w.f_lo, w.f_hi, w.k_over, pp["n_f0"],
                             pp["n_fdot"], pp["fdot_min"],
                             pp["fdot_min"] + (pp["n_fdot"] - 1) * pp["fdot_step"], w.p_peak,
-                            w.n_dir, w.top_k, w.subband_hz)),
+                            n_dir or w.n_dir, w.top_k, w.subband_hz)),
            "l2": "flushed between timed steps (256 MiB write)"}
     if extra:
         cfg.update(extra)
@@ -359,6 +361,24 @@ def measure_step(fh, torch, w, inp, pp, dev, steps, warmup, flush, world=1, cloc
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
                 "algorithmic": "8 B/peak/direction (positions) + 8 B/cell/direction (profile) "
                                "+ 16 B/FFT per step"}
+    # the correction (a1-a3) is bound by the GPU's binary64 rate: its algorithmic
+    # operations per step over its event-timed duration, against fh_bench_fp64
+    fp64_peak, _ = fh.fh_bench_fp64(4096)
+    corr_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    fp64_ops = 4 * inp.n_peaks * n_dir + 7 * w.n_fft * n_dir + 6 * w.n_fft
+    roof_fp64 = {"bound": "fp64", "achieved": fp64_ops / (corr_ms * 1e-3) / 1e9,
+                 "peak": fp64_peak / 1e9, "unit": "Gop/s",
+                 "frac": fp64_ops / (corr_ms * 1e-3) / fp64_peak,
+                 "kernel": "correct_kernel (one launch per fh_correct_doppler call)",
+                 "algorithmic": "4 binary64 operations per (peak, direction): f r, - f0_min, "
+                                "x KT, + (0.5 - 0.5 K); 7 per (FFT, direction): v.n (3 "
+                                "multiplies, 2 adds), 1 + v.n, 1 / den; 6 per FFT: the shift "
+                                "tables; %d per step" % fp64_ops,
+                 "peak_source": "own microbenchmark fh_bench_fp64: independent IEEE multiply "
+                                "and add chains on every SM, measured in this run",
+                 "duration_ms": corr_ms,
+                 "duration_note": "CUDA events around fh_correct_doppler (one 32-byte memset "
+                                  "and the correction kernel)"}
     res = {"updates_per_step": upd_step, "ms_per_step": total_ms / steps,
            "value": upd_step * steps * world / (total_ms * 1e-3),
            "breakdown_ms": {"correct_doppler": statistics.mean(e[0].elapsed_time(e[1])
@@ -367,7 +387,8 @@ def measure_step(fh, torch, w, inp, pp, dev, steps, warmup, flush, world=1, cloc
                             "select": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
                             "transform_windows_kernel": win_ms_sum / steps,
                             "transform_kernel": kern_ms_sum / steps},
-           "roofline": roof, "roofline_hbm": roof_hbm, "gpu_launches": launches,
+           "roofline": roof, "roofline_hbm": roof_hbm, "roofline_correction": roof_fp64,
+           "gpu_launches": launches,
            "clocks": clk}
     return res, plan, cand, (tile, warps)
 
@@ -426,6 +447,9 @@ def run_ours(args):
 
     w = synth.WORKLOADS[args.workload]
     inp = synth.make_inputs(w)
+    if args.dirs > 0:
+        inp = synth.Inputs(w=w, t=inp.t, offsets=inp.offsets, freq=inp.freq, v=inp.v,
+                           sky=np.ascontiguousarray(inp.sky[:args.dirs]))
     pp = w.plan_params()
     dev = [torch.from_numpy(x).cuda() for x in (inp.t, inp.offsets, inp.freq, inp.v, inp.sky)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -440,12 +464,13 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "i64/i32 (f64 Doppler)",
            "data": "synthetic (seeded SplitMix64 peakmap, paper-shaped)",
-           "config": config_of(w),
+           "config": config_of(w, n_dir=inp.sky.shape[0]),
            "inputs": "device-resident" + (" (larger than L2)" if inp.n_peaks * 8 > (256 << 20)
                                           else ""),
            "parallelism": "replicas" if world > 1 else "single GPU",
            "breakdown_ms": m["breakdown_ms"], "roofline": m["roofline"],
-           "roofline_hbm": m["roofline_hbm"], "clocks": m["clocks"],
+           "roofline_hbm": m["roofline_hbm"], "roofline_correction": m["roofline_correction"],
+           "clocks": m["clocks"],
            "gpu_launches": m["gpu_launches"], "e2e": e2e}
 
     legs = set(args.legs.split(","))
@@ -515,6 +540,7 @@ def summary_of(out):
     return {"workload": out["config"]["workload"], "updates_per_s": out["value"],
             "ms_per_step": out["ms_per_step"], "transform_frac": r.get("frac"),
             "transform_ms_per_launch": r.get("duration_ms"),
+            "correction_fp64_frac": g(out, "roofline_correction", "frac"),
             "e2e_updates_per_s": g(out, "e2e", "value"),
             "single_sky_updates_per_s": g(out, "single_sky", "value"),
             "single_sky_transform_frac": g(out, "single_sky", "roofline", "frac"),

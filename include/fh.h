@@ -252,10 +252,10 @@ int fh_sync(fh_plan plan, void *stream);
 /* Time fh_transform over its launch shapes on the current directions (at most
  * 8 of them: the per-item work does not depend on the count) and keep the
  * fastest in the plan; returns its tile width and block warps.  The shapes
- * are: rows per slab (64 with two 16-bit counts per shared word, where the
- * plain START map allows it, and 32), block warps (16, 24, 32) and tile
- * widths up to the widest that fits shared memory with that slab's guard
- * cells.  Synchronises.  Results are cached per process by grid shape (GPU
+ * are: direction pairs (two directions with one 16-bit count each per shared
+ * word, where the plain START map allows it) or single directions, block
+ * warps (16, 20, 24, 32) and tile widths up to the widest that fits shared
+ * memory with the guard cells of that choice.  Synchronises.  Results are cached per process by grid shape (GPU
  * model, counting mode, weighting, n_f0, n_fdot, K, T_FFT, N_t, n_dir); when
  * the environment variable FH_AUTOTUNE_CACHE names a file, they are also
  * read from and written to it (JSON, one entry per line), so later processes

@@ -133,14 +133,17 @@ int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_
     return guard_for(host_drift(d, kt, t, n_fft));
 }
 
-int32_t packed_slab_rows(const fh_plan_desc &d, int device, int32_t n_fft, unsigned long long drift)
+int32_t pair_delta(const fh_plan_desc &d) { return 2 * d.k_over + 4; }
+
+bool pairs_apply(const fh_plan_desc &d, int device, int32_t n_fft, int32_t n_dir,
+                 unsigned long long drift)
 {
-    if (n_fft <= 0 || n_fft >= 65536 || (int64_t)d.k_over * n_fft >= ((int64_t)1 << 25))
-        return kRows;
-    const int32_t g64 = guard_for(drift, 2 * kRows - 1);
-    if (transform_smem_bytes(256, d.k_over, FH_MODE_START, 32, g64) > (size_t)max_optin_smem(device))
-        return kRows;
-    return 2 * kRows;
+    if (n_dir < 2 || n_fft <= 0 || n_fft >= 65536 ||
+        (int64_t)d.k_over * n_fft >= ((int64_t)1 << 25))
+        return false;
+    const int32_t g = guard_for(drift) + pair_delta(d);
+    return transform_smem_bytes(256, d.k_over, FH_MODE_START, 32, g) <=
+           (size_t)max_optin_smem(device);
 }
 
 int validate_desc(const fh_plan_desc &d)
@@ -228,11 +231,13 @@ struct fh_plan_s {
     unsigned long long *dmax = nullptr;  // largest |D_i| of the current peakmap (in err's block)
     int32_t *dense = nullptr;            // set by the window pre-pass: an FFT with two peaks
                                          // in one cell (in err's block)
-    int2 *win = nullptr;                 // peak windows of the directions being transformed
+    int32_t *unit_delta = nullptr;       // per direction pair of a group: the largest distance
+                                         // between a peak's two cells (window pre-pass)
+    uint32_t *win = nullptr;             // peak windows of the directions being transformed
     size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path (32 rows)
     unsigned long long drift = 0;        // bound of max |D_i| the guards are sized for
-    int32_t slab_pref = 0;               // 0: packed 64-row slabs where they apply; 32: never
+    int32_t slab_pref = 0;               // 0: direction pairs where they apply; 1: never
     int32_t n_fft = -1;
     int64_t n_peaks = 0;
     int32_t n_dir = 0;
@@ -255,7 +260,7 @@ struct fh_plan_s {
         for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
         tev.clear();
         void *bufs[] = {t,    freq, v,   sky,  offsets, offsets_raw, S0, D,
-                        A,    profile, cand, err, win,  wq,  ws};  // dmax lives in err's block
+                        A,    profile, cand, err, win,  wq,  ws, unit_delta};  // dmax: in err's block
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -268,6 +273,7 @@ struct fh_plan_s {
         win = nullptr;
         win_bytes = 0;
         wq = nullptr;
+        unit_delta = nullptr;
         ws = nullptr;
     }
 };
@@ -457,7 +463,8 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                   {(void **)&p->freq, s.freq},     {(void **)&p->v, s.v},
                   {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
                   {(void **)&p->profile, s.profile}, {(void **)&p->cand, s.cand},
-                  {(void **)&p->err, kErrWordsBytes}};
+                  {(void **)&p->err, kErrWordsBytes},
+                  {(void **)&p->unit_delta, 4 * ((int64_t)desc->max_dir / 2 + 1)}};
     for (auto &a : allocs) {
         e = cudaMalloc(a.ptr, (size_t)std::max<int64_t>(a.bytes, 16));
         if (e != cudaSuccess) {
@@ -805,20 +812,17 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     return FH_OK;
 }
 
-// Rows per slab for the plan's current peakmap: 64 (packed 16-bit counters)
-// for a plain START map whose stripe-start counts fit 16 bits by its size
-// (n_fft < 2^16; the window pre-pass checks the spacing of the peaks) and
-// whose counts keep the packed reduction key below 2^31 (K n_fft < 2^25), when
-// a tile still fits shared memory with the 63-row guard; else 32.
-static int32_t plan_slab_rows(fh_plan p, int32_t pref)
+// Direction pairs for n_dir directions of the plan's current peakmap (pref 0:
+// where they apply; 1: never).
+static bool plan_pairs(fh_plan p, int32_t n_dir, int32_t pref)
 {
-    if (pref == kRows || p->mode != FH_MODE_START || p->weighted) return kRows;
-    return packed_slab_rows(p->d, p->device, p->n_fft, p->drift);
+    if (pref == 1 || p->mode != FH_MODE_START || p->weighted) return false;
+    return pairs_apply(p->d, p->device, p->n_fft, n_dir, p->drift);
 }
 
-static int32_t plan_guard(fh_plan p, int32_t rows)
+static int32_t plan_guard(fh_plan p, bool pairs)
 {
-    return rows == 2 * kRows ? guard_for(p->drift, 2 * kRows - 1) : p->guard;
+    return pairs ? p->guard + pair_delta(p->d) : p->guard;
 }
 
 static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
@@ -827,8 +831,8 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
 {
     const fh_plan_desc &d = p->d;
     // keep the tile's counters within shared memory with this plan's guard cells
-    const int32_t rows = plan_slab_rows(p, slab_pref);
-    const int32_t guard = plan_guard(p, rows);
+    const bool pairs = schedule != FH_SCHED_PLAIN && plan_pairs(p, n_dir, slab_pref);
+    const int32_t guard = plan_guard(p, pairs);
     const int32_t wmax = default_tile(d, p->device, p->mode, nwarps, guard);
     if (tile > wmax) tile = wmax;
     const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps, guard);
@@ -857,23 +861,30 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.n_fdot = d.n_fdot;
     job.k_over = d.k_over;
     job.tile_cells = tile;
-    job.slab_rows = rows;
+    job.dir_pairs = pairs ? 1 : 0;
     job.dense = p->dense;
-    job.n_slabs = (d.n_fdot + rows - 1) / rows;
+    job.unit_delta = p->unit_delta;
+    job.delta_alloc = pair_delta(d);
+    job.n_slabs = (d.n_fdot + kRows - 1) / kRows;
     job.n_tiles = (d.n_f0 + tile - 1) / tile;
     const int64_t per_dir = (int64_t)job.n_slabs * job.n_tiles;
     int bps = transform_blocks_per_sm(p->mode, nwarps, smem);
     if (bps < 1) return set_error(FH_ERR_CUDA, "transform kernel cannot be resident");
-    // peak windows of a group of directions (bounded table), then the transform
-    const size_t per_dir_win = sizeof(int2) * (size_t)per_dir * (size_t)std::max(1, p->n_fft);
+    // peak windows of a group of directions (bounded table), then the transform;
+    // with direction pairs the table and the work items are per pair, and a group
+    // holds whole pairs
+    const size_t per_dir_win = sizeof(uint32_t) * (size_t)per_dir * (size_t)std::max(1, p->n_fft);
     const size_t win_cap = std::max(per_dir_win, (size_t)1 << 32);
-    // (the windows grid has one block row per direction: at most 65535)
+    const int32_t per_unit = pairs ? 2 : 1;
+    // (the windows grid has one block row per unit: at most 65535)
     const size_t zcap = 65535;
-    const int32_t group = schedule == FH_SCHED_PLAIN
-                              ? 1
-                              : (int32_t)std::max<size_t>(1, std::min<size_t>(
-                                    std::min<size_t>((size_t)n_dir, zcap), win_cap / per_dir_win));
-    const size_t need = per_dir_win * (size_t)group;
+    int32_t group = schedule == FH_SCHED_PLAIN
+                        ? 1
+                        : (int32_t)std::max<size_t>(1, std::min<size_t>(
+                              std::min<size_t>((size_t)n_dir, zcap),
+                              per_unit * (win_cap / per_dir_win)));
+    if (pairs && group < n_dir) group = std::max(2, group & ~1);
+    const size_t need = per_dir_win * (size_t)((group + per_unit - 1) / per_unit);
     if (need > p->win_bytes) {
         if (p->win) cudaFree(p->win);
         p->win = nullptr;
@@ -893,8 +904,12 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
         job.n_dir = gn;
         job.maps = out_maps ? out_maps + (int64_t)g0 * d.n_fdot * d.n_f0 : nullptr;
         job.item_begin = 0;
-        job.n_items = per_dir * gn;
+        job.n_items = per_dir * ((gn + per_unit - 1) / per_unit);
         job.windows = p->win;
+        if (pairs) {
+            e = cudaMemsetAsync(p->unit_delta, 0, sizeof(int32_t) * (size_t)((gn + 1) / 2), s);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(pair distances)");
+        }
         cudaEvent_t *ev = nullptr;
         if (p->timing && !p->tev.empty()) {
             ev = &p->tev[3 * (size_t)(p->tev_next % kTimingSlots)];
@@ -1005,12 +1020,12 @@ int fh_select_candidates(fh_plan p, int32_t dir_begin, int32_t n_dir, fh_candida
 
 namespace {
 
-// Autotuner results: (tile width, block warps, rows per slab) per grid shape,
+// Autotuner results: (tile width, block warps, direction pairs) per grid shape,
 // kept in memory for the process and, when FH_AUTOTUNE_CACHE names a file, in
 // that JSON file (one entry per line, rewritten atomically by rename) so that
 // later processes on the same GPU model reuse them.
 struct TuneChoice {
-    int32_t tile = 0, warps = 0, rows = 0;
+    int32_t tile = 0, warps = 0, pairs = 0;
     double ms = 0.0;
 };
 std::mutex g_tune_mu;
@@ -1037,14 +1052,14 @@ void tune_load_locked()
         TuneChoice c;
         const char *t = std::strstr(ke, "\"tile_cells\": ");
         const char *w = std::strstr(ke, "\"block_warps\": ");
-        const char *r = std::strstr(ke, "\"slab_rows\": ");
+        const char *r = std::strstr(ke, "\"dir_pairs\": ");
         const char *m = std::strstr(ke, "\"ms\": ");
         if (!t || !w || !r || std::sscanf(t + 14, "%d", &c.tile) != 1 ||
-            std::sscanf(w + 15, "%d", &c.warps) != 1 || std::sscanf(r + 13, "%d", &c.rows) != 1)
+            std::sscanf(w + 15, "%d", &c.warps) != 1 || std::sscanf(r + 13, "%d", &c.pairs) != 1)
             continue;
         if (m) std::sscanf(m + 6, "%lf", &c.ms);
-        if (c.tile < 32 || (c.warps != 16 && c.warps != 24 && c.warps != 32) ||
-            (c.rows != kRows && c.rows != 2 * kRows))
+        if (c.tile < 32 || (c.warps != 16 && c.warps != 20 && c.warps != 24 && c.warps != 32) ||
+            (c.pairs != 0 && c.pairs != 1))
             continue;  // not one of ours: ignored
         g_tune[std::string(k, ke)] = c;
     }
@@ -1063,8 +1078,8 @@ void tune_store_locked()
     for (const auto &e : g_tune) {
         std::fprintf(f,
                      "{\"key\": \"%s\", \"tile_cells\": %d, \"block_warps\": %d, "
-                     "\"slab_rows\": %d, \"ms\": %.6f}%s\n",
-                     e.first.c_str(), e.second.tile, e.second.warps, e.second.rows, e.second.ms,
+                     "\"dir_pairs\": %d, \"ms\": %.6f}%s\n",
+                     e.first.c_str(), e.second.tile, e.second.warps, e.second.pairs, e.second.ms,
                      ++k < g_tune.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
@@ -1102,7 +1117,7 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     auto apply = [&](const TuneChoice &c) {
         p->tile_cells = c.tile;
         p->block_warps = c.warps;
-        p->slab_pref = c.rows;
+        p->slab_pref = c.pairs ? 0 : 1;
         if (tile_cells) *tile_cells = p->tile_cells;
         if (block_warps) *block_warps = p->block_warps;
     };
@@ -1115,37 +1130,38 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
             return FH_OK;
         }
     }
-    // candidates: rows per slab (packed 64 where it applies, 32), block warps,
-    // tile widths up to the widest that fits with that slab's guard cells
+    // candidates: direction pairs (where they apply) or single directions, block
+    // warps, tile widths up to the widest that fits with that choice's guard cells
     const int lim = max_optin_smem(p->device);
     std::vector<TuneChoice> cands;
-    const int32_t rows_auto = plan_slab_rows(p, 0);
-    for (int32_t rows : {rows_auto, (int32_t)kRows}) {
-        if (rows == kRows && rows_auto == kRows && !cands.empty()) break;
-        const int32_t guard = plan_guard(p, rows);
-        for (int nw : {24, 32, 16}) {
-            if (nw == 24 && p->mode == FH_MODE_DIFF) continue;  // DIFF kernels: 512 / 1024 threads
+    const int32_t nt = std::min<int32_t>(n_dir, 8);
+    const bool pairs_ok = plan_pairs(p, nt, 0);
+    for (int pr : {1, 0}) {
+        if (pr && !pairs_ok) continue;
+        const int32_t guard = plan_guard(p, pr != 0);
+        for (int nw : {24, 20, 32, 16}) {
+            // DIFF kernels: 512 / 1024 threads
+            if ((nw == 24 || nw == 20) && p->mode == FH_MODE_DIFF) continue;
             const int32_t wmax = default_tile(d, p->device, p->mode, nw, guard);
             for (int32_t w : {wmax, 1280, 1024, 768}) {
                 if (w > wmax || w > d.n_f0) continue;
                 if (transform_smem_bytes(w, d.k_over, p->mode, nw, guard) > (size_t)lim) continue;
                 bool dup = false;
-                for (const auto &c : cands) dup = dup || (c.tile == w && c.warps == nw && c.rows == rows);
-                if (!dup) cands.push_back({w, nw, rows, 0.0});
+                for (const auto &c : cands) dup = dup || (c.tile == w && c.warps == nw && c.pairs == pr);
+                if (!dup) cands.push_back({w, nw, pr, 0.0});
             }
         }
     }
-    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps, kRows, 0.0});
+    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps, 0, 0.0});
     // timed on at most 8 of the directions (one window group): the per-item
     // work, and so the best tile, does not depend on how many there are
-    const int32_t nt = std::min<int32_t>(n_dir, 8);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     TuneChoice pick = cands[0];
     for (auto &c : cands) {
-        const int32_t pref = c.rows == kRows ? kRows : 0;
+        const int32_t pref = c.pairs ? 0 : 1;
         rc = run_transform(p, dir_begin, nt, nullptr, c.tile, c.warps, FH_SCHED_BATCHED, s, pref);
         if (rc) break;
         float ms = 0.f;

@@ -18,6 +18,9 @@ namespace fh {
 constexpr int kRows = 32;
 constexpr int kMaxBatchJobs = 12;
 constexpr int64_t kFixedLimit = int64_t(1) << 28;  // |cells| bound for 32.32 fixed point
+// window table entry of an FFT whose window start or count does not fit 16 bits:
+// the transform looks that window up by binary search instead
+constexpr uint32_t kWinLookup = 0xFFFFFFFFu;
 
 // error bits written by the device-side input checks
 enum : int32_t { kErrUnsorted = 1, kErrRange = 2, kErrInvalid = 4, kErrCsr = 8 };
@@ -37,13 +40,20 @@ struct TransformJob {
     const int32_t *weights;  // nullable (plain map): adaptive integer weights, [dir][n_fft]
                              // (absolute directions); each update adds its FFT's weight
     int64_t count_bound;     // no count of the job's maps exceeds it
-    const int2 *windows;     // nullable: precomputed peak windows (first, end) per
-                             // [dir - dir_begin][slab][tile][fft]; else looked up
+    const uint32_t *windows; // nullable: precomputed peak windows per
+                             // [dir - dir_begin][slab][tile][fft], each the first peak
+                             // relative to the FFT's first (low 16 bits) and the count
+                             // (high 16 bits), or kWinLookup: looked up (binary search)
     int32_t *dense;          // nullable: set by the window pre-pass when some FFT has two
                              // peaks within one cell (the packed counters then do not
-                             // apply: the job's 64-row slabs run as two 32-row passes)
-    int32_t slab_rows;       // rows per slab: 32 (0 means 32), or 64 for the packed
-                             // layout (plain START map: every job of a launch alike)
+                             // apply: each direction of a pair is walked on its own)
+    int32_t dir_pairs;       // 1: items cover directions 2u and 2u + 1 with two 16-bit
+                             // counts per shared word (plain START map, every job of a
+                             // launch alike); the window table is per pair
+    int32_t *unit_delta;     // (dir_pairs) per pair, the largest cell distance between a
+                             // peak's two positions (+2), from the window pre-pass
+    int32_t delta_alloc;     // (dir_pairs) the part of the guard that holds that distance;
+                             // a pair beyond it takes the clamped walk
     int64_t n_peaks;
     int64_t item_begin;      // first work item of this job in the launch
     int64_t n_items;         // n_dir * n_slabs * n_tiles
@@ -130,7 +140,7 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
 int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem);
 // Peak windows of every (direction, slab, tile, FFT) of a job, written to
 // job.windows (the job's other fields as for the transform).
-cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t s);
+cudaError_t launch_windows(const TransformJob &job, uint32_t *windows, cudaStream_t s);
 cudaError_t launch_select(const SelectArgs &a, cudaStream_t s);
 // Adaptive map's count bound: bound[d] += sum_i W[d][i] c_{d,i}, c_{d,i} = the
 // most positions of FFT i (direction d) inside a half-open window of K cells
@@ -186,13 +196,17 @@ int32_t host_guard(const fh_plan_desc &d, double kt, const double *t, int32_t n_
 // the drift bounds behind those guards: max |D_i| in 32.32 cells per row
 unsigned long long default_drift(const fh_plan_desc &d);
 unsigned long long host_drift(const fh_plan_desc &d, double kt, const double *t, int32_t n_fft);
-// Rows per slab of a plain START map: 64 (packed 16-bit counters) when its
-// stripe-start counts fit 16 bits by its size (n_fft < 2^16; the window
-// pre-pass checks the peaks' spacing), its counts keep the packed reduction
-// key below 2^31 (K n_fft < 2^25) and a tile fits with the 63-row guard of
-// drift bound `drift`; else 32.
-int32_t packed_slab_rows(const fh_plan_desc &d, int device, int32_t n_fft,
-                         unsigned long long drift);
+// Whether a plain START map of n_dir directions may pair them (two 16-bit
+// counts per shared word): its stripe-start counts fit 16 bits by its size
+// (n_fft < 2^16; the window pre-pass checks the peaks' spacing), its counts
+// keep the reduction key below 2^31 (K n_fft < 2^25) and a tile fits with the
+// guard of drift bound `drift` plus the pair allowance pair_delta(d).
+bool pairs_apply(const fh_plan_desc &d, int device, int32_t n_fft, int32_t n_dir,
+                 unsigned long long drift);
+// Cells of guard kept for the distance between a peak's positions in the two
+// directions of a pair: neighbouring directions of a sky grid at the Doppler
+// resolution differ by about one input bin (K cells); 2 K + 4 leaves room.
+int32_t pair_delta(const fh_plan_desc &d);
 int validate_desc(const fh_plan_desc &d);
 // host-memory inputs: CSR, ordering, finiteness and the 32.32 fixed-point range
 int validate_host_inputs(const fh_plan_desc &d, double kt, const fh_peakmap *pm, const double *v,

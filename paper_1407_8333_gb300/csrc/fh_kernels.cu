@@ -415,23 +415,25 @@ __device__ __forceinline__ void lookup_window(const int64_t *__restrict__ Ad,
 // positions whose stripe reaches the tile on some row of the slab.  The
 // window is a superset of the peaks that reach the tile, by less than one cell
 // on each side; those extra peaks reach only guard cells (the transform's
-// guard keeps a margin of two cells), so they change no count.
+// guard keeps a margin of two cells), so they change no count.  For a pair of
+// directions (PAIR) the entry is the union, as one index range, of the two
+// directions' windows.
 //
-// A block takes 8 FFTs of one direction; warp w copies FFT w's peak cells
-// (ascending) into shared memory once, between one sentinel on each side (an
-// FFT with more than kWinPeaks - 2 peaks is read from global memory, with
-// bounds checks).  Lane l of warp w then takes FFT l mod 8 and tiles
-// 4 w + l / 8 + 32 m (M per pass, M = 1 .. 3 from the tile count, so that the
-// per-slab work -- the 64-bit bounds, the branches -- is shared by M entries
-// and the M searches of a slab are independent), and walks the slabs in
-// order: the first slab's bounds come from a binary search, each later one
-// from a step in the direction of its FFT's drift D (both bounds move
-// monotonically with the slab, by 32 D).  A warp's 32 entries of a slab are
-// 4 tiles x 8 consecutive FFTs, i.e. four 64-byte runs of the [slab][tile][FFT]
-// table the transform reads with one 8-byte load per lane, so each warp
-// writes its own runs and the slab loop has no barrier.
-// grid (ceil(n_fft / 8), n_dir), 256 threads.
-constexpr int kWinPeaks = 1024;
+// A block takes 8 FFTs of one unit (a direction, or a pair of them): warp w
+// copies FFT w's peak cells (ascending) of each direction into shared memory
+// once, between one sentinel on each side, four loads per lane in flight (an
+// FFT with more than kPeaks - 2 peaks is read from global memory, with bounds
+// checks).  Lane l of warp w then takes FFT l mod 8 and tiles 4 w + l / 8 +
+// 32 m (M per pass, M = 1 .. 3 from the tile count, so that the per-slab work
+// -- the 64-bit bounds, the branches -- is shared by M entries and the M
+// searches of a slab are independent), and walks the slabs in order: the
+// first slab's bounds come from a binary search, each later one from a step in
+// the direction of its FFT's drift D (both bounds move monotonically with the
+// slab, by 32 D; D does not depend on the direction).  A warp's 32 entries of a
+// slab are 4 tiles x 8 consecutive FFTs, i.e. four 32-byte runs of the
+// [slab][tile][FFT] table, so each warp writes its own runs and the slab loop
+// has no barrier.
+// grid (ceil(n_fft / 8), units), 256 threads.
 constexpr int kWinPad = 1;
 constexpr int kWinMaxM = 3;
 __device__ __forceinline__ int lower_bound_cell(const int32_t *a, int n, int x)
@@ -470,21 +472,25 @@ __device__ __forceinline__ int step_down(const int32_t *a, int q, int x)
     return q;
 }
 
-template <int M>
+template <int M, bool PAIR>
 __global__ void __launch_bounds__(256, 4)
-windows_kernel(const TransformJob J, int2 *__restrict__ windows)
+windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
 {
     constexpr int kTiles = 32 * M;  // tiles per pass
+    constexpr int ND = PAIR ? 2 : 1;
+    // staged peaks per FFT and direction (the static shared memory holds 48 KB)
+    constexpr int kPeaks = PAIR ? 736 : 1024;
     // rows padded by one word: lanes on different FFTs fall on different banks
-    __shared__ int32_t cell_s[8][kWinPeaks + 1];
+    __shared__ int32_t cell_s[ND][8][kPeaks + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d_rel = blockIdx.y;
-    const int d_abs = J.dir_begin + d_rel;
-    const int64_t *Ad = J.A + (int64_t)d_abs * J.n_peaks;
-    {
-        // the transform merges into this direction's profile by atomicMax from 0:
-        // the blocks of the direction clear it here, a strided slice each
-        uint64_t *pr = J.profile + (int64_t)d_abs * J.n_f0;
+    const int unit = blockIdx.y;
+    const int nd = PAIR ? min(2, J.n_dir - 2 * unit) : 1;  // directions of the unit
+    const int d_first = J.dir_begin + (PAIR ? 2 * unit : unit);
+    const int64_t *A0 = J.A + (int64_t)d_first * J.n_peaks;
+    // the transform merges into each direction's profile by atomicMax from 0:
+    // the blocks of the unit clear it here, a strided slice each
+    for (int di = 0; di < nd; ++di) {
+        uint64_t *pr = J.profile + (int64_t)(d_first + di) * J.n_f0;
         for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < J.n_f0;
              k += (int64_t)gridDim.x * blockDim.x)
             pr[k] = 0;
@@ -498,26 +504,47 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
         const bool ls = is < J.n_fft;
         const int64_t os = ls ? J.offsets[is] : 0;
         const int ns = ls ? (int)(J.offsets[is + 1] - os) : 0;
-        const bool stage = ns + 2 * kWinPad <= kWinPeaks;
-        int32_t *c = &cell_s[warp][kWinPad];
-        const int64_t *As = Ad + os;
+        const bool stage = ns + 2 * kWinPad <= kPeaks;
+        bool close = false;
         if (stage || J.dense != nullptr) {
-            bool close = false;
-            int carry = 0;
-            for (int k0 = 0; k0 < ns; k0 += 32) {
-                const int k = k0 + lane;
-                const int cur = k < ns ? global_cell(As, k) : 0;
-                if (stage && k < ns) c[k] = cur;
-                int prev = __shfl_up_sync(kFull, cur, 1);
-                if (lane == 0) prev = carry;
-                if (k > 0 && k < ns && (int64_t)cur - (int64_t)prev <= 1) close = true;
-                carry = __shfl_sync(kFull, cur, 31);
+            for (int di = 0; di < nd; ++di) {
+                const int64_t *As = A0 + (int64_t)di * J.n_peaks + os;
+                int32_t *c = &cell_s[PAIR ? di : 0][warp][kWinPad];
+                int carry = 0;
+                for (int k0 = 0; k0 < ns; k0 += 128) {
+                    int cur[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int k = k0 + 32 * r + lane;
+                        cur[r] = k < ns ? global_cell(As, k) : 0;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int k = k0 + 32 * r + lane;
+                        if (stage && k < ns) c[k] = cur[r];
+                        int prev = __shfl_up_sync(kFull, cur[r], 1);
+                        if (lane == 0) prev = carry;
+                        if (k > 0 && k < ns && (int64_t)cur[r] - (int64_t)prev <= 1) close = true;
+                        carry = __shfl_sync(kFull, cur[r], 31);
+                    }
+                }
+                if (stage && lane < kWinPad) {
+                    c[-1 - lane] = INT_MIN;
+                    c[ns + lane] = INT_MAX;
+                }
             }
             if (J.dense != nullptr && __any_sync(kFull, close) && lane == 0) atomicOr(J.dense, 1);
         }
-        if (stage && lane < kWinPad) {
-            c[-1 - lane] = INT_MIN;
-            c[ns + lane] = INT_MAX;
+        if (PAIR && nd == 2 && J.unit_delta != nullptr && lane == 0 && ns > 0) {
+            // the pair's largest distance between a peak's two cells: the positions
+            // differ by f (r_b - r_a) KT (+ rounding), linear in f, so it is largest
+            // at the FFT's first or last peak (ascending frequencies); 2 cells of
+            // rounding margin
+            const int64_t *Aa = A0 + os, *Ab = Aa + J.n_peaks;
+            const int64_t d0 = (int64_t)global_cell(Ab, 0) - global_cell(Aa, 0);
+            const int64_t d1 = (int64_t)global_cell(Ab, ns - 1) - global_cell(Aa, ns - 1);
+            const int64_t dm = max(d0 < 0 ? -d0 : d0, d1 < 0 ? -d1 : d1) + 2;
+            atomicMax(J.unit_delta + unit, (int32_t)min(dm, (int64_t)INT_MAX));
         }
     }
     __syncthreads();
@@ -528,21 +555,19 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
     const bool live = i < J.n_fft;
     const int64_t o0 = live ? J.offsets[i] : 0;
     const int n = live ? (int)(J.offsets[i + 1] - o0) : 0;
-    const bool staged = n + 2 * kWinPad <= kWinPeaks;
-    const int64_t *Ai = Ad + o0;
-    const int32_t *cs = &cell_s[f][kWinPad];
+    const bool staged = n + 2 * kWinPad <= kPeaks;
     const int64_t dv = live ? J.D[i] : 0;
     const int64_t s0 = live ? J.S0[i] : 0;
     const int K = J.k_over, W = J.tile_cells;
     const int64_t nf = J.n_fft;
     const int64_t slab_stride = (int64_t)J.n_tiles * nf;
-    int2 *out = windows + (int64_t)d_rel * J.n_slabs * slab_stride;
+    uint32_t *out = windows + (int64_t)unit * J.n_slabs * slab_stride;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kTiles) {
         const int nt = min(kTiles, J.n_tiles - t0);
         // the lane's tiles: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
-        int blo[M], bhi[M], qa[M], qb[M];
+        int blo[M], bhi[M], qa[ND][M], qb[ND][M];
         bool ok[M];
-        int2 *dst[M];
+        uint32_t *dst[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int tt = tq + 32 * m;
@@ -550,14 +575,17 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
             const int b0 = (t0 + tt) * W;
             blo[m] = b0 - K + 1;
             bhi[m] = b0 + min(W, J.n_f0 - b0);
-            qa[m] = 0;
-            qb[m] = 0;
+#pragma unroll
+            for (int di = 0; di < ND; ++di) {
+                qa[di][m] = 0;
+                qb[di][m] = 0;
+            }
             dst[m] = out + (int64_t)(t0 + tt) * nf + i;
         }
-        // bounds of slab j0 = RS s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
+        // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
         // ceil((S0 + j0 D + max(0, (R-1) D)) / 2^32) (+ the tile's terms), kept
-        // as 64-bit sums that advance by RS D per full slab
-        const int RS = J.slab_rows == 2 * kRows ? 2 * kRows : kRows;
+        // as 64-bit sums that advance by 32 D per full slab
+        constexpr int RS = kRows;
         const int64_t span_full = (int64_t)(RS - 1) * dv;
         int64_t u = s0 + (span_full < 0 ? span_full : 0);
         int64_t w = s0 + (span_full > 0 ? span_full : 0);
@@ -572,47 +600,71 @@ windows_kernel(const TransformJob J, int2 *__restrict__ windows)
             }
             const int ul = (int)(u >> 32);
             const int wh = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0);
-            if (!staged) {
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    if (!ok[m]) continue;
-                    const int xl = ul + blo[m], xh = wh + bhi[m];
-                    int qa_m = qa[m], qb_m = qb[m];
-                    if (slab == 0) {
-                        qa_m = lower_bound_cell_g(Ai, n, xl);
-                        qb_m = lower_bound_cell_g(Ai, n, xh);
-                    } else {
-                        while (qa_m < n && global_cell(Ai, qa_m) < xl) ++qa_m;
-                        while (qa_m > 0 && global_cell(Ai, qa_m - 1) >= xl) --qa_m;
-                        while (qb_m < n && global_cell(Ai, qb_m) < xh) ++qb_m;
-                        while (qb_m > 0 && global_cell(Ai, qb_m - 1) >= xh) --qb_m;
+            for (int di = 0; di < ND; ++di) {
+                if (di >= nd) break;
+                const int32_t *cs = &cell_s[di][f][kWinPad];
+                const int64_t *Ai = A0 + (int64_t)di * J.n_peaks + o0;
+                if (!staged) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        if (!ok[m]) continue;
+                        const int xl = ul + blo[m], xh = wh + bhi[m];
+                        int qa_m = qa[di][m], qb_m = qb[di][m];
+                        if (slab == 0) {
+                            qa_m = lower_bound_cell_g(Ai, n, xl);
+                            qb_m = lower_bound_cell_g(Ai, n, xh);
+                        } else {
+                            while (qa_m < n && global_cell(Ai, qa_m) < xl) ++qa_m;
+                            while (qa_m > 0 && global_cell(Ai, qa_m - 1) >= xl) --qa_m;
+                            while (qb_m < n && global_cell(Ai, qb_m) < xh) ++qb_m;
+                            while (qb_m > 0 && global_cell(Ai, qb_m - 1) >= xh) --qb_m;
+                        }
+                        qa[di][m] = qa_m;
+                        qb[di][m] = qb_m;
                     }
-                    qa[m] = qa_m;
-                    qb[m] = qb_m;
-                }
-            } else if (slab == 0) {
-                // every lane searches (the sentinels bound the tiles past the last one)
+                } else if (slab == 0) {
+                    // every lane searches (the sentinels bound the tiles past the last one)
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    qa[m] = lower_bound_cell(cs, n, ul + blo[m]);
-                    qb[m] = lower_bound_cell(cs, n, wh + bhi[m]);
-                }
-            } else if (dv >= 0) {
+                    for (int m = 0; m < M; ++m) {
+                        qa[di][m] = lower_bound_cell(cs, n, ul + blo[m]);
+                        qb[di][m] = lower_bound_cell(cs, n, wh + bhi[m]);
+                    }
+                } else if (dv >= 0) {
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    qa[m] = step_up(cs, qa[m], ul + blo[m]);
-                    qb[m] = step_up(cs, qb[m], wh + bhi[m]);
-                }
-            } else {
+                    for (int m = 0; m < M; ++m) {
+                        qa[di][m] = step_up(cs, qa[di][m], ul + blo[m]);
+                        qb[di][m] = step_up(cs, qb[di][m], wh + bhi[m]);
+                    }
+                } else {
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    qa[m] = step_down(cs, qa[m], ul + blo[m]);
-                    qb[m] = step_down(cs, qb[m], wh + bhi[m]);
+                    for (int m = 0; m < M; ++m) {
+                        qa[di][m] = step_down(cs, qa[di][m], ul + blo[m]);
+                        qb[di][m] = step_down(cs, qb[di][m], wh + bhi[m]);
+                    }
                 }
             }
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                if (ok[m]) *dst[m] = make_int2((int)(o0 + qa[m]), (int)(o0 + max(qa[m], qb[m])));
+                if (ok[m]) {
+                    int lo = qa[0][m], hi = max(qa[0][m], qb[0][m]);
+                    if (PAIR && nd == 2) {
+                        // union with the pair's second direction, as one index range
+                        const int lo2 = qa[ND - 1][m], hi2 = max(qa[ND - 1][m], qb[ND - 1][m]);
+                        if (hi2 > lo2) {
+                            if (hi > lo) {
+                                lo = min(lo, lo2);
+                                hi = max(hi, hi2);
+                            } else {
+                                lo = lo2;
+                                hi = hi2;
+                            }
+                        }
+                    }
+                    const int cnt = hi - lo;
+                    *dst[m] = (lo < 0xFFFF && cnt < 0xFFFF) ? (uint32_t)lo | ((uint32_t)cnt << 16)
+                                                            : kWinLookup;
+                }
                 dst[m] += slab_stride;
             }
             u += RS * dv;
@@ -713,12 +765,13 @@ __device__ __forceinline__ void pair_steps(std::integer_sequence<int, Ts...>, ui
     (pair_step<CLAMP, WEIGHTED, Ts>(rbase, X1, X2, e, stride, E, w), ...);
 }
 
-// Step T of the packed walk (64-row slab, two 16-bit counters per word: row
-// r in the low half, row r + 32 in the high half of the same word): X1, X2 are
-// the lane's two peaks on row lane ^ g(T), Y1, Y2 the same peaks 32 rows
-// further (Y = X - 32 D), so all four share the row offset and the step; the
-// low-half updates add 1, the high-half ones 2^16.  Every lane is still on its
-// own bank.
+// Step T of the paired walk (two directions of one pair, two 16-bit counters
+// per word: the pair's first direction in the low half, its second in the
+// high half): X1, X2 are the lane's two peaks in the first direction on row
+// lane ^ g(T), Y1, Y2 the same peaks in the second.  A peak's shift tables do
+// not depend on the direction (Eq. due), so all four share the row offset
+// and the step; the low-half updates add 1, the high-half ones 2^16.  Every
+// lane is still on its own bank.
 template <bool CLAMP, int T>
 __device__ __forceinline__ void quad_step(uint32_t rbase, int64_t &X1, int64_t &X2, int64_t &Y1,
                                           int64_t &Y2, const int64_t (&e)[5], uint32_t stride,
@@ -761,6 +814,26 @@ __device__ __forceinline__ void quad_steps(std::integer_sequence<int, Ts...>, ui
     (quad_step<CLAMP, Ts>(rbase, X1, X2, Y1, Y2, e, stride, E), ...);
 }
 
+// The first S Gray-code steps of the paired walk (unclamped), for a compacted
+// last round (S < 32): a loop rather than unrolled steps, so that the paired
+// kernel's registers stay within a 24-warp block.  Row lane ^ g(t) is reached
+// from the start row lane by adding (lane - row) D.
+__device__ __forceinline__ void quad_steps_short(int S, uint32_t rbase, uint32_t lane, int64_t X1,
+                                                 int64_t X2, int64_t Y1, int64_t Y2, int64_t dv,
+                                                 uint32_t stride)
+{
+#pragma unroll 1
+    for (int t = 0; t < S; ++t) {
+        const uint32_t gt = (uint32_t)(t ^ (t >> 1));
+        const int64_t dl = (int64_t)((int)lane - (int)(lane ^ gt)) * dv;
+        const uint32_t rb = rbase ^ (gt << 2);
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(cell_of(X1 + dl) * stride + rb) : "memory");
+        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(cell_of(X2 + dl) * stride + rb) : "memory");
+        asm volatile("red.shared.add.u32 [%0], 65536;" ::"r"(cell_of(Y1 + dl) * stride + rb) : "memory");
+        asm volatile("red.shared.add.u32 [%0], 65536;" ::"r"(cell_of(Y2 + dl) * stride + rb) : "memory");
+    }
+}
+
 template <int... Ts>
 __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, int32_t *H0, int lane,
                                            int64_t X, const int64_t (&e)[5], int E, int Wt, int K,
@@ -787,18 +860,24 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // (pair_step / quad_step / diff_step), so the 32 atomics of one warp
 // instruction always go to 32 different banks.
 //
-// PACK (START mode, plain map): a slab has 64 rows and each counter word holds
-// two 16-bit counts, row r in the low half and row r + 32 in the high half, so
-// one dealt pair of peaks feeds 128 updates (quad_step).  A stripe-start count
-// stays below 2^16 when no FFT has two peaks within one cell (each FFT then
-// starts at most one stripe per cell and row) and n_fft < 2^16; the window
-// pre-pass flags the first condition per job (`dense`) and a flagged job runs
-// its 64-row slabs as two 32-row passes with whole-word counts instead.
+// PACK (START mode, plain map, several directions): an item covers two sky
+// directions, d_a = 2u and d_b = 2u + 1 of the job, and each counter word holds
+// two 16-bit counts of the same (cell, row), d_a's in the low half and d_b's in
+// the high half.  The shift tables S0, D do not depend on the direction, so a
+// dealt pair of peaks is walked in both directions with one step table (four
+// atomics per step, quad_step); the item's windows are the union of the two
+// directions' windows, and the guard cells hold in addition the largest cell
+// distance between a peak's two positions (the window pre-pass measures it per
+// pair; a pair beyond the job's allowance takes the clamped walk).  A
+// stripe-start count stays below 2^16 when no FFT has two peaks within one cell
+// (each FFT then starts at most one stripe per cell and row) and n_fft < 2^16;
+// the window pre-pass flags the first condition per job (`dense`), and a
+// flagged job walks each direction of a pair on its own with whole-word counts.
 //
 // Emit: warps take 16-cell groups along f0 (START, packed counts) or segments
-// (DIFF, or counts too large to pack); lane l walks row l (and, packed, row
-// l + 32): START sums a K-cell window of starts, DIFF takes a running sum with
-// the other segments' totals as carry-in.  The count goes to the map
+// (DIFF, or counts too large to pack); lane l walks row l (of both directions
+// of a pair): START sums a K-cell window of starts, DIFF takes a running sum
+// with the other segments' totals as carry-in.  The count goes to the map
 // (optional) and the warp's max over rows (smallest row on ties) to the
 // direction's profile by a 64-bit atomicMax, which is order-independent.
 template <int MODE, int MAXT, bool WEIGHTED, bool PACK>
@@ -807,7 +886,6 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                  int32_t guard, uint32_t cell_stride)
 {
     static_assert(!PACK || (MODE == FH_MODE_START && !WEIGHTED), "packed counters: plain START");
-    constexpr int RS = PACK ? 2 * kRows : kRows;  // rows per slab
     extern __shared__ __align__(16) int32_t smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -831,14 +909,16 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
     // hold sorted positions, so every row of every windowed peak lands in the
     // guard cells or the tile; after a failed check (unsorted or non-finite
     // input) the windows can hold anything and the clamped walk, which keeps
-    // every update in [0, E], runs instead.  (PACK) the packed counters are
-    // used while the window pre-pass found no FFT with two peaks in one cell.
+    // every update in [0, E], runs instead.  (PACK) direction pairs need the
+    // job's allowance for the distance between a peak's two positions in the
+    // guards too, and take the packed counters while the window pre-pass found
+    // no FFT with two peaks in one cell.
     unsigned job_fast = 0;    // bit j: job j may take the unclamped walk
     unsigned job_packed = 0;  // bit j: job j's stripe-start counts fit 16 bits
     for (int j = 0; j < tbl.n_jobs; ++j) {
         const TransformJob &Jt = tbl.job[j];
         if (Jt.dmax != nullptr && Jt.err != nullptr && *Jt.err == 0 &&
-            guard_for(*Jt.dmax, RS - 1) <= guard)
+            guard_for(*Jt.dmax) + (PACK && Jt.dir_pairs ? Jt.delta_alloc : 0) <= guard)
             job_fast |= 1u << j;
         if (PACK && Jt.dense != nullptr && *Jt.dense == 0) job_packed |= 1u << j;
     }
@@ -848,42 +928,50 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         while (jb + 1 < tbl.n_jobs && item >= tbl.job[jb + 1].item_begin) ++jb;
         const TransformJob *J = &tbl.job[jb];
         const int64_t rem = item - J->item_begin;
-        const int per_dir = J->n_slabs * J->n_tiles;
-        const int d_rel = (int)(rem / per_dir);
-        const int r2 = (int)(rem - (int64_t)d_rel * per_dir);
+        const int per_unit = J->n_slabs * J->n_tiles;
+        const int unit = (int)(rem / per_unit);  // a direction, or (PACK) a pair of them
+        const int r2 = (int)(rem - (int64_t)unit * per_unit);
         const int slab = r2 / J->n_tiles;
         const int tile = r2 - slab * J->n_tiles;
         const int K = J->k_over, W = J->tile_cells, n_f0 = J->n_f0, n_fdot = J->n_fdot;
         const int n_fft = J->n_fft;
-        const int js = slab * RS;
-        const int R_slab = min(RS, n_fdot - js);
+        const int js = slab * kRows;
+        const int R_slab = min(kRows, n_fdot - js);
         const int b0 = tile * W;
         const int Wt = min(W, n_f0 - b0);
         const int E = Wt + K - 1;
+        const bool paired = PACK && J->dir_pairs;
+        const int d_rel = paired ? 2 * unit : unit;  // d_a, relative to the job's first
+        const bool has_b = paired && d_rel + 1 < J->n_dir;
         const int d_abs = J->dir_begin + d_rel;
         const int64_t *__restrict__ Ad = J->A + (int64_t)d_abs * J->n_peaks;
+        const int64_t *__restrict__ Ad_b = has_b ? Ad + J->n_peaks : Ad;
         const int64_t *__restrict__ offs = J->offsets;
         const int64_t *__restrict__ S0 = J->S0;
         const int64_t *__restrict__ Dt = J->D;
-        const int2 *__restrict__ wrow =
-            J->windows ? J->windows + (((int64_t)d_rel * J->n_slabs + slab) * J->n_tiles + tile) *
+        const uint32_t *__restrict__ wrow =
+            J->windows ? J->windows + (((int64_t)unit * J->n_slabs + slab) * J->n_tiles + tile) *
                                           n_fft
                        : nullptr;
         const int32_t *__restrict__ wts =
             J->weights ? J->weights + (int64_t)d_abs * n_fft : nullptr;
-        const bool fast = MODE == FH_MODE_START && ((job_fast >> jb) & 1u);
+        // a pair whose positions lie further apart than the job allows walks clamped
+        const bool fast = MODE == FH_MODE_START && ((job_fast >> jb) & 1u) &&
+                          (!has_b || J->unit_delta == nullptr ||
+                           J->unit_delta[unit] <= J->delta_alloc);
         const int64_t base_shift = (int64_t)(b0 - K + 1) * 4294967296LL;
         const int64_t e_fixed = (int64_t)E * 4294967296LL;
         const int nchunks = (n_fft + 31) >> 5;
 
         // One pass over the tile: zero the counters, accumulate rows j0 .. j0 +
-        // R - 1 (QUAD: rows j0 .. j0 + 31 in the low halves and j0 + 32 .. j0 +
-        // R - 1 in the high halves), emit.  The windows (table or lookup) cover
-        // the whole slab, a superset of the pass's rows when a packed slab runs
-        // as two passes.
-        auto pass = [&](const int j0, const int R, auto quad_tag) {
+        // R - 1 of direction d_a + dsel (QUAD: of both directions of the pair, d_a
+        // in the low halves, d_b in the high halves), emit.  The windows of a pair
+        // (table or lookup) are the union of its two directions' windows, a
+        // superset of either's.
+        auto pass = [&](const int j0, const int R, auto quad_tag, const int dsel) {
             constexpr bool QUAD = decltype(quad_tag)::value;
             const bool row_ok = lane < R;
+            const int64_t *__restrict__ Ap = dsel ? Ad_b : Ad;
 
             // zero the counters (with the guard cells in the fast path); reset the chunk counter
             {
@@ -904,34 +992,47 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 int32_t wt = 1;
                 if constexpr (WEIGHTED)
                     if (wts != nullptr && (c << 5) + lane < n_fft) wt = __ldg(wts + (c << 5) + lane);
-                if (wrow != nullptr) {
-                    // precomputed window: one coalesced load; trusted on the unclamped walk
-                    // (the input checks passed and the table was built from the sanitised
-                    // CSR), else clamped into the FFT's CSR range
-                    const int i = (c << 5) + lane;
+                const int i_l = (c << 5) + lane;
+                const uint32_t wv = (wrow != nullptr && i_l < n_fft) ? wrow[i_l] : kWinLookup;
+                if (wrow != nullptr && wv != kWinLookup) {
+                    // precomputed window: one coalesced load (start relative to the FFT's
+                    // first peak, count); trusted on the unclamped walk (the input checks
+                    // passed and the table was built from the sanitised CSR), else clamped
+                    // into the FFT's CSR range
+                    const int i = i_l;
+                    const int64_t o0 = __ldg(offs + i);
+                    dv = __ldg(Dt + i);
+                    cb = __ldg(S0 + i) + (int64_t)j0 * dv + base_shift;
+                    if (fast) {
+                        q0 = o0 + (wv & 0xFFFFu);
+                        n = (int)(wv >> 16);
+                    } else {
+                        const int64_t o1 = __ldg(offs + i + 1);
+                        const int64_t a = min(o0 + (int64_t)(wv & 0xFFFFu), o1);
+                        q0 = a;
+                        n = (int)min((int64_t)(wv >> 16), o1 - a);
+                    }
+                } else if (wrow != nullptr && i_l >= n_fft) {
                     cb = 0;
                     dv = 0;
                     q0 = 0;
                     n = 0;
-                    if (i < n_fft) {
-                        const int2 wv = wrow[i];
-                        dv = __ldg(Dt + i);
-                        cb = __ldg(S0 + i) + (int64_t)j0 * dv + base_shift;
-                        if (fast) {
-                            q0 = wv.x;
-                            n = wv.y - wv.x;
-                        } else {
-                            const int64_t o0 = __ldg(offs + i), o1 = __ldg(offs + i + 1);
-                            const int64_t a = wv.x < o0 ? o0 : (wv.x > o1 ? o1 : wv.x);
-                            const int64_t b = wv.y < a ? a : (wv.y > o1 ? o1 : wv.y);
-                            q0 = a;
-                            n = (int)(b - a);
-                        }
-                    }
                 } else {
                     int64_t cbs;
-                    lookup_window(Ad, offs, S0, Dt, n_fft, (c << 5) + lane, js, R_slab, base_shift,
+                    lookup_window(Ap, offs, S0, Dt, n_fft, (c << 5) + lane, js, R_slab, base_shift,
                                   e_fixed, cbs, dv, q0, n);
+                    if constexpr (QUAD) {
+                        // the union (as one index range) with the other direction's window
+                        int64_t cb2, dv2, q0b;
+                        int nb;
+                        lookup_window(Ad_b, offs, S0, Dt, n_fft, (c << 5) + lane, js, R_slab,
+                                      base_shift, e_fixed, cb2, dv2, q0b, nb);
+                        if (nb > 0) {
+                            const int64_t hi = n > 0 ? max(q0 + n, q0b + nb) : q0b + nb;
+                            q0 = n > 0 ? min(q0, q0b) : q0b;
+                            n = (int)(hi - q0);
+                        }
+                    }
                     cb = cbs + (int64_t)(j0 - js) * dv;
                 }
                 // START mode deals the peaks out in pairs of one FFT (one slot = two
@@ -963,7 +1064,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 // and 2 (g - P) + 1 (if below q0 + n), or (singles) g - P: the owner
                 // publishes kq = q0 - 2 P (q0 - P) and its window end qe.
                 int before = 0;
-                auto fetch = [&](int base, int64_t &a1, int64_t &a2, bool &two, int &owner) {
+                // QUAD: b1, b2 are the same peaks' positions in direction d_b
+                auto fetch = [&](int base, int64_t &a1, int64_t &a2, int64_t &b1, int64_t &b2,
+                                 bool &two, int &owner) {
                     const unsigned rel = (unsigned)(P - base);
                     const unsigned bits =
                         __reduce_or_sync(kFull, (has && rel < 32u) ? (1u << rel) : 0u);
@@ -977,11 +1080,15 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                         const int oqe = __shfl_sync(kFull, qe, owner);
                         const int k = okq + 2 * g;
                         two = live && k + 1 < oqe;
-                        a1 = live ? __ldg(Ad + k) : 0;
-                        a2 = two ? __ldg(Ad + k + 1) : 0;
+                        a1 = live ? __ldg(Ap + k) : 0;
+                        a2 = two ? __ldg(Ap + k + 1) : 0;
+                        if constexpr (QUAD) {
+                            b1 = live ? __ldg(Ad_b + k) : 0;
+                            b2 = two ? __ldg(Ad_b + k + 1) : 0;
+                        }
                     } else {
                         two = false;
-                        a1 = live ? __ldg(Ad + (okq + g)) : 0;
+                        a1 = live ? __ldg(Ap + (okq + g)) : 0;
                         a2 = 0;
                     }
                 };
@@ -989,15 +1096,18 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 // empty slot (g >= T) is parked in guard cell -1 with zero steps.  An
                 // empty second peak walks with the first one's steps from a start
                 // that keeps all the pass's rows in guard cells -guard .. -1 on the
-                // unclamped walk (|(RS - 1) D| is below guard - 1 cells there), and far
-                // below cell 0 on the clamped walk (which sends it to the dump cell).
-                // Never read.  On the unclamped walk every windowed peak's rows stay
-                // inside the guard cells: the window holds the peaks with A - cb_slab
-                // in [min(0, (R_slab-1) D), max(0, (R_slab-1) D) + E 2^32) (to one
-                // cell), and |(RS - 1) D| stays below guard - 2 cells.  QUAD: Y1, Y2
-                // are the same peaks 32 rows further.
-                auto setup = [&](int g, int64_t a1, int64_t a2, bool two, int owner, int64_t &X1,
-                                 int64_t &X2, int64_t (&e)[5], int32_t &ow, int64_t &dv_slot) {
+                // unclamped walk (|31 D| is below guard - 1 cells there), and far below
+                // cell 0 on the clamped walk (which sends it to the dump cell).  Never
+                // read.  On the unclamped walk every windowed peak's rows stay inside
+                // the guard cells: the window holds the peaks with A - cb in
+                // [min(0, (R_slab-1) D), max(0, (R_slab-1) D) + E 2^32) (to one cell),
+                // and |31 D| stays below guard - 2 cells; a pair's union window holds
+                // peaks whose position in the other direction is that close, so each
+                // position lies within the pair's distance of it, which the guard also
+                // holds.  QUAD: Y1, Y2 are the same peaks in direction d_b.
+                auto setup = [&](int g, int64_t a1, int64_t a2, int64_t b1, int64_t b2, bool two,
+                                 int owner, int64_t &X1, int64_t &X2, int64_t &Y1, int64_t &Y2,
+                                 int64_t (&e)[5], int32_t &ow) {
                     if constexpr (WEIGHTED)
                         ow = __shfl_sync(kFull, wt, owner);
                     else
@@ -1006,7 +1116,6 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     const int64_t odv0 = __shfl_sync(kFull, dv, owner);
                     const bool live = g < T;
                     const int64_t odv = live ? odv0 : 0;
-                    dv_slot = odv;
                     // e[b] = +-(D << b), + when bit b of the lane is set
                     const int64_t ndv = -odv;
 #pragma unroll
@@ -1014,23 +1123,30 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                         e[b] = (((lane >> b) & 1) ? odv : ndv) * (int64_t)(1 << b);
                     const int64_t lane_dv = (int64_t)lane * odv;
                     X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
+                    if constexpr (QUAD) Y1 = live ? b1 - ocb - lane_dv : -(int64_t(1) << 32);
                     if (kPairs) {
                         const int64_t park =
                             fast ? (odv > 0 ? -(int64_t(1) << 32) : -((int64_t)guard << 32)) -
                                        lane_dv
                                  : -(int64_t(1) << 62);
                         X2 = two ? a2 - ocb - lane_dv : park;
+                        if constexpr (QUAD) Y2 = two ? b2 - ocb - lane_dv : park;
                     }
                 };
-                int64_t a1_nx = 0, a2_nx = 0;
+                // the next round's peaks are loaded a round ahead, except on the paired
+                // walk, whose registers hold four positions per slot already
+                constexpr bool kAhead = !QUAD;
+                int64_t a1_nx = 0, a2_nx = 0, b1_nx = 0, b2_nx = 0;
                 bool two_nx = false;
                 int own_nx = 0;
-                if (T > 0) fetch(0, a1_nx, a2_nx, two_nx, own_nx);
+                if (kAhead && T > 0) fetch(0, a1_nx, a2_nx, b1_nx, b2_nx, two_nx, own_nx);
                 for (int base = 0; base < T; base += 32) {
-                    int64_t a1 = a1_nx, a2 = a2_nx;
+                    int64_t a1 = a1_nx, a2 = a2_nx, b1 = b1_nx, b2 = b2_nx;
                     bool two = two_nx;
                     int owner = own_nx;
-                    if (base + 32 < T) fetch(base + 32, a1_nx, a2_nx, two_nx, own_nx);
+                    if (!kAhead) fetch(base, a1, a2, b1, b2, two, owner);
+                    else if (base + 32 < T)
+                        fetch(base + 32, a1_nx, a2_nx, b1_nx, b2_nx, two_nx, own_nx);
                     // A last round of L <= 16 slots (unclamped START walk): S = the
                     // power of two >= L; slot q = lane mod S is walked by the 32 / S
                     // lanes lane = q + S p, lane p taking rows S p .. S p + S - 1 in
@@ -1044,41 +1160,28 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                         const int src = lane & (S - 1);
                         a1 = __shfl_sync(kFull, a1, src);
                         a2 = __shfl_sync(kFull, a2, src);
+                        if constexpr (QUAD) {
+                            b1 = __shfl_sync(kFull, b1, src);
+                            b2 = __shfl_sync(kFull, b2, src);
+                        }
                         two = __shfl_sync(kFull, (int)two, src) != 0;
                         owner = __shfl_sync(kFull, owner, src);
                     }
-                    int64_t X1, X2 = 0, e[5], dv_slot;
+                    int64_t X1, X2 = 0, Y1 = 0, Y2 = 0, e[5];
                     int32_t ow;
-                    setup(base + (lane & (S - 1)), a1, a2, two, owner, X1, X2, e, ow, dv_slot);
+                    setup(base + (lane & (S - 1)), a1, a2, b1, b2, two, owner, X1, X2, Y1, Y2, e, ow);
                     if (MODE == FH_MODE_START) {
                         using std::make_integer_sequence;
                         const uint32_t st = cell_stride, ee = (uint32_t)E, ww = (uint32_t)ow;
                         if constexpr (QUAD) {
-                            // the same peaks 32 rows further, in the high halves
-                            const int64_t Y1 = X1 - 32 * dv_slot, Y2 = X2 - 32 * dv_slot;
-                            if (fast) {
-                                switch (S) {
-                                case 1:
-                                    quad_steps<false>(make_integer_sequence<int, 1>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
-                                    break;
-                                case 2:
-                                    quad_steps<false>(make_integer_sequence<int, 2>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
-                                    break;
-                                case 4:
-                                    quad_steps<false>(make_integer_sequence<int, 4>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
-                                    break;
-                                case 8:
-                                    quad_steps<false>(make_integer_sequence<int, 8>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
-                                    break;
-                                case 16:
-                                    quad_steps<false>(make_integer_sequence<int, 16>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
-                                    break;
-                                default:
-                                    quad_steps<false>(make_integer_sequence<int, 32>{}, rbase, X1, X2, Y1, Y2, e, st, ee);
-                                }
-                            } else
-                                quad_steps<true>(make_integer_sequence<int, 32>{}, rbase, X1, X2,
-                                                 Y1, Y2, e, st, ee);
+                            // the same peaks in direction d_b, in the high halves
+                            // (the paired walk runs unclamped only)
+                            if (S == 32)
+                                quad_steps<false>(make_integer_sequence<int, 32>{}, rbase, X1, X2,
+                                                  Y1, Y2, e, st, ee);
+                            else  // e[0] = +-D, + on odd lanes
+                                quad_steps_short(S, rbase, (uint32_t)lane, X1, X2, Y1, Y2,
+                                                 (lane & 1) ? e[0] : -e[0], st);
                         } else if (fast) {
                             switch (S) {
                             case 1:
@@ -1115,99 +1218,106 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             __syncthreads();
 
             // emit counts, map and profile
-            unsigned long long *prof =
-                reinterpret_cast<unsigned long long *>(J->profile) + (int64_t)d_abs * n_f0 + b0;
+            unsigned long long *prof = reinterpret_cast<unsigned long long *>(J->profile) +
+                                       (int64_t)(d_abs + dsel) * n_f0 + b0;
             if constexpr (QUAD) {
-                // Packed words: row lane in the low half, row lane + 32 in the high
-                // half.  Per cell the lane forms both counts (K-cell windows of
-                // starts), keys them as 64 count + (63 - row in the slab) and one
-                // signed reduction gives the warp's (max count, smallest row) over
-                // the 64 rows; rows beyond the slab start their windows at -2^25 and
-                // never win (counts stay below 2^25 on this path).
-                const bool hi_ok = lane + kRows < R;
-                int32_t *maplo = nullptr, *maphi = nullptr;
-                if (J->maps != nullptr) {
-                    int32_t *m0 = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
-                    maplo = row_ok ? m0 : nullptr;
-                    maphi = hi_ok ? m0 + (int64_t)kRows * n_f0 : nullptr;
+                // Packed words: direction d_a's count of (cell, row lane) in the low
+                // half, d_b's in the high half.  Per cell the lane forms both counts
+                // (K-cell windows of starts) and one signed reduction per direction
+                // gives the warp's (max count, smallest row), keyed 32 count + (31 -
+                // lane); rows beyond the slab start their windows at -2^26 and never
+                // win (counts stay below 2^25 on this path).
+                unsigned long long *prof_b = prof + n_f0;
+                int32_t *map_a = nullptr, *map_b = nullptr;
+                if (J->maps != nullptr && row_ok) {
+                    map_a = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
+                    map_b = map_a + (int64_t)n_fdot * n_f0;
                 }
                 const int seg = (((Wt + nwarps - 1) / nwarps) + 15) & ~15;
                 const int c0 = min(Wt, warp * seg);
                 const int c1 = min(Wt, c0 + seg);
-                const int klo = 63 - lane, khi = 31 - lane;
-                int winlo = row_ok ? 0 : -(1 << 25);
-                int winhi = hi_ok ? 0 : -(1 << 25);
+                const int c31 = 31 - lane;
+                int wa = row_ok ? 0 : -(1 << 26);
+                int wb = wa;
                 if (c0 < c1)
                     for (int L = c0; L < c0 + K; ++L) {
                         const uint32_t h = (uint32_t)H[L * kRows + lane];
-                        winlo += (int)(h & 0xFFFFu);
-                        winhi += (int)(h >> 16);
+                        wa += (int)(h & 0xFFFFu);
+                        wb += (int)(h >> 16);
                     }
-                const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 63u;
+                const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 31u;
                 auto key_of = [&](int v) {
-                    return ((unsigned long long)(uint32_t)(v >> 6) << 32) |
-                           (unsigned long long)(key_lo + (uint32_t)(v & 63));
+                    return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
+                           (unsigned long long)(key_lo + (uint32_t)(v & 31));
                 };
-                // the high row is 32 n_f0 words after the low one: same alignment
-                const int32_t *mrow = maplo ? maplo : maphi;
-                const bool vec_map = mrow != nullptr && (((uintptr_t)mrow & 15u) == 0);
+                // 16-byte stores only where both directions' rows are 16-byte aligned
+                // (d_b's map starts n_fdot n_f0 words after d_a's)
+                const bool vec_map = map_a != nullptr && (((uintptr_t)map_a & 15u) == 0) &&
+                                     (((uintptr_t)map_b & 15u) == 0);
                 auto run = [&](auto map_tag) {
                     constexpr bool kMap = decltype(map_tag)::value;
                     int c = c0;
                     for (; c + 16 <= c1; c += 16) {
                         const int32_t *h0 = H + c * kRows + lane;
                         const int32_t *h1 = h0 + K * kRows;
-                        int myv = 0;
-                        int cl[kMap ? 16 : 1], ch[kMap ? 16 : 1];
+                        int myva = 0, myvb = 0;
+                        int ca[kMap ? 16 : 1], cbn[kMap ? 16 : 1];
 #pragma unroll
                         for (int m = 0; m < 16; ++m) {
-                            const int lo = winlo, hi = winhi;
-                            const uint32_t a = (uint32_t)h1[m * kRows], b = (uint32_t)h0[m * kRows];
-                            winlo += (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
-                            winhi += (int)(a >> 16) - (int)(b >> 16);
+                            const int na = wa, nb = wb;
+                            const uint32_t x = (uint32_t)h1[m * kRows], y = (uint32_t)h0[m * kRows];
+                            wa += (int)(x & 0xFFFFu) - (int)(y & 0xFFFFu);
+                            wb += (int)(x >> 16) - (int)(y >> 16);
                             if constexpr (kMap) {
-                                cl[m] = lo;
-                                ch[m] = hi;
+                                ca[m] = na;
+                                cbn[m] = nb;
                             }
-                            const int v = max(lo * 64 + klo, hi * 64 + khi);
-                            const int r = __reduce_max_sync(kFull, v);
-                            if (lane == m) myv = r;
+                            const int va = __reduce_max_sync(kFull, na * 32 + c31);
+                            const int vb = __reduce_max_sync(kFull, nb * 32 + c31);
+                            if (lane == m) {
+                                myva = va;
+                                myvb = vb;
+                            }
                         }
                         if constexpr (kMap) {
                             if (vec_map) {
-                                if (maplo) {
-                                    int4 *d4 = reinterpret_cast<int4 *>(maplo + c);
+                                int4 *da = reinterpret_cast<int4 *>(map_a + c);
+                                int4 *db = reinterpret_cast<int4 *>(map_b + c);
 #pragma unroll
-                                    for (int q = 0; q < 4; ++q)
-                                        d4[q] = make_int4(cl[4 * q], cl[4 * q + 1], cl[4 * q + 2], cl[4 * q + 3]);
+                                for (int q = 0; q < 4; ++q) {
+                                    da[q] = make_int4(ca[4 * q], ca[4 * q + 1], ca[4 * q + 2], ca[4 * q + 3]);
+                                    db[q] = make_int4(cbn[4 * q], cbn[4 * q + 1], cbn[4 * q + 2], cbn[4 * q + 3]);
                                 }
-                                if (maphi) {
-                                    int4 *d4 = reinterpret_cast<int4 *>(maphi + c);
-#pragma unroll
-                                    for (int q = 0; q < 4; ++q)
-                                        d4[q] = make_int4(ch[4 * q], ch[4 * q + 1], ch[4 * q + 2], ch[4 * q + 3]);
-                                }
-                            } else {
+                            } else if (map_a) {
 #pragma unroll
                                 for (int m = 0; m < 16; ++m) {
-                                    if (maplo) maplo[c + m] = cl[m];
-                                    if (maphi) maphi[c + m] = ch[m];
+                                    map_a[c + m] = ca[m];
+                                    map_b[c + m] = cbn[m];
                                 }
                             }
                         }
-                        if (lane < 16) atomicMax(prof + c + lane, key_of(myv));
+                        if (lane < 16) {
+                            atomicMax(prof + c + lane, key_of(myva));
+                            atomicMax(prof_b + c + lane, key_of(myvb));
+                        }
                     }
                     for (; c < c1; ++c) {
-                        const int lo = winlo, hi = winhi;
+                        const int na = wa, nb = wb;
                         // the segment's last step may read cell E (the dump cell); that value is unused
-                        const uint32_t a = (uint32_t)H[(c + K) * kRows + lane];
-                        const uint32_t b = (uint32_t)H[c * kRows + lane];
-                        winlo += (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
-                        winhi += (int)(a >> 16) - (int)(b >> 16);
-                        if (kMap && maplo) maplo[c] = lo;
-                        if (kMap && maphi) maphi[c] = hi;
-                        const int v = __reduce_max_sync(kFull, max(lo * 64 + klo, hi * 64 + khi));
-                        if (lane == 0) atomicMax(prof + c, key_of(v));
+                        const uint32_t x = (uint32_t)H[(c + K) * kRows + lane];
+                        const uint32_t y = (uint32_t)H[c * kRows + lane];
+                        wa += (int)(x & 0xFFFFu) - (int)(y & 0xFFFFu);
+                        wb += (int)(x >> 16) - (int)(y >> 16);
+                        if (kMap && map_a) {
+                            map_a[c] = na;
+                            map_b[c] = nb;
+                        }
+                        const int va = __reduce_max_sync(kFull, na * 32 + c31);
+                        const int vb = __reduce_max_sync(kFull, nb * 32 + c31);
+                        if (lane == 0) {
+                            atomicMax(prof + c, key_of(va));
+                            atomicMax(prof_b + c, key_of(vb));
+                        }
                     }
                 };
                 if (J->maps != nullptr)
@@ -1217,7 +1327,7 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             } else {
                 int32_t *maprow = nullptr;
                 if (J->maps != nullptr && row_ok)
-                    maprow = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
+                    maprow = J->maps + ((int64_t)(d_rel + dsel) * n_fdot + j0 + lane) * n_f0 + b0;
                 // Per cell the profile takes the warp's max over its rows, smallest row
                 // on ties.  Counts below 2^26 fit one packed signed reduction
                 // 32 count + (31 - lane); rows beyond the pass start their window at
@@ -1330,17 +1440,16 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         };
 
         if constexpr (PACK) {
-            if (((job_packed >> jb) & 1u) && R_slab > kRows) {
-                pass(js, R_slab, std::true_type{});
+            if (has_b && fast && ((job_packed >> jb) & 1u)) {
+                pass(js, R_slab, std::true_type{}, 0);
             } else {
-                // 32 rows or fewer (the counts stay in the low halves, whole-word
-                // counts equal them), or a job whose counts need whole words: the
-                // slab as one or two 32-row passes
-                pass(js, min(kRows, R_slab), std::false_type{});
-                if (R_slab > kRows) pass(js + kRows, R_slab - kRows, std::false_type{});
+                // a single direction, a pair whose counts need whole words, or one
+                // that takes the clamped walk: each direction on its own
+                pass(js, R_slab, std::false_type{}, 0);
+                if (has_b) pass(js, R_slab, std::false_type{}, 1);
             }
         } else {
-            pass(js, R_slab, std::false_type{});
+            pass(js, R_slab, std::false_type{}, 0);
         }
     }
 }
@@ -1656,8 +1765,8 @@ size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, in
 }
 
 // Kernel instantiation for a counting mode and block size: blocks of up to 512
-// threads get up to 128 registers per thread, of up to 768 threads (START
-// mode) 80, of 1024 threads 64.
+// threads get up to 128 registers per thread, of up to 640 threads (START
+// mode) 102, of up to 768 threads 80, of 1024 threads 64.
 template <bool WEIGHTED, bool PACK, typename F>
 static auto with_transform_kernel_w(int32_t mode, int32_t nwarps, F &&f)
 {
@@ -1667,11 +1776,12 @@ static auto with_transform_kernel_w(int32_t mode, int32_t nwarps, F &&f)
                                : f(transform_kernel<FH_MODE_DIFF, 512, WEIGHTED, false>);
     }
     return nwarps > 24   ? f(transform_kernel<FH_MODE_START, 1024, WEIGHTED, PACK>)
-           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 768, WEIGHTED, PACK>)
+           : nwarps > 20 ? f(transform_kernel<FH_MODE_START, 768, WEIGHTED, PACK>)
+           : nwarps > 16 ? f(transform_kernel<FH_MODE_START, 640, WEIGHTED, PACK>)
                          : f(transform_kernel<FH_MODE_START, 512, WEIGHTED, PACK>);
 }
 // weighted: instantiation that adds per-FFT weights (adaptive map); plain: +1;
-// pack: 64-row slabs with two 16-bit counts per word (plain START map only)
+// pack: direction pairs with two 16-bit counts per word (plain START map only)
 template <typename F>
 static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, bool pack, F &&f)
 {
@@ -1683,7 +1793,7 @@ static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, b
 cudaError_t transform_prepare(int32_t mode, size_t smem)
 {
     cudaError_t e = cudaSuccess;
-    for (int nw : {16, 24, 32})
+    for (int nw : {16, 20, 24, 32})
         for (int v = 0; v < 3; ++v) {
             const bool wt = v == 1, pk = v == 2;
             if (pk && mode != FH_MODE_START) continue;
@@ -1721,7 +1831,7 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
     bool weighted = false, pack = mode == FH_MODE_START && tbl.n_jobs > 0;
     for (int j = 0; j < tbl.n_jobs; ++j) {
         weighted = weighted || tbl.job[j].weights != nullptr;
-        pack = pack && tbl.job[j].slab_rows == 2 * kRows;
+        pack = pack && tbl.job[j].dir_pairs != 0;
     }
     if (weighted && pack) return cudaErrorInvalidValue;  // packed counters hold plain counts only
     with_transform_kernel(mode, nwarps, weighted, pack, [&](auto k) {
@@ -1731,18 +1841,25 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
     return cudaGetLastError();
 }
 
-cudaError_t launch_windows(const TransformJob &job, int2 *windows, cudaStream_t s)
+cudaError_t launch_windows(const TransformJob &job, uint32_t *windows, cudaStream_t s)
 {
     if (job.n_fft <= 0 || job.n_dir <= 0) return cudaSuccess;
-    dim3 grid((job.n_fft + 7) / 8, job.n_dir);
+    dim3 grid((job.n_fft + 7) / 8, job.dir_pairs ? (job.n_dir + 1) / 2 : job.n_dir);
     // tiles per lane and pass: enough for all tiles in one pass, at most kWinMaxM
     const int m = std::min(kWinMaxM, std::max(1, (job.n_tiles + 31) / 32));
-    if (m == 1)
-        windows_kernel<1><<<grid, 256, 0, s>>>(job, windows);
-    else if (m == 2)
-        windows_kernel<2><<<grid, 256, 0, s>>>(job, windows);
+    auto go = [&](auto pair_tag) {
+        constexpr bool P = decltype(pair_tag)::value;
+        if (m == 1)
+            windows_kernel<1, P><<<grid, 256, 0, s>>>(job, windows);
+        else if (m == 2)
+            windows_kernel<2, P><<<grid, 256, 0, s>>>(job, windows);
+        else
+            windows_kernel<3, P><<<grid, 256, 0, s>>>(job, windows);
+    };
+    if (job.dir_pairs)
+        go(std::true_type{});
     else
-        windows_kernel<3><<<grid, 256, 0, s>>>(job, windows);
+        go(std::false_type{});
     return cudaGetLastError();
 }
 

@@ -65,13 +65,12 @@ struct Job {
     int32_t *d_err = nullptr;
     unsigned long long *d_dmax = nullptr;
     int32_t guard = 0;
-    int32_t rows = kRows;   // rows per slab: 64 with packed 16-bit counters, else 32
-    int2 *d_win = nullptr;  // peak windows [dir][slab][tile][fft] at the job's tile
+    uint32_t *d_win = nullptr;  // peak windows [dir][slab][tile][fft] at the job's tile
     size_t pin_off = 0;  // offset of its candidates in the batch's pinned buffer
     size_t err_off = 0;
 
     int64_t cand_count() const { return (int64_t)n_dir * n_sb * d.top_k; }
-    int32_t n_slabs() const { return (d.n_fdot + rows - 1) / rows; }
+    int32_t n_slabs() const { return (d.n_fdot + kRows - 1) / kRows; }
     int32_t n_tiles() const { return tile > 0 ? (d.n_f0 + tile - 1) / tile : 0; }
 
     // layout of the job's single device allocation
@@ -94,12 +93,12 @@ struct Job {
         const size_t a_prof = take(8 * (size_t)n_dir * (size_t)d.n_f0);
         const size_t a_cand = take(sizeof(fh_candidate) * (size_t)cand_count());
         const size_t a_err = take(16);
-        const size_t a_win = take(sizeof(int2) * (size_t)n_dir * (size_t)n_slabs() *
+        const size_t a_win = take(sizeof(uint32_t) * (size_t)n_dir * (size_t)n_slabs() *
                                   (size_t)n_tiles() * (size_t)std::max(1, n_fft));
         const size_t a_dmax = take(16);
         if (carve) {
             d_dmax = (unsigned long long *)(dbuf + a_dmax);
-            d_win = (int2 *)(dbuf + a_win);
+            d_win = (uint32_t *)(dbuf + a_win);
             d_off = (int64_t *)(dbuf + a_off);
             d_t = (double *)(dbuf + a_t);
             d_freq = (double *)(dbuf + a_freq);
@@ -227,25 +226,23 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             e = cudaMemsetAsync(j->d_prof, 0, 8 * (size_t)j->n_dir * d.n_f0, s);
         if (e != cudaSuccess) return cuda_error(e, "job set-up");
     }
-    // One persistent transform launch per group of up to kMaxBatchJobs jobs of
-    // one slab height.  A launch has one guard width (the largest its jobs
-    // need) and each job keeps the tile its window table was sized for, so jobs
-    // (in order of slab height, then guard) join a group only while every
-    // member's tile still fits in shared memory with the group's guard.
+    // One persistent transform launch per group of up to kMaxBatchJobs jobs.
+    // A launch has one guard width (the largest its jobs need) and each job
+    // keeps the tile its window table was sized for, so jobs (in order of
+    // guard) join a group only while every member's tile still fits in shared
+    // memory with the group's guard.
     const int nwarps = kServeWarps;
     const size_t lim = (size_t)max_optin_smem(device);
     std::vector<Job *> order(batch.begin(), batch.end());
-    std::stable_sort(order.begin(), order.end(), [](const Job *x, const Job *y) {
-        return x->rows != y->rows ? x->rows < y->rows : x->guard < y->guard;
-    });
+    std::stable_sort(order.begin(), order.end(),
+                     [](const Job *x, const Job *y) { return x->guard < y->guard; });
     auto fits = [&](const Job *j, int32_t guard) {
         return transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps, guard) <= lim;
     };
     for (size_t g = 0; g < order.size();) {
         size_t g_end = g + 1;
         int32_t guard = std::max<int32_t>(2, order[g]->guard);
-        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs &&
-               order[g_end]->rows == order[g]->rows) {
+        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs) {
             const int32_t gn = std::max(guard, order[g_end]->guard);
             bool ok = true;
             for (size_t k = g; k <= g_end && ok; ++k) ok = fits(order[k], gn);
@@ -280,7 +277,6 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.dir_begin = 0;
             t.n_dir = j->n_dir;
             t.windows = j->d_win;
-            t.slab_rows = j->rows;
             t.dense = reinterpret_cast<int32_t *>(j->d_dmax + 1);  // beside dmax, cleared with it
             t.item_begin = items;
             t.n_items = (int64_t)t.n_slabs * t.n_tiles * j->n_dir;
@@ -491,12 +487,10 @@ int copy_job(const fh_job_desc *jd, Job &j, int device)
     j.freq.assign(pm.freq, pm.freq + pm.n_peaks);
     j.v.assign(jd->v_over_c, jd->v_over_c + 3 * (size_t)pm.n_fft);
     j.sky.assign(jd->sky_n, jd->sky_n + 3 * (size_t)jd->n_dir);
-    // the job runs with packed 64-row slabs where they apply, and the
-    // library's default tile for its own guard cells
+    // the job runs with the library's default tile for its own guard cells
     const unsigned long long drift =
         std::max(default_drift(j.d), host_drift(j.d, j.kt, j.t.data(), j.n_fft));
-    j.rows = packed_slab_rows(j.d, device, j.n_fft, drift);
-    j.guard = guard_for(drift, j.rows - 1);
+    j.guard = guard_for(drift);
     j.tile = default_tile(j.d, device, FH_MODE_START, kServeWarps, j.guard);
     j.bytes = j.layout(false);
     return FH_OK;

@@ -314,8 +314,33 @@ def refined_sky(n_hat, n_d: float, k_sky: int) -> np.ndarray:
     return pts
 
 
+def pair_order(sky: np.ndarray) -> np.ndarray:
+    """An order of the directions that lists them in neighbouring pairs (entries
+    2u and 2u + 1): repeatedly the remaining direction farthest from the patch's
+    centroid with its nearest remaining neighbour (ties: lower index).  A sky
+    patch scanned this way keeps each pair's Doppler shifts within about one
+    input bin of each other."""
+    n = sky.shape[0]
+    if n < 3:
+        return np.arange(n)
+    cen = sky.mean(axis=0)
+    cen = cen / np.linalg.norm(cen)
+    ang = np.arccos(np.clip(sky @ sky.T, -1.0, 1.0))
+    rem = list(range(n))
+    order = []
+    while len(rem) > 1:
+        a = min(rem, key=lambda i: (float(sky[i] @ cen), i))
+        rem.remove(a)
+        b = min(rem, key=lambda j: (float(ang[a, j]), j))
+        rem.remove(b)
+        order += [a, b]
+    order += rem
+    return np.asarray(order)
+
+
 def sky_patch(w: Workload) -> np.ndarray:
-    """``w.n_dir`` grid directions nearest a seeded centre, shape (n_dir, 3)."""
+    """``w.n_dir`` grid directions nearest a seeded centre, shape (n_dir, 3),
+    listed in neighbouring pairs (``pair_order``)."""
     if not w.doppler and w.n_dir == 1:
         return np.array([[1.0, 0.0, 0.0]])
     n_d = doppler_number(w.f_hi, w.t_fft)
@@ -329,7 +354,8 @@ def sky_patch(w: Workload) -> np.ndarray:
     order = np.lexsort((np.arange(len(grid)), -dots))
     if w.n_dir > len(grid):
         raise ValueError("sky patch larger than the grid")
-    return np.ascontiguousarray(grid[order[: w.n_dir]])
+    patch = grid[order[: w.n_dir]]
+    return np.ascontiguousarray(patch[pair_order(patch)])
 
 
 # --------------------------------------------------------------------------

@@ -526,3 +526,46 @@ def test_host_input_errors_checked_on_the_device(fh):
             fh.fh_plan_set_input_checks(plan, 7)
     finally:
         fh.fh_destroy_plan(plan)
+
+
+def test_windows_beyond_16_bits_are_looked_up(fh, oracle_mod):
+    """A window table entry holds the window's first peak relative to its FFT's
+    first and its count in 16 bits each; an FFT with 150,000 peaks 0.002 bins
+    apart has windows whose count, and later whose start, do not fit, so the
+    transform looks those windows up by binary search.  (The same peaks are also
+    two to a cell, so packed counters do not apply to the job.)  Maps and
+    candidates equal the oracle's."""
+    inp, pp = synth.dense_case(91, dense_ffts=(2,), n_dense=150000, spacing_bins=0.002,
+                               n_fft=6, n_bins=400, n_fdot=9, n_dir=1, p=0.2)
+    assert int(inp.offsets[3] - inp.offsets[2]) == 150000
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    for tile, warps in ((1024, 16), (1408, 8)):
+        g = run_gpu(fh, inp, pp, tile=tile, warps=warps)
+        compare(g, o, pp, inp.t.shape[0])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_ffts_with_more_peaks_than_staged_are_read_from_global_memory(fh, oracle_mod, mode):
+    """The window pre-pass stages each FFT's peak cells in shared memory up to
+    a fixed count per FFT and direction (fewer when it stages the two
+    directions of a pair); FFTs 1 and 3 here hold 900 and 1100 peaks, 0.3
+    bins (3 cells) apart, beyond one or both limits, so their windows come from
+    searches in global memory.  Three directions: one pair and one single
+    direction in START mode.  Maps and candidates equal the oracle's."""
+    inp, pp = synth.dense_case(93, dense_ffts=(1,), n_dense=900, spacing_bins=0.3,
+                               n_fft=6, n_bins=400, n_fdot=40, n_dir=3, p=0.2)
+    more, _ = synth.dense_case(93, dense_ffts=(3,), n_dense=1100, spacing_bins=0.3,
+                               n_fft=6, n_bins=400, n_fdot=40, n_dir=3, p=0.2)
+    counts = np.diff(inp.offsets)
+    counts[3] = np.diff(more.offsets)[3]
+    offsets = np.zeros(7, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    parts = [inp.freq[inp.offsets[i]:inp.offsets[i + 1]] if i != 3 else
+             more.freq[more.offsets[3]:more.offsets[4]] for i in range(6)]
+    inp = synth.Inputs(w=inp.w, t=inp.t, offsets=offsets, freq=np.concatenate(parts),
+                       v=inp.v, sky=inp.sky)
+    assert counts[1] == 900 and counts[3] == 1100
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    for tile, warps in ((0, 0), (256, 8)):
+        g = run_gpu(fh, inp, pp, mode=mode, tile=tile, warps=warps)
+        compare(g, o, pp, inp.t.shape[0])
