@@ -931,8 +931,11 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int per_unit = J->n_slabs * J->n_tiles;
         const int unit = (int)(rem / per_unit);  // a direction, or (PACK) a pair of them
         const int r2 = (int)(rem - (int64_t)unit * per_unit);
-        const int slab = r2 / J->n_tiles;
-        const int tile = r2 - slab * J->n_tiles;
+        // items go tile by tile, a tile's slabs together: the blocks at work at one
+        // time read the peaks of a few tiles' windows, which stay in L2 for all of
+        // those tiles' slabs
+        const int tile = r2 / J->n_slabs;
+        const int slab = r2 - tile * J->n_slabs;
         const int K = J->k_over, W = J->tile_cells, n_f0 = J->n_f0, n_fdot = J->n_fdot;
         const int n_fft = J->n_fft;
         const int js = slab * kRows;
