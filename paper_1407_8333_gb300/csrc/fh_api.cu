@@ -233,6 +233,8 @@ struct fh_plan_s {
                                          // in one cell (in err's block)
     int32_t *unit_delta = nullptr;       // per direction pair of a group: the largest distance
                                          // between a peak's two cells (window pre-pass)
+    unsigned int *sched = nullptr;       // the batched transform's item counter (2 words,
+                                         // zero between launches)
     uint32_t *win = nullptr;             // peak windows of the directions being transformed
     size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path (32 rows)
@@ -260,7 +262,7 @@ struct fh_plan_s {
         for (cudaEvent_t ev : tev) cudaEventDestroy(ev);
         tev.clear();
         void *bufs[] = {t,    freq, v,   sky,  offsets, offsets_raw, S0, D,
-                        A,    profile, cand, err, win,  wq,  ws, unit_delta};  // dmax: in err's block
+                        A,    profile, cand, err, win,  wq,  ws, unit_delta, sched};  // dmax: in err's block
         for (void *b : bufs)
             if (b) cudaFree(b);
         if (h_err) cudaFreeHost(h_err);
@@ -274,6 +276,7 @@ struct fh_plan_s {
         win_bytes = 0;
         wq = nullptr;
         unit_delta = nullptr;
+        sched = nullptr;
         ws = nullptr;
     }
 };
@@ -464,7 +467,8 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
                   {(void **)&p->sky, s.sky},       {(void **)&p->A, s.A},
                   {(void **)&p->profile, s.profile}, {(void **)&p->cand, s.cand},
                   {(void **)&p->err, kErrWordsBytes},
-                  {(void **)&p->unit_delta, 4 * ((int64_t)desc->max_dir / 2 + 1)}};
+                  {(void **)&p->unit_delta, 4 * ((int64_t)desc->max_dir / 2 + 1)},
+                  {(void **)&p->sched, 16}};
     for (auto &a : allocs) {
         e = cudaMalloc(a.ptr, (size_t)std::max<int64_t>(a.bytes, 16));
         if (e != cudaSuccess) {
@@ -487,6 +491,7 @@ int fh_create_plan(const fh_plan_desc *desc, fh_plan *out)
         return set_error(FH_ERR_NOMEM, "cudaMallocHost failed");
     }
     cudaMemset(p->err, 0, kErrWordsBytes);
+    cudaMemset(p->sched, 0, 16);
     *out = p;
     return FH_OK;
 }
@@ -928,7 +933,8 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
         } else {
             const int64_t cap = (int64_t)p->n_sm * bps;
             const int32_t grid = (int32_t)std::min<int64_t>(job.n_items, cap);
-            e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, guard, s);
+            e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, guard, s,
+                                 p->sched);
         }
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
         ++p->launches;

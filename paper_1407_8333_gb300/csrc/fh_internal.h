@@ -134,9 +134,13 @@ __host__ __device__ int32_t guard_for(unsigned long long dmax, int32_t span_rows
 size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, int32_t nwarps,
                             int32_t guard);
 cudaError_t transform_prepare(int32_t mode, size_t smem);  // opt-in dynamic smem
+// sched: null (every block takes every grid-th item) or two device words that
+// are zero at the launch (a counter handing out items after each block's
+// first, and a count of finished blocks); the kernel's last block zeroes them
+// again, so launches on one stream can share them (not concurrent launches).
 cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_items,
                              int32_t grid, int32_t nwarps, size_t smem, int32_t guard,
-                             cudaStream_t s);
+                             cudaStream_t s, unsigned int *sched = nullptr);
 int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem);
 // Peak windows of every (direction, slab, tile, FFT) of a job, written to
 // job.windows (the job's other fields as for the transform).

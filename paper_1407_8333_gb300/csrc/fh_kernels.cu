@@ -883,7 +883,7 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 template <int MODE, int MAXT, bool WEIGHTED, bool PACK>
 __global__ void __launch_bounds__(MAXT, 1)
 transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words,
-                 int32_t guard, uint32_t cell_stride)
+                 int32_t guard, uint32_t cell_stride, unsigned int *__restrict__ sched)
 {
     static_assert(!PACK || (MODE == FH_MODE_START && !WEIGHTED), "packed counters: plain START");
     extern __shared__ __align__(16) int32_t smem_raw[];
@@ -902,6 +902,7 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
     int32_t *const tab = Hlo + hist_words + warp * 32;  // per-warp owner table
     int32_t *const next_chunk = Hlo + hist_words + nwarps * 32 +
                                 (MODE == FH_MODE_DIFF ? nwarps * 32 : 0);
+    int32_t *const next_item = next_chunk + 1;  // the block's next item (sched)
     const unsigned lanemask_le = 0xffffffffu >> (31 - lane);
     const unsigned lanemask_lt = (1u << lane) - 1u;
     // Per job: the unclamped walk runs when the job's largest drift over a slab
@@ -923,7 +924,16 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         if (PACK && Jt.dense != nullptr && *Jt.dense == 0) job_packed |= 1u << j;
     }
 
-    for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
+    // Items: the first one per block by block index, then (sched) whichever
+    // comes next from the launch's counter, so that blocks whose items were
+    // cheaper take more of them; without a counter, every gridDim.x-th.
+    auto next_of = [&](int64_t it) -> int64_t {
+        if (sched == nullptr) return it + gridDim.x;
+        if (threadIdx.x == 0) *next_item = (int32_t)atomicAdd(sched, 1u);
+        __syncthreads();
+        return (int64_t)gridDim.x + *next_item;
+    };
+    for (int64_t item = blockIdx.x; item < total_items; item = next_of(item)) {
         int jb = 0;
         while (jb + 1 < tbl.n_jobs && item >= tbl.job[jb + 1].item_begin) ++jb;
         const TransformJob *J = &tbl.job[jb];
@@ -1455,6 +1465,15 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             pass(js, R_slab, std::false_type{}, 0);
         }
     }
+    // the last block to finish returns the counter to zero for the next launch
+    // on this stream (every block's last fetch precedes its count here)
+    if (sched != nullptr && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+            atomicExch(sched, 0u);
+            atomicExch(sched + 1, 0u);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- a6
@@ -1822,9 +1841,10 @@ int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem)
 
 cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_items,
                              int32_t grid, int32_t nwarps, size_t smem, int32_t guard,
-                             cudaStream_t s)
+                             cudaStream_t s, unsigned int *sched)
 {
     if (total_items <= 0) return cudaSuccess;
+    if (total_items >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
     // counters (+ dump cell) of the widest tile with its guard cells; owner tables follow
     int32_t hist_words = 0;
     for (int j = 0; j < tbl.n_jobs; ++j) {
@@ -1838,7 +1858,7 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
     }
     if (weighted && pack) return cudaErrorInvalidValue;  // packed counters hold plain counts only
     with_transform_kernel(mode, nwarps, weighted, pack, [&](auto k) {
-        k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u);
+        k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u, sched);
         return cudaSuccess;
     });
     return cudaGetLastError();

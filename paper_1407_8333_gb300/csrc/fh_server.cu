@@ -118,6 +118,7 @@ struct Job {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    unsigned int *sched = nullptr;  // the stream's transform item counter (zero between launches)
     char *pinned = nullptr;
     size_t pinned_bytes = 0;
     bool busy = false;
@@ -293,7 +294,7 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
         }
         const int bps = std::max(1, transform_blocks_per_sm(FH_MODE_START, nwarps, smem));
         const int32_t grid = (int32_t)std::min<int64_t>(items, (int64_t)n_sm * bps);
-        e = launch_transform(FH_MODE_START, tbl, items, grid, nwarps, smem, guard, s);
+        e = launch_transform(FH_MODE_START, tbl, items, grid, nwarps, smem, guard, s, slot.sched);
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
         g = g_end;
     }
@@ -527,11 +528,14 @@ int fh_server_create(int64_t device_mem_budget, int32_t max_inflight, fh_server 
     for (Slot &sl : sv->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.sched, 16);
+        if (e == cudaSuccess) e = cudaMemset(sl.sched, 0, 16);
     }
     if (e != cudaSuccess) {
         for (Slot &sl : sv->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
+            if (sl.sched) cudaFree(sl.sched);
         }
         if (sv->pool) cudaMemPoolDestroy(sv->pool);
         delete sv;
@@ -581,6 +585,7 @@ int fh_server_destroy(fh_server sv)
         cudaStreamSynchronize(sl.stream);
         cudaStreamDestroy(sl.stream);
         cudaEventDestroy(sl.done);
+        if (sl.sched) cudaFree(sl.sched);
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
     if (sv->pool) cudaMemPoolDestroy(sv->pool);
