@@ -926,10 +926,11 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
 
     // Items: the first one per block by block index, then (sched) whichever
     // comes next from the launch's counter, so that blocks whose items were
-    // cheaper take more of them; without a counter, every gridDim.x-th.
+    // cheaper take more of them; without a counter, every gridDim.x-th.  Thread
+    // 0 asks the counter when its warp has no accumulation left to do (the
+    // other warps may still be busy), and the answer is read after the emit.
     auto next_of = [&](int64_t it) -> int64_t {
         if (sched == nullptr) return it + gridDim.x;
-        if (threadIdx.x == 0) *next_item = (int32_t)atomicAdd(sched, 1u);
         __syncthreads();
         return (int64_t)gridDim.x + *next_item;
     };
@@ -1228,6 +1229,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 if (lane == 0) nc = atomicAdd(next_chunk, 1);
                 c = __shfl_sync(kFull, nc, 0);
             }
+            if (sched != nullptr && dsel == 0 && threadIdx.x == 0)
+                *next_item = (int32_t)atomicAdd(sched, 1u);
             __syncthreads();
 
             // emit counts, map and profile
