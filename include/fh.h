@@ -255,7 +255,9 @@ int fh_sync(fh_plan plan, void *stream);
  * are: direction pairs (two directions with one 16-bit count each per shared
  * word, where the plain START map allows it) or single directions, block
  * warps (16, 20, 24, 32) and tile widths up to the widest that fits shared
- * memory with the guard cells of that choice.  Synchronises.  Results are cached per process by grid shape (GPU
+ * memory with the guard cells of that choice; then, for the fastest of them,
+ * the item schedule (blocks taking their next item from a device counter, or
+ * every grid-th item).  Synchronises.  Results are cached per process by grid shape (GPU
  * model, counting mode, weighting, n_f0, n_fdot, K, T_FFT, N_t, n_dir); when
  * the environment variable FH_AUTOTUNE_CACHE names a file, they are also
  * read from and written to it (JSON, one entry per line), so later processes

@@ -239,7 +239,9 @@ struct fh_plan_s {
     size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path (32 rows)
     unsigned long long drift = 0;        // bound of max |D_i| the guards are sized for
-    int32_t slab_pref = 0;               // 0: direction pairs where they apply; 1: never
+    int32_t pair_pref = 0;               // 0: direction pairs where they apply; 1: never
+    int32_t item_counter = 1;            // batched transform: items from the counter (1) or
+                                         // every grid-th item per block (0)
     int32_t n_fft = -1;
     int64_t n_peaks = 0;
     int32_t n_dir = 0;
@@ -832,11 +834,11 @@ static int32_t plan_guard(fh_plan p, bool pairs)
 
 static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
                          int32_t tile, int32_t nwarps, int32_t schedule, cudaStream_t s,
-                         int32_t slab_pref)
+                         int32_t pair_pref, int32_t item_counter)
 {
     const fh_plan_desc &d = p->d;
     // keep the tile's counters within shared memory with this plan's guard cells
-    const bool pairs = schedule != FH_SCHED_PLAIN && plan_pairs(p, n_dir, slab_pref);
+    const bool pairs = schedule != FH_SCHED_PLAIN && plan_pairs(p, n_dir, pair_pref);
     const int32_t guard = plan_guard(p, pairs);
     const int32_t wmax = default_tile(d, p->device, p->mode, nwarps, guard);
     if (tile > wmax) tile = wmax;
@@ -934,7 +936,7 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
             const int64_t cap = (int64_t)p->n_sm * bps;
             const int32_t grid = (int32_t)std::min<int64_t>(job.n_items, cap);
             e = launch_transform(p->mode, tbl, job.n_items, grid, nwarps, smem, guard, s,
-                                 p->sched);
+                                 item_counter ? p->sched : nullptr);
         }
         if (e != cudaSuccess) return cuda_error(e, "transform launch");
         ++p->launches;
@@ -950,7 +952,7 @@ int fh_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
     if (rc) return rc;
     DeviceGuard g(p->device);
     return run_transform(p, dir_begin, n_dir, out_maps, p->tile_cells, p->block_warps,
-                         p->d.schedule, as_stream(stream), p->slab_pref);
+                         p->d.schedule, as_stream(stream), p->pair_pref, p->item_counter);
 }
 
 int fh_copy_profile(fh_plan p, int32_t dir_begin, int32_t n_dir, uint64_t *out, void *stream)
@@ -1031,7 +1033,7 @@ namespace {
 // that JSON file (one entry per line, rewritten atomically by rename) so that
 // later processes on the same GPU model reuse them.
 struct TuneChoice {
-    int32_t tile = 0, warps = 0, pairs = 0;
+    int32_t tile = 0, warps = 0, pairs = 0, counter = 1;
     double ms = 0.0;
 };
 std::mutex g_tune_mu;
@@ -1060,12 +1062,14 @@ void tune_load_locked()
         const char *w = std::strstr(ke, "\"block_warps\": ");
         const char *r = std::strstr(ke, "\"dir_pairs\": ");
         const char *m = std::strstr(ke, "\"ms\": ");
+        const char *ic = std::strstr(ke, "\"item_counter\": ");
         if (!t || !w || !r || std::sscanf(t + 14, "%d", &c.tile) != 1 ||
             std::sscanf(w + 15, "%d", &c.warps) != 1 || std::sscanf(r + 13, "%d", &c.pairs) != 1)
             continue;
         if (m) std::sscanf(m + 6, "%lf", &c.ms);
+        if (ic && std::sscanf(ic + 16, "%d", &c.counter) != 1) continue;
         if (c.tile < 32 || (c.warps != 16 && c.warps != 20 && c.warps != 24 && c.warps != 32) ||
-            (c.pairs != 0 && c.pairs != 1))
+            (c.pairs != 0 && c.pairs != 1) || (c.counter != 0 && c.counter != 1))
             continue;  // not one of ours: ignored
         g_tune[std::string(k, ke)] = c;
     }
@@ -1084,9 +1088,9 @@ void tune_store_locked()
     for (const auto &e : g_tune) {
         std::fprintf(f,
                      "{\"key\": \"%s\", \"tile_cells\": %d, \"block_warps\": %d, "
-                     "\"dir_pairs\": %d, \"ms\": %.6f}%s\n",
-                     e.first.c_str(), e.second.tile, e.second.warps, e.second.pairs, e.second.ms,
-                     ++k < g_tune.size() ? "," : "");
+                     "\"dir_pairs\": %d, \"item_counter\": %d, \"ms\": %.6f}%s\n",
+                     e.first.c_str(), e.second.tile, e.second.warps, e.second.pairs,
+                     e.second.counter, e.second.ms, ++k < g_tune.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
     const bool ok = std::fclose(f) == 0;
@@ -1123,7 +1127,8 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     auto apply = [&](const TuneChoice &c) {
         p->tile_cells = c.tile;
         p->block_warps = c.warps;
-        p->slab_pref = c.pairs ? 0 : 1;
+        p->pair_pref = c.pairs ? 0 : 1;
+        p->item_counter = c.counter;
         if (tile_cells) *tile_cells = p->tile_cells;
         if (block_warps) *block_warps = p->block_warps;
     };
@@ -1154,11 +1159,11 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
                 if (transform_smem_bytes(w, d.k_over, p->mode, nw, guard) > (size_t)lim) continue;
                 bool dup = false;
                 for (const auto &c : cands) dup = dup || (c.tile == w && c.warps == nw && c.pairs == pr);
-                if (!dup) cands.push_back({w, nw, pr, 0.0});
+                if (!dup) cands.push_back({w, nw, pr, 1, 0.0});
             }
         }
     }
-    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps, 0, 0.0});
+    if (cands.empty()) cands.push_back({p->tile_cells, p->block_warps, 0, 1, 0.0});
     // timed on at most 8 of the directions (one window group): the per-item
     // work, and so the best tile, does not depend on how many there are
     cudaEvent_t e0, e1;
@@ -1166,16 +1171,17 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     cudaEventCreate(&e1);
     float best = 1e30f;
     TuneChoice pick = cands[0];
-    for (auto &c : cands) {
+    auto time_choice = [&](TuneChoice &c) {
         const int32_t pref = c.pairs ? 0 : 1;
-        rc = run_transform(p, dir_begin, nt, nullptr, c.tile, c.warps, FH_SCHED_BATCHED, s, pref);
-        if (rc) break;
+        rc = run_transform(p, dir_begin, nt, nullptr, c.tile, c.warps, FH_SCHED_BATCHED, s, pref,
+                           c.counter);
+        if (rc) return;
         float ms = 0.f;
         for (int reps = 1; reps <= 4 && rc == FH_OK; reps *= 4) {
             cudaEventRecord(e0, s);
             for (int r = 0; r < reps && rc == FH_OK; ++r)
                 rc = run_transform(p, dir_begin, nt, nullptr, c.tile, c.warps, FH_SCHED_BATCHED,
-                                   s, pref);
+                                   s, pref, c.counter);
             cudaEventRecord(e1, s);
             if (rc) break;
             cudaEventSynchronize(e1);
@@ -1188,6 +1194,18 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
             best = ms;
             pick = c;
         }
+    };
+    for (auto &c : cands) {
+        time_choice(c);
+        if (rc) break;
+    }
+    // the item schedule of the fastest shape: the counter, or every grid-th item
+    // per block (no counter round trip per item; better balanced only when the
+    // items cost alike)
+    if (rc == FH_OK) {
+        TuneChoice c = pick;
+        c.counter = 0;
+        time_choice(c);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

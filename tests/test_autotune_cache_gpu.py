@@ -1,7 +1,7 @@
 """The autotuner's persistent cache (FH_AUTOTUNE_CACHE).
 
 fh_autotune keeps each grid shape's fastest launch shape (tile width, block
-warps, direction pairs on or off) in a JSON file when FH_AUTOTUNE_CACHE names one; a later
+warps, direction pairs on or off, item schedule) in a JSON file when FH_AUTOTUNE_CACHE names one; a later
 process reads it and takes the cached shape without timing.  Checked on the
 GPU with fresh processes: the shape a first process chose is reused by a
 second one, a hand-written entry is taken as given, and both searches equal
@@ -60,6 +60,7 @@ def test_second_process_reuses_the_cached_shape(tmp_path):
     assert first["oracle_equal"]
     entries = json.load(open(cache))["entries"]
     assert len(entries) == 1 and entries[0]["tile_cells"] == first["tile"]
+    assert entries[0]["item_counter"] in (0, 1) and entries[0]["dir_pairs"] in (0, 1)
     second = _child(cache)
     assert second["oracle_equal"]
     assert (second["tile"], second["warps"]) == (first["tile"], first["warps"])
@@ -70,9 +71,13 @@ def test_a_written_entry_is_taken_as_given(tmp_path):
     probe = _child(cache)
     key = ("%s|mode2|w0|n_f0=%d|n_fdot=%d|K=%d|T=%.17g|n_fft=40|n_dir=2"
            % (probe["gpu"], probe["n_f0"], probe["n_fdot"], probe["k"], probe["t_fft"]))
-    with open(cache, "w") as f:
-        f.write('{"version": 1, "entries": [\n{"key": "%s", "tile_cells": 512, '
-                '"block_warps": 16, "dir_pairs": 0, "ms": 0}\n]}\n' % key)
-    got = _child(cache)
-    assert (got["tile"], got["warps"]) == (512, 16)
-    assert got["oracle_equal"]
+    # every written shape is taken as given and searches like the oracle: single
+    # directions with the item counter, pairs with every grid-th item
+    for pairs, counter in ((0, 1), (1, 0)):
+        with open(cache, "w") as f:
+            f.write('{"version": 1, "entries": [\n{"key": "%s", "tile_cells": 512, '
+                    '"block_warps": 16, "dir_pairs": %d, "item_counter": %d, "ms": 0}\n]}\n'
+                    % (key, pairs, counter))
+        got = _child(cache)
+        assert (got["tile"], got["warps"]) == (512, 16)
+        assert got["oracle_equal"]
