@@ -982,10 +982,17 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         // in the low halves, d_b in the high halves), emit.  The windows of a pair
         // (table or lookup) are the union of its two directions' windows, a
         // superset of either's.
-        auto pass = [&](const int j0, const int R, auto quad_tag, const int dsel) {
+        auto pass = [&](const int j0, const int R, auto quad_tag, const int dsel, auto short_tag) {
             constexpr bool QUAD = decltype(quad_tag)::value;
+            constexpr bool SHORT = decltype(short_tag)::value;
             const bool row_ok = lane < R;
             const int64_t *__restrict__ Ap = dsel ? Ad_b : Ad;
+            // SHORT: a pass of R <= 16 rows (a short last slab) on the unclamped
+            // walk: every lane takes its own slot through the Srows =
+            // 2^ceil(log2 R) rows of its aligned block of Srows lanes, counting
+            // virtual row lane mod Srows in the lane's own bank (row lane ^ g(t));
+            // the 32 / Srows copies of a row are summed before the emit.
+            const int Srows = SHORT ? (R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : R <= 8 ? 8 : 16) : 32;
 
             // zero the counters (with the guard cells in the fast path); reset the chunk counter
             {
@@ -1119,9 +1126,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 // peaks whose position in the other direction is that close, so each
                 // position lies within the pair's distance of it, which the guard also
                 // holds.  QUAD: Y1, Y2 are the same peaks in direction d_b.
-                auto setup = [&](int g, int64_t a1, int64_t a2, int64_t b1, int64_t b2, bool two,
-                                 int owner, int64_t &X1, int64_t &X2, int64_t &Y1, int64_t &Y2,
-                                 int64_t (&e)[5], int32_t &ow) {
+                auto setup = [&](int g, int vlane, int64_t a1, int64_t a2, int64_t b1, int64_t b2,
+                                 bool two, int owner, int64_t &X1, int64_t &X2, int64_t &Y1,
+                                 int64_t &Y2, int64_t (&e)[5], int32_t &ow) {
                     if constexpr (WEIGHTED)
                         ow = __shfl_sync(kFull, wt, owner);
                     else
@@ -1135,7 +1142,8 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
 #pragma unroll
                     for (int b = 0; b < 5; ++b)
                         e[b] = (((lane >> b) & 1) ? odv : ndv) * (int64_t)(1 << b);
-                    const int64_t lane_dv = (int64_t)lane * odv;
+                    // the start row: the lane's own, or its virtual row on a short pass
+                    const int64_t lane_dv = (int64_t)vlane * odv;
                     X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
                     if constexpr (QUAD) Y1 = live ? b1 - ocb - lane_dv : -(int64_t(1) << 32);
                     if (kPairs) {
@@ -1167,8 +1175,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     // S Gray-code steps (row = lane ^ g(t), t < S).  Every (slot, row)
                     // is added once, the 32 lanes stay on 32 banks, and the start
                     // X = A - cb - lane D and the step table are those of a full round.
-                    int S = 32;
-                    if (MODE == FH_MODE_START && fast && T - base <= 16) {
+                    // (A short pass walks Srows steps with one slot per lane instead.)
+                    int S = Srows;
+                    if (!SHORT && MODE == FH_MODE_START && fast && T - base <= 16) {
                         const int L = T - base;
                         S = L <= 1 ? 1 : (L <= 2 ? 2 : (L <= 4 ? 4 : (L <= 8 ? 8 : 16)));
                         const int src = lane & (S - 1);
@@ -1183,7 +1192,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     }
                     int64_t X1, X2 = 0, Y1 = 0, Y2 = 0, e[5];
                     int32_t ow;
-                    setup(base + (lane & (S - 1)), a1, a2, b1, b2, two, owner, X1, X2, Y1, Y2, e, ow);
+                    setup(SHORT ? base + lane : base + (lane & (S - 1)),
+                          SHORT ? (lane & (Srows - 1)) : lane, a1, a2, b1, b2, two, owner, X1, X2,
+                          Y1, Y2, e, ow);
                     if (MODE == FH_MODE_START) {
                         using std::make_integer_sequence;
                         const uint32_t st = cell_stride, ee = (uint32_t)E, ww = (uint32_t)ow;
@@ -1232,6 +1243,19 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             if (sched != nullptr && dsel == 0 && threadIdx.x == 0)
                 *next_item = (int32_t)atomicAdd(sched, 1u);
             __syncthreads();
+            if constexpr (SHORT) {
+                // row r's count is the sum of its copies in banks r + Srows k (a
+                // butterfly over the lane bits >= log2 Srows); cells 0 .. E (the
+                // dump cell too, which the emit may read).  Packed words add half by
+                // half: each half's sum is the count the direction would have in
+                // one word.
+                for (int cell = warp; cell <= E; cell += nwarps) {
+                    int32_t v = H[cell * kRows + lane];
+                    for (int o = 16; o >= Srows; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                    H[cell * kRows + lane] = v;
+                }
+                __syncthreads();
+            }
 
             // emit counts, map and profile
             unsigned long long *prof = reinterpret_cast<unsigned long long *>(J->profile) +
@@ -1455,17 +1479,23 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
             __syncthreads();
         };
 
+        const std::false_type nos{};
         if constexpr (PACK) {
             if (has_b && fast && ((job_packed >> jb) & 1u)) {
-                pass(js, R_slab, std::true_type{}, 0);
+                if (R_slab <= 16)
+                    pass(js, R_slab, std::true_type{}, 0, std::true_type{});
+                else
+                    pass(js, R_slab, std::true_type{}, 0, nos);
             } else {
                 // a single direction, a pair whose counts need whole words, or one
                 // that takes the clamped walk: each direction on its own
-                pass(js, R_slab, std::false_type{}, 0);
-                if (has_b) pass(js, R_slab, std::false_type{}, 1);
+                pass(js, R_slab, std::false_type{}, 0, nos);
+                if (has_b) pass(js, R_slab, std::false_type{}, 1, nos);
             }
+        } else if (MODE == FH_MODE_START && fast && R_slab <= 16) {
+            pass(js, R_slab, std::false_type{}, 0, std::true_type{});
         } else {
-            pass(js, R_slab, std::false_type{}, 0);
+            pass(js, R_slab, std::false_type{}, 0, nos);
         }
     }
     // the last block to finish returns the counter to zero for the next launch
