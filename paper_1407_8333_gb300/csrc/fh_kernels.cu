@@ -842,8 +842,10 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
     (diff_step<Ts>(H0, lane, X, e, E, Wt, K, w), ...);
 }
 
-// One block per work item (direction, slab of spin-down rows, tile of W
-// frequency cells); a persistent grid strides over the items of all jobs.
+// One block per work item (unit = a direction or a pair of them, tile of W
+// frequency cells, slab of spin-down rows; items tile by tile, a tile's slabs
+// together); a persistent grid takes the items of all jobs, each block its
+// first by block index and then (with a launch counter) whichever is next.
 //
 // Shared memory holds the tile's counters H[L][row], L = s - (b0 - K + 1) for
 // a stripe starting at cell s (so L in [0, W + K - 1) covers every stripe that
@@ -854,11 +856,14 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // (precomputed by windows_kernel, else a binary search).  The windowed peaks
 // of the 32 FFTs are dealt out to the lanes in rounds of 32 slots (a warp scan
 // of the per-FFT slot counts; each lane finds the FFT owning its slot from the
-// round's start bits); START mode puts two peaks of one FFT in a slot.  The
-// next round's positions are loaded while the current round is added, and
-// every lane adds its peaks' row updates along the Gray-code row order
-// (pair_step / quad_step / diff_step), so the 32 atomics of one warp
-// instruction always go to 32 different banks.
+// round's start bits); START mode puts two peaks of one FFT in a slot.  For a
+// single direction the next round's positions are loaded while the current
+// round is added; every lane adds its peaks' row updates along the Gray-code
+// row order (pair_step / quad_step / diff_step), so the 32 atomics of one warp
+// instruction always go to 32 different banks.  A short last slab (R <= 16
+// rows, unclamped walk) has a pass of its own in which every lane walks only
+// the rows of its aligned block of 2^ceil(log2 R) lanes and the copies of a
+// row are folded before the emit.
 //
 // PACK (START mode, plain map, several directions): an item covers two sky
 // directions, d_a = 2u and d_b = 2u + 1 of the job, and each counter word holds
@@ -868,7 +873,8 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // atomics per step, quad_step); the item's windows are the union of the two
 // directions' windows, and the guard cells hold in addition the largest cell
 // distance between a peak's two positions (the window pre-pass measures it per
-// pair; a pair beyond the job's allowance takes the clamped walk).  A
+// pair; a pair beyond the job's allowance walks each direction on its own,
+// clamped).  A
 // stripe-start count stays below 2^16 when no FFT has two peaks within one cell
 // (each FFT then starts at most one stripe per cell and row) and n_fft < 2^16;
 // the window pre-pass flags the first condition per job (`dense`), and a
