@@ -569,3 +569,17 @@ def test_ffts_with_more_peaks_than_staged_are_read_from_global_memory(fh, oracle
     for tile, warps in ((0, 0), (256, 8)):
         g = run_gpu(fh, inp, pp, mode=mode, tile=tile, warps=warps)
         compare(g, o, pp, inp.t.shape[0])
+
+
+@pytest.mark.parametrize("n_fdot", [1, 2, 34, 35, 36, 40, 48, 49, 64])
+def test_short_last_slab_every_width(fh, oracle_mod, n_fdot):
+    """A last slab of R <= 16 rows is walked in 2^ceil(log2 R) steps with the
+    row copies folded before the emit (1, 2, 3, 4, 8, 16 rows here; 17 and 32
+    take the full walk), for a pair of directions and a single one (three
+    directions), in START mode; maps, profiles and candidates equal the
+    oracle's."""
+    inp, pp = synth.random_case(500 + n_fdot, n_fft=24, n_bins=200, k_over=10, n_fdot=n_fdot,
+                                n_dir=3, p=0.3)
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    g = run_gpu(fh, inp, pp, mode=2, tile=320, warps=8)
+    compare(g, o, pp, inp.t.shape[0])
