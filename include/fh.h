@@ -37,8 +37,9 @@
  * stream-ordered: unless a function says it synchronises, it only enqueues
  * work, and device buffers the caller passed must stay valid until that work
  * completes.  The caller owns every buffer it passes; the library owns the
- * plan's internal buffers.  A plan is used by one host thread at a time; a
- * server is thread-safe.
+ * plan's internal buffers.  A plan is used by one host thread at a time, and
+ * its work on one stream at a time (its buffers, the transform's item counter
+ * among them, are shared by every call on the plan); a server is thread-safe.
  */
 #ifndef FH_H
 #define FH_H
