@@ -146,10 +146,11 @@ TRAFFIC_JSON = os.path.join(ROOT, "profiles", "transform_traffic.json")
 
 
 def transform_source_sha1():
-    """SHA-1 of the transform section of the kernel source (a4 + a5 + profile)."""
+    """SHA-1 of the transform kernel's source: from its first helper (the cell
+    of a fixed-point position) to the end of the a4 + a5 + profile section."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_1407_8333_gb300", "csrc", "fh_kernels.cu")).read()
-    a = src.index("// ---------------------------------------------------------------- a4 + a5 + profile")
+    a = src.index("// Cell of a 32.32 fixed-point position")
     b = src.index("// ---------------------------------------------------------------- a6")
     return hashlib.sha1(src[a:b].encode()).hexdigest()
 

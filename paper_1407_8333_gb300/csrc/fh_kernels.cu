@@ -562,6 +562,9 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
     const int64_t nf = J.n_fft;
     const int64_t slab_stride = (int64_t)J.n_tiles * nf;
     uint32_t *out = windows + (int64_t)unit * J.n_slabs * slab_stride;
+    // every FFT of the block staged (the usual case): the slab loop reads shared
+    // memory only; else the whole block takes the global-memory searches
+    const bool all_staged = __syncthreads_and(staged ? 1 : 0) != 0;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kTiles) {
         const int nt = min(kTiles, J.n_tiles - t0);
         // the lane's tiles: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
@@ -589,7 +592,13 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
         const int64_t span_full = (int64_t)(RS - 1) * dv;
         int64_t u = s0 + (span_full < 0 ? span_full : 0);
         int64_t w = s0 + (span_full > 0 ? span_full : 0);
-        for (int slab = 0; slab < J.n_slabs; ++slab) {
+        // One slab: its bounds, the searches (FIRST: binary; later slabs: steps
+        // in the direction of D, UP for D >= 0, both bounds moving monotonically
+        // with the slab), the entries.
+        auto slab_pass = [&](auto first_tag, auto staged_tag, auto up_tag, const int slab) {
+            constexpr bool FIRST = decltype(first_tag)::value;
+            constexpr bool STG = decltype(staged_tag)::value;
+            constexpr bool UP = decltype(up_tag)::value;
             if (slab == J.n_slabs - 1) {
                 // the last slab may hold fewer rows
                 const int R = J.n_fdot - slab * RS;
@@ -603,15 +612,30 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
 #pragma unroll
             for (int di = 0; di < ND; ++di) {
                 if (di >= nd) break;
-                const int32_t *cs = &cell_s[di][f][kWinPad];
-                const int64_t *Ai = A0 + (int64_t)di * J.n_peaks + o0;
-                if (!staged) {
+                if constexpr (STG) {
+                    // every lane searches (the sentinels bound the tiles past the last one)
+                    const int32_t *cs = &cell_s[di][f][kWinPad];
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        if constexpr (FIRST) {
+                            qa[di][m] = lower_bound_cell(cs, n, ul + blo[m]);
+                            qb[di][m] = lower_bound_cell(cs, n, wh + bhi[m]);
+                        } else if constexpr (UP) {
+                            qa[di][m] = step_up(cs, qa[di][m], ul + blo[m]);
+                            qb[di][m] = step_up(cs, qb[di][m], wh + bhi[m]);
+                        } else {
+                            qa[di][m] = step_down(cs, qa[di][m], ul + blo[m]);
+                            qb[di][m] = step_down(cs, qb[di][m], wh + bhi[m]);
+                        }
+                    }
+                } else {
+                    const int64_t *Ai = A0 + (int64_t)di * J.n_peaks + o0;
 #pragma unroll
                     for (int m = 0; m < M; ++m) {
                         if (!ok[m]) continue;
                         const int xl = ul + blo[m], xh = wh + bhi[m];
                         int qa_m = qa[di][m], qb_m = qb[di][m];
-                        if (slab == 0) {
+                        if constexpr (FIRST) {
                             qa_m = lower_bound_cell_g(Ai, n, xl);
                             qb_m = lower_bound_cell_g(Ai, n, xh);
                         } else {
@@ -622,25 +646,6 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
                         }
                         qa[di][m] = qa_m;
                         qb[di][m] = qb_m;
-                    }
-                } else if (slab == 0) {
-                    // every lane searches (the sentinels bound the tiles past the last one)
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        qa[di][m] = lower_bound_cell(cs, n, ul + blo[m]);
-                        qb[di][m] = lower_bound_cell(cs, n, wh + bhi[m]);
-                    }
-                } else if (dv >= 0) {
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        qa[di][m] = step_up(cs, qa[di][m], ul + blo[m]);
-                        qb[di][m] = step_up(cs, qb[di][m], wh + bhi[m]);
-                    }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        qa[di][m] = step_down(cs, qa[di][m], ul + blo[m]);
-                        qb[di][m] = step_down(cs, qb[di][m], wh + bhi[m]);
                     }
                 }
             }
@@ -669,7 +674,18 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
             }
             u += RS * dv;
             w += RS * dv;
-        }
+        };
+        auto run = [&](auto staged_tag, auto up_tag) {
+            slab_pass(std::true_type{}, staged_tag, up_tag, 0);
+            for (int slab = 1; slab < J.n_slabs; ++slab)
+                slab_pass(std::false_type{}, staged_tag, up_tag, slab);
+        };
+        if (!all_staged)
+            run(std::false_type{}, std::true_type{});  // (both directions handled there)
+        else if (dv >= 0)
+            run(std::true_type{}, std::true_type{});
+        else
+            run(std::true_type{}, std::false_type{});
     }
 }
 
