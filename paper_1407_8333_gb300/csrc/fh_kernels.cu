@@ -417,22 +417,29 @@ __device__ __forceinline__ void lookup_window(const int64_t *__restrict__ Ad,
 // on each side; those extra peaks reach only guard cells (the transform's
 // guard keeps a margin of two cells), so they change no count.  For a pair of
 // directions (PAIR) the entry is the union, as one index range, of the two
-// directions' windows.
+// directions' windows: with c_max(k) and c_min(k) the larger and the smaller
+// of peak k's two cells (both non-decreasing in k, as each direction's cells
+// are), the union of [lb_a(x), lb_a(y)) and [lb_b(x), lb_b(y)) is
+// [lb_max(x), lb_min(y)), lb the first index whose cell is >= the bound -- so a
+// pair costs two searches per entry, like one direction.  (Were one window
+// empty, this range could also hold peaks whose two cells lie on both sides of
+// the tile; the guard allowance for the pair distance makes that impossible
+// on the paired walk, and the clamped walk takes any range.)
 //
 // A block takes 8 FFTs of one unit (a direction, or a pair of them): warp w
-// copies FFT w's peak cells (ascending) of each direction into shared memory
+// copies FFT w's peak cells (for a pair: c_max and c_min) into shared memory
 // once, between one sentinel on each side, four loads per lane in flight (an
 // FFT with more than kPeaks - 2 peaks is read from global memory, with bounds
-// checks).  Lane l of warp w then takes FFT l mod 8 and tiles 4 w + l / 8 +
-// 32 m (M per pass, M = 1 .. 3 from the tile count, so that the per-slab work
-// -- the 64-bit bounds, the branches -- is shared by M entries and the M
-// searches of a slab are independent), and walks the slabs in order: the
-// first slab's bounds come from a binary search, each later one from a step in
-// the direction of its FFT's drift D (both bounds move monotonically with the
-// slab, by 32 D; D does not depend on the direction).  A warp's 32 entries of a
-// slab are 4 tiles x 8 consecutive FFTs, i.e. four 32-byte runs of the
-// [slab][tile][FFT] table, so each warp writes its own runs and the slab loop
-// has no barrier.
+// checks, by the whole block).  Lane l of warp w then takes FFT l mod 8 and
+// tiles 4 w + l / 8 + 32 m (M per pass, M = 1 .. 3 from the tile count, so
+// that the per-slab work -- the 64-bit bounds, the branches -- is shared by M
+// entries and the M searches of a slab are independent), and walks the slabs
+// in order: the first slab's bounds come from a binary search, each later one
+// from a step in the direction of its FFT's drift D (both bounds move
+// monotonically with the slab, by 32 D; D does not depend on the direction).
+// A warp's 32 entries of a slab are 4 tiles x 8 consecutive FFTs, i.e. four
+// 32-byte runs of the [slab][tile][FFT] table, so each warp writes its own
+// runs and the slab loop has no barrier.
 // grid (ceil(n_fft / 8), units), 256 threads.
 constexpr int kWinPad = 1;
 constexpr int kWinMaxM = 3;
@@ -472,21 +479,42 @@ __device__ __forceinline__ int step_down(const int32_t *a, int q, int x)
     return q;
 }
 
+// cell of peak k for the lower (HI = false: the larger of a pair's two cells)
+// or the upper (HI = true: the smaller) window bound; Ab = Aa for one direction
+template <bool HI>
+__device__ __forceinline__ int pair_cell_g(const int64_t *Aa, const int64_t *Ab, int k)
+{
+    const int ca = global_cell(Aa, k), cb = global_cell(Ab, k);
+    return HI ? min(ca, cb) : max(ca, cb);
+}
+template <bool HI>
+__device__ __forceinline__ int lower_bound_pair_g(const int64_t *Aa, const int64_t *Ab, int n,
+                                                  int x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (pair_cell_g<HI>(Aa, Ab, m) < x) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+
 template <int M, bool PAIR>
 __global__ void __launch_bounds__(256, 4)
 windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
 {
     constexpr int kTiles = 32 * M;  // tiles per pass
-    constexpr int ND = PAIR ? 2 : 1;
-    // staged peaks per FFT and direction (the static shared memory holds 48 KB)
+    constexpr int NR = PAIR ? 2 : 1;  // staged rows per FFT: c_max, c_min (PAIR)
+    // staged peaks per FFT (the static shared memory holds 48 KB)
     constexpr int kPeaks = PAIR ? 736 : 1024;
     // rows padded by one word: lanes on different FFTs fall on different banks
-    __shared__ int32_t cell_s[ND][8][kPeaks + 1];
+    __shared__ int32_t cell_s[NR][8][kPeaks + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int unit = blockIdx.y;
     const int nd = PAIR ? min(2, J.n_dir - 2 * unit) : 1;  // directions of the unit
     const int d_first = J.dir_begin + (PAIR ? 2 * unit : unit);
     const int64_t *A0 = J.A + (int64_t)d_first * J.n_peaks;
+    const int64_t *A1 = nd == 2 ? A0 + J.n_peaks : A0;  // the pair's second direction
     // the transform merges into each direction's profile by atomicMax from 0:
     // the blocks of the unit clear it here, a strided slice each
     for (int di = 0; di < nd; ++di) {
@@ -497,9 +525,9 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
     }
     {
         // warp w stages FFT w of the block; with J.dense it also flags two
-        // consecutive peaks whose cells differ by at most 1 (positions less
-        // than one cell apart imply that), which the packed transform's 16-bit
-        // counters cannot take
+        // consecutive peaks whose cells (in either direction) differ by at most
+        // 1 (positions less than one cell apart imply that), which the packed
+        // transform's 16-bit counters cannot take
         const int is = blockIdx.x * 8 + warp;
         const bool ls = is < J.n_fft;
         const int64_t os = ls ? J.offsets[is] : 0;
@@ -507,31 +535,42 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
         const bool stage = ns + 2 * kWinPad <= kPeaks;
         bool close = false;
         if (stage || J.dense != nullptr) {
-            for (int di = 0; di < nd; ++di) {
-                const int64_t *As = A0 + (int64_t)di * J.n_peaks + os;
-                int32_t *c = &cell_s[PAIR ? di : 0][warp][kWinPad];
-                int carry = 0;
-                for (int k0 = 0; k0 < ns; k0 += 128) {
-                    int cur[4];
+            const int64_t *Aa = A0 + os, *Ab = A1 + os;
+            int32_t *c0 = &cell_s[0][warp][kWinPad];
+            int32_t *c1 = &cell_s[NR - 1][warp][kWinPad];
+            int carry_a = 0, carry_b = 0;
+            for (int k0 = 0; k0 < ns; k0 += 128) {
+                int ca[4], cb[4];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int k = k0 + 32 * r + lane;
-                        cur[r] = k < ns ? global_cell(As, k) : 0;
+                for (int r = 0; r < 4; ++r) {
+                    const int k = k0 + 32 * r + lane;
+                    ca[r] = k < ns ? global_cell(Aa, k) : 0;
+                    cb[r] = (PAIR && k < ns) ? global_cell(Ab, k) : ca[r];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int k = k0 + 32 * r + lane;
+                    if (stage && k < ns) {
+                        c0[k] = max(ca[r], cb[r]);
+                        if (PAIR) c1[k] = min(ca[r], cb[r]);
                     }
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int k = k0 + 32 * r + lane;
-                        if (stage && k < ns) c[k] = cur[r];
-                        int prev = __shfl_up_sync(kFull, cur[r], 1);
-                        if (lane == 0) prev = carry;
-                        if (k > 0 && k < ns && (int64_t)cur[r] - (int64_t)prev <= 1) close = true;
-                        carry = __shfl_sync(kFull, cur[r], 31);
+                    int pa = __shfl_up_sync(kFull, ca[r], 1);
+                    if (lane == 0) pa = carry_a;
+                    if (k > 0 && k < ns && (int64_t)ca[r] - (int64_t)pa <= 1) close = true;
+                    carry_a = __shfl_sync(kFull, ca[r], 31);
+                    if constexpr (PAIR) {
+                        int pb = __shfl_up_sync(kFull, cb[r], 1);
+                        if (lane == 0) pb = carry_b;
+                        if (k > 0 && k < ns && (int64_t)cb[r] - (int64_t)pb <= 1) close = true;
+                        carry_b = __shfl_sync(kFull, cb[r], 31);
                     }
                 }
-                if (stage && lane < kWinPad) {
-                    c[-1 - lane] = INT_MIN;
-                    c[ns + lane] = INT_MAX;
-                }
+            }
+            if (stage && lane < kWinPad) {
+                c0[-1 - lane] = INT_MIN;
+                c0[ns + lane] = INT_MAX;
+                c1[-1 - lane] = INT_MIN;
+                c1[ns + lane] = INT_MAX;
             }
             if (J.dense != nullptr && __any_sync(kFull, close) && lane == 0) atomicOr(J.dense, 1);
         }
@@ -540,7 +579,7 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
             // differ by f (r_b - r_a) KT (+ rounding), linear in f, so it is largest
             // at the FFT's first or last peak (ascending frequencies); 2 cells of
             // rounding margin
-            const int64_t *Aa = A0 + os, *Ab = Aa + J.n_peaks;
+            const int64_t *Aa = A0 + os, *Ab = A1 + os;
             const int64_t d0 = (int64_t)global_cell(Ab, 0) - global_cell(Aa, 0);
             const int64_t d1 = (int64_t)global_cell(Ab, ns - 1) - global_cell(Aa, ns - 1);
             const int64_t dm = max(d0 < 0 ? -d0 : d0, d1 < 0 ? -d1 : d1) + 2;
@@ -562,13 +601,16 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
     const int64_t nf = J.n_fft;
     const int64_t slab_stride = (int64_t)J.n_tiles * nf;
     uint32_t *out = windows + (int64_t)unit * J.n_slabs * slab_stride;
+    const int32_t *cs_lo = &cell_s[0][f][kWinPad];       // lower bounds: c_max
+    const int32_t *cs_hi = &cell_s[NR - 1][f][kWinPad];  // upper bounds: c_min
+    const int64_t *Aa = A0 + o0, *Ab = A1 + o0;
     // every FFT of the block staged (the usual case): the slab loop reads shared
     // memory only; else the whole block takes the global-memory searches
     const bool all_staged = __syncthreads_and(staged ? 1 : 0) != 0;
     for (int t0 = 0; t0 < J.n_tiles; t0 += kTiles) {
         const int nt = min(kTiles, J.n_tiles - t0);
         // the lane's tiles: lower bound = Lc + b0 - K + 1, upper bound = Hc + b0 + Wt
-        int blo[M], bhi[M], qa[ND][M], qb[ND][M];
+        int blo[M], bhi[M], qa[M], qb[M];
         bool ok[M];
         uint32_t *dst[M];
 #pragma unroll
@@ -578,11 +620,8 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
             const int b0 = (t0 + tt) * W;
             blo[m] = b0 - K + 1;
             bhi[m] = b0 + min(W, J.n_f0 - b0);
-#pragma unroll
-            for (int di = 0; di < ND; ++di) {
-                qa[di][m] = 0;
-                qb[di][m] = 0;
-            }
+            qa[m] = 0;
+            qb[m] = 0;
             dst[m] = out + (int64_t)(t0 + tt) * nf + i;
         }
         // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
@@ -609,64 +648,44 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
             }
             const int ul = (int)(u >> 32);
             const int wh = (int)(w >> 32) + ((uint32_t)w != 0u ? 1 : 0);
+            if constexpr (STG) {
+                // every lane searches (the sentinels bound the tiles past the last one)
 #pragma unroll
-            for (int di = 0; di < ND; ++di) {
-                if (di >= nd) break;
-                if constexpr (STG) {
-                    // every lane searches (the sentinels bound the tiles past the last one)
-                    const int32_t *cs = &cell_s[di][f][kWinPad];
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        if constexpr (FIRST) {
-                            qa[di][m] = lower_bound_cell(cs, n, ul + blo[m]);
-                            qb[di][m] = lower_bound_cell(cs, n, wh + bhi[m]);
-                        } else if constexpr (UP) {
-                            qa[di][m] = step_up(cs, qa[di][m], ul + blo[m]);
-                            qb[di][m] = step_up(cs, qb[di][m], wh + bhi[m]);
-                        } else {
-                            qa[di][m] = step_down(cs, qa[di][m], ul + blo[m]);
-                            qb[di][m] = step_down(cs, qb[di][m], wh + bhi[m]);
-                        }
+                for (int m = 0; m < M; ++m) {
+                    if constexpr (FIRST) {
+                        qa[m] = lower_bound_cell(cs_lo, n, ul + blo[m]);
+                        qb[m] = lower_bound_cell(cs_hi, n, wh + bhi[m]);
+                    } else if constexpr (UP) {
+                        qa[m] = step_up(cs_lo, qa[m], ul + blo[m]);
+                        qb[m] = step_up(cs_hi, qb[m], wh + bhi[m]);
+                    } else {
+                        qa[m] = step_down(cs_lo, qa[m], ul + blo[m]);
+                        qb[m] = step_down(cs_hi, qb[m], wh + bhi[m]);
                     }
-                } else {
-                    const int64_t *Ai = A0 + (int64_t)di * J.n_peaks + o0;
+                }
+            } else {
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        if (!ok[m]) continue;
-                        const int xl = ul + blo[m], xh = wh + bhi[m];
-                        int qa_m = qa[di][m], qb_m = qb[di][m];
-                        if constexpr (FIRST) {
-                            qa_m = lower_bound_cell_g(Ai, n, xl);
-                            qb_m = lower_bound_cell_g(Ai, n, xh);
-                        } else {
-                            while (qa_m < n && global_cell(Ai, qa_m) < xl) ++qa_m;
-                            while (qa_m > 0 && global_cell(Ai, qa_m - 1) >= xl) --qa_m;
-                            while (qb_m < n && global_cell(Ai, qb_m) < xh) ++qb_m;
-                            while (qb_m > 0 && global_cell(Ai, qb_m - 1) >= xh) --qb_m;
-                        }
-                        qa[di][m] = qa_m;
-                        qb[di][m] = qb_m;
+                for (int m = 0; m < M; ++m) {
+                    if (!ok[m]) continue;
+                    const int xl = ul + blo[m], xh = wh + bhi[m];
+                    int qa_m = qa[m], qb_m = qb[m];
+                    if constexpr (FIRST) {
+                        qa_m = lower_bound_pair_g<false>(Aa, Ab, n, xl);
+                        qb_m = lower_bound_pair_g<true>(Aa, Ab, n, xh);
+                    } else {
+                        while (qa_m < n && pair_cell_g<false>(Aa, Ab, qa_m) < xl) ++qa_m;
+                        while (qa_m > 0 && pair_cell_g<false>(Aa, Ab, qa_m - 1) >= xl) --qa_m;
+                        while (qb_m < n && pair_cell_g<true>(Aa, Ab, qb_m) < xh) ++qb_m;
+                        while (qb_m > 0 && pair_cell_g<true>(Aa, Ab, qb_m - 1) >= xh) --qb_m;
                     }
+                    qa[m] = qa_m;
+                    qb[m] = qb_m;
                 }
             }
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 if (ok[m]) {
-                    int lo = qa[0][m], hi = max(qa[0][m], qb[0][m]);
-                    if (PAIR && nd == 2) {
-                        // union with the pair's second direction, as one index range
-                        const int lo2 = qa[ND - 1][m], hi2 = max(qa[ND - 1][m], qb[ND - 1][m]);
-                        if (hi2 > lo2) {
-                            if (hi > lo) {
-                                lo = min(lo, lo2);
-                                hi = max(hi, hi2);
-                            } else {
-                                lo = lo2;
-                                hi = hi2;
-                            }
-                        }
-                    }
-                    const int cnt = hi - lo;
+                    const int lo = qa[m], cnt = max(qa[m], qb[m]) - lo;
                     *dst[m] = (lo < 0xFFFF && cnt < 0xFFFF) ? (uint32_t)lo | ((uint32_t)cnt << 16)
                                                             : kWinLookup;
                 }
