@@ -146,6 +146,17 @@ bool pairs_apply(const fh_plan_desc &d, int device, int32_t n_fft, int32_t n_dir
            (size_t)max_optin_smem(device);
 }
 
+bool rows_apply(const fh_plan_desc &d, int device, int32_t n_fft, int32_t n_dir,
+                unsigned long long drift)
+{
+    if (n_dir != 1 || d.n_fdot <= kRows || n_fft <= 0 || n_fft >= 65536 ||
+        (int64_t)d.k_over * n_fft >= ((int64_t)1 << 25))
+        return false;
+    const int32_t g = guard_for(drift, 2 * kRows - 1);
+    return transform_smem_bytes(256, d.k_over, FH_MODE_START, 32, g) <=
+           (size_t)max_optin_smem(device);
+}
+
 int validate_desc(const fh_plan_desc &d)
 {
     auto bad = [](const char *m) { return set_error(FH_ERR_INVALID_ARG, "plan: %s", m); };
@@ -821,15 +832,23 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
 
 // Direction pairs for n_dir directions of the plan's current peakmap (pref 0:
 // where they apply; 1: never).
-static bool plan_pairs(fh_plan p, int32_t n_dir, int32_t pref)
+// What an item of n_dir directions of the plan's current peakmap pairs in
+// the shared counter words (pref 0: where it applies; 1: never): 0 nothing,
+// 1 two directions, 2 (one direction) two 32-row halves of a 64-row slab.
+enum : int32_t { kPairNone = 0, kPairDirs = 1, kPairRows = 2 };
+static int32_t plan_pairs(fh_plan p, int32_t n_dir, int32_t pref)
 {
-    if (pref == 1 || p->mode != FH_MODE_START || p->weighted) return false;
-    return pairs_apply(p->d, p->device, p->n_fft, n_dir, p->drift);
+    if (pref == 1 || p->mode != FH_MODE_START || p->weighted) return kPairNone;
+    if (pairs_apply(p->d, p->device, p->n_fft, n_dir, p->drift)) return kPairDirs;
+    if (rows_apply(p->d, p->device, p->n_fft, n_dir, p->drift)) return kPairRows;
+    return kPairNone;
 }
 
-static int32_t plan_guard(fh_plan p, bool pairs)
+static int32_t plan_guard(fh_plan p, int32_t kind)
 {
-    return pairs ? p->guard + pair_delta(p->d) : p->guard;
+    return kind == kPairDirs   ? p->guard + pair_delta(p->d)
+           : kind == kPairRows ? std::max(p->guard, guard_for(p->drift, 2 * kRows - 1))
+                               : p->guard;
 }
 
 static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *out_maps,
@@ -838,8 +857,9 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
 {
     const fh_plan_desc &d = p->d;
     // keep the tile's counters within shared memory with this plan's guard cells
-    const bool pairs = schedule != FH_SCHED_PLAIN && plan_pairs(p, n_dir, pair_pref);
-    const int32_t guard = plan_guard(p, pairs);
+    const int32_t kind = schedule != FH_SCHED_PLAIN ? plan_pairs(p, n_dir, pair_pref) : kPairNone;
+    const bool pairs = kind == kPairDirs;
+    const int32_t guard = plan_guard(p, kind);
     const int32_t wmax = default_tile(d, p->device, p->mode, nwarps, guard);
     if (tile > wmax) tile = wmax;
     const size_t smem = transform_smem_bytes(tile, d.k_over, p->mode, nwarps, guard);
@@ -869,10 +889,12 @@ static int run_transform(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *o
     job.k_over = d.k_over;
     job.tile_cells = tile;
     job.dir_pairs = pairs ? 1 : 0;
+    job.row_pairs = kind == kPairRows ? 1 : 0;
     job.dense = p->dense;
     job.unit_delta = p->unit_delta;
     job.delta_alloc = pair_delta(d);
-    job.n_slabs = (d.n_fdot + kRows - 1) / kRows;
+    const int32_t slab_rows = kind == kPairRows ? 2 * kRows : kRows;
+    job.n_slabs = (d.n_fdot + slab_rows - 1) / slab_rows;
     job.n_tiles = (d.n_f0 + tile - 1) / tile;
     const int64_t per_dir = (int64_t)job.n_slabs * job.n_tiles;
     int bps = transform_blocks_per_sm(p->mode, nwarps, smem);
@@ -1146,10 +1168,11 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
     const int lim = max_optin_smem(p->device);
     std::vector<TuneChoice> cands;
     const int32_t nt = std::min<int32_t>(n_dir, 8);
-    const bool pairs_ok = plan_pairs(p, nt, 0);
+    const int32_t pair_kind = plan_pairs(p, nt, 0);
+    const bool pairs_ok = pair_kind != kPairNone;
     for (int pr : {1, 0}) {
         if (pr && !pairs_ok) continue;
-        const int32_t guard = plan_guard(p, pr != 0);
+        const int32_t guard = plan_guard(p, pr ? pair_kind : kPairNone);
         for (int nw : {24, 20, 32, 16}) {
             // DIFF kernels: 512 / 1024 threads
             if ((nw == 24 || nw == 20) && p->mode == FH_MODE_DIFF) continue;

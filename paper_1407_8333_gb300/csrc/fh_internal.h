@@ -54,9 +54,13 @@ struct TransformJob {
                              // peak's two positions (+2), from the window pre-pass
     int32_t delta_alloc;     // (dir_pairs) the part of the guard that holds that distance;
                              // a pair beyond it takes the clamped walk
+    int32_t row_pairs;       // 1 (plain START map of one direction, not with dir_pairs):
+                             // slabs of 64 rows, rows j0 + r and j0 + 32 + r in the low and
+                             // high halves of one shared word; the window table is per
+                             // 64-row slab and the guard holds 63 rows of drift
     int64_t n_peaks;
     int64_t item_begin;      // first work item of this job in the launch
-    int64_t n_items;         // n_dir * n_slabs * n_tiles
+    int64_t n_items;         // units * n_slabs * n_tiles
     int32_t n_fft, n_f0, n_fdot, k_over;
     int32_t tile_cells;      // W
     int32_t n_slabs, n_tiles;
@@ -207,6 +211,12 @@ unsigned long long host_drift(const fh_plan_desc &d, double kt, const double *t,
 // guard of drift bound `drift` plus the pair allowance pair_delta(d).
 bool pairs_apply(const fh_plan_desc &d, int device, int32_t n_fft, int32_t n_dir,
                  unsigned long long drift);
+// Whether one direction (n_dir == 1) of a plain START map may pair the two
+// 32-row halves of 64-row slabs in the counters' 16-bit halves: the same
+// 16-bit and key conditions as for direction pairs, and a tile fits with the
+// guard of 63 rows of drift.
+bool rows_apply(const fh_plan_desc &d, int device, int32_t n_fft, int32_t n_dir,
+                unsigned long long drift);
 // Cells of guard kept for the distance between a peak's positions in the two
 // directions of a pair: neighbouring directions of a sky grid at the Doppler
 // resolution differ by about one input bin (K cells); 2 K + 4 leaves room.

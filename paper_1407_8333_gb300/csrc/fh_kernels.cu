@@ -627,7 +627,7 @@ windows_kernel(const TransformJob J, uint32_t *__restrict__ windows)
         // bounds of slab j0 = 32 s: floor((S0 + j0 D + min(0, (R-1) D)) / 2^32) and
         // ceil((S0 + j0 D + max(0, (R-1) D)) / 2^32) (+ the tile's terms), kept
         // as 64-bit sums that advance by 32 D per full slab
-        constexpr int RS = kRows;
+        const int RS = J.row_pairs ? 2 * kRows : kRows;  // rows per slab
         const int64_t span_full = (int64_t)(RS - 1) * dv;
         int64_t u = s0 + (span_full < 0 ? span_full : 0);
         int64_t w = s0 + (span_full > 0 ? span_full : 0);
@@ -921,11 +921,12 @@ __device__ __forceinline__ void diff_steps(std::integer_sequence<int, Ts...>, in
 // with the other segments' totals as carry-in.  The count goes to the map
 // (optional) and the warp's max over rows (smallest row on ties) to the
 // direction's profile by a 64-bit atomicMax, which is order-independent.
-template <int MODE, int MAXT, bool WEIGHTED, bool PACK>
+template <int MODE, int MAXT, bool WEIGHTED, int PACK>
 __global__ void __launch_bounds__(MAXT, 1)
 transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int32_t hist_words,
                  int32_t guard, uint32_t cell_stride, unsigned int *__restrict__ sched)
 {
+    // PACK: 0 full-word counters; 1 direction pairs; 2 row pairs (one direction)
     static_assert(!PACK || (MODE == FH_MODE_START && !WEIGHTED), "packed counters: plain START");
     extern __shared__ __align__(16) int32_t smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -960,7 +961,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
     for (int j = 0; j < tbl.n_jobs; ++j) {
         const TransformJob &Jt = tbl.job[j];
         if (Jt.dmax != nullptr && Jt.err != nullptr && *Jt.err == 0 &&
-            guard_for(*Jt.dmax) + (PACK && Jt.dir_pairs ? Jt.delta_alloc : 0) <= guard)
+            guard_for(*Jt.dmax, PACK == 2 && Jt.row_pairs ? 2 * kRows - 1 : kRows - 1) +
+                    (PACK == 1 && Jt.dir_pairs ? Jt.delta_alloc : 0) <=
+                guard)
             job_fast |= 1u << j;
         if (PACK && Jt.dense != nullptr && *Jt.dense == 0) job_packed |= 1u << j;
     }
@@ -990,12 +993,16 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         const int slab = r2 - tile * J->n_slabs;
         const int K = J->k_over, W = J->tile_cells, n_f0 = J->n_f0, n_fdot = J->n_fdot;
         const int n_fft = J->n_fft;
-        const int js = slab * kRows;
-        const int R_slab = min(kRows, n_fdot - js);
+        // (PACK) row pairs: one direction in slabs of 64 rows, rows j0 .. j0 + 31 in
+        // the low halves and j0 + 32 .. j0 + 63 in the high halves of the counters
+        const bool rowp = PACK == 2 && J->row_pairs;
+        const int srows = rowp ? 2 * kRows : kRows;
+        const int js = slab * srows;
+        const int R_slab = min(srows, n_fdot - js);
         const int b0 = tile * W;
         const int Wt = min(W, n_f0 - b0);
         const int E = Wt + K - 1;
-        const bool paired = PACK && J->dir_pairs;
+        const bool paired = PACK == 1 && J->dir_pairs;
         const int d_rel = paired ? 2 * unit : unit;  // d_a, relative to the job's first
         const bool has_b = paired && d_rel + 1 < J->n_dir;
         const int d_abs = J->dir_begin + d_rel;
@@ -1024,7 +1031,10 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         // (table or lookup) are the union of its two directions' windows, a
         // superset of either's.
         auto pass = [&](const int j0, const int R, auto quad_tag, const int dsel, auto short_tag) {
-            constexpr bool QUAD = decltype(quad_tag)::value;
+            // quad_tag: 0 one direction, 1 a pair of directions, 2 (ROWQ) the two
+            // 32-row halves of a 64-row slab of one direction
+            constexpr bool QUAD = decltype(quad_tag)::value != 0;
+            constexpr bool ROWQ = decltype(quad_tag)::value == 2;
             constexpr bool SHORT = decltype(short_tag)::value;
             const bool row_ok = lane < R;
             const int64_t *__restrict__ Ap = dsel ? Ad_b : Ad;
@@ -1083,7 +1093,7 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     int64_t cbs;
                     lookup_window(Ap, offs, S0, Dt, n_fft, (c << 5) + lane, js, R_slab, base_shift,
                                   e_fixed, cbs, dv, q0, n);
-                    if constexpr (QUAD) {
+                    if (QUAD && !ROWQ) {
                         // the union (as one index range) with the other direction's window
                         int64_t cb2, dv2, q0b;
                         int nb;
@@ -1145,8 +1155,9 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                         a1 = live ? __ldg(Ap + k) : 0;
                         a2 = two ? __ldg(Ap + k + 1) : 0;
                         if constexpr (QUAD) {
-                            b1 = live ? __ldg(Ad_b + k) : 0;
-                            b2 = two ? __ldg(Ad_b + k + 1) : 0;
+                            // (row pairs: the same peaks 32 rows further, from a1, a2)
+                            b1 = (live && !ROWQ) ? __ldg(Ad_b + k) : 0;
+                            b2 = (two && !ROWQ) ? __ldg(Ad_b + k + 1) : 0;
                         }
                     } else {
                         two = false;
@@ -1186,14 +1197,18 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                     // the start row: the lane's own, or its virtual row on a short pass
                     const int64_t lane_dv = (int64_t)vlane * odv;
                     X1 = live ? a1 - ocb - lane_dv : -(int64_t(1) << 32);
-                    if constexpr (QUAD) Y1 = live ? b1 - ocb - lane_dv : -(int64_t(1) << 32);
+                    // (row pairs: row r + 32 of the same peak is 32 D further down)
+                    const int64_t y_off = ROWQ ? odv * kRows : 0;
+                    if constexpr (QUAD)
+                        Y1 = live ? (ROWQ ? a1 : b1) - ocb - lane_dv - y_off : -(int64_t(1) << 32);
                     if (kPairs) {
                         const int64_t park =
                             fast ? (odv > 0 ? -(int64_t(1) << 32) : -((int64_t)guard << 32)) -
                                        lane_dv
                                  : -(int64_t(1) << 62);
                         X2 = two ? a2 - ocb - lane_dv : park;
-                        if constexpr (QUAD) Y2 = two ? b2 - ocb - lane_dv : park;
+                        if constexpr (QUAD)
+                            Y2 = two ? (ROWQ ? a2 : b2) - ocb - lane_dv - y_off : park;
                     }
                 };
                 // the next round's peaks are loaded a round ahead, except on the paired
@@ -1308,18 +1323,23 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                 // gives the warp's (max count, smallest row), keyed 32 count + (31 -
                 // lane); rows beyond the slab start their windows at -2^26 and never
                 // win (counts stay below 2^25 on this path).
-                unsigned long long *prof_b = prof + n_f0;
+                // Row pairs: the high halves are rows j0 + 32 + lane of the same
+                // direction, merged into its profile with the low halves' keys.
+                unsigned long long *prof_b = ROWQ ? prof : prof + n_f0;
+                const bool ok_a = lane < min(R, kRows);
+                const bool ok_b = ROWQ ? lane < R - kRows : ok_a;
                 int32_t *map_a = nullptr, *map_b = nullptr;
-                if (J->maps != nullptr && row_ok) {
-                    map_a = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
-                    map_b = map_a + (int64_t)n_fdot * n_f0;
+                if (J->maps != nullptr) {
+                    int32_t *const m0 = J->maps + ((int64_t)d_rel * n_fdot + j0 + lane) * n_f0 + b0;
+                    if (ok_a) map_a = m0;
+                    if (ok_b) map_b = m0 + (ROWQ ? (int64_t)kRows * n_f0 : (int64_t)n_fdot * n_f0);
                 }
                 const int seg = (((Wt + nwarps - 1) / nwarps) + 15) & ~15;
                 const int c0 = min(Wt, warp * seg);
                 const int c1 = min(Wt, c0 + seg);
                 const int c31 = 31 - lane;
-                int wa = row_ok ? 0 : -(1 << 26);
-                int wb = wa;
+                int wa = ok_a ? 0 : -(1 << 26);
+                int wb = ok_b ? 0 : -(1 << 26);
                 if (c0 < c1)
                     for (int L = c0; L < c0 + K; ++L) {
                         const uint32_t h = (uint32_t)H[L * kRows + lane];
@@ -1327,13 +1347,19 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                         wb += (int)(h >> 16);
                     }
                 const uint32_t key_lo = 0xFFFFFFFFu - (uint32_t)j0 - 31u;
+                const uint32_t key_lo_b = ROWQ ? key_lo - (uint32_t)kRows : key_lo;
                 auto key_of = [&](int v) {
                     return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
                            (unsigned long long)(key_lo + (uint32_t)(v & 31));
                 };
-                // 16-byte stores only where both directions' rows are 16-byte aligned
+                auto key_of_b = [&](int v) {
+                    return ((unsigned long long)(uint32_t)(v >> 5) << 32) |
+                           (unsigned long long)(key_lo_b + (uint32_t)(v & 31));
+                };
+                // 16-byte stores only where both rows exist and are 16-byte aligned
                 // (d_b's map starts n_fdot n_f0 words after d_a's)
-                const bool vec_map = map_a != nullptr && (((uintptr_t)map_a & 15u) == 0) &&
+                const bool vec_map = map_a != nullptr && map_b != nullptr &&
+                                     (((uintptr_t)map_a & 15u) == 0) &&
                                      (((uintptr_t)map_b & 15u) == 0);
                 auto run = [&](auto map_tag) {
                     constexpr bool kMap = decltype(map_tag)::value;
@@ -1369,17 +1395,22 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                                     da[q] = make_int4(ca[4 * q], ca[4 * q + 1], ca[4 * q + 2], ca[4 * q + 3]);
                                     db[q] = make_int4(cbn[4 * q], cbn[4 * q + 1], cbn[4 * q + 2], cbn[4 * q + 3]);
                                 }
-                            } else if (map_a) {
+                            } else {
 #pragma unroll
                                 for (int m = 0; m < 16; ++m) {
-                                    map_a[c + m] = ca[m];
-                                    map_b[c + m] = cbn[m];
+                                    if (map_a) map_a[c + m] = ca[m];
+                                    if (map_b) map_b[c + m] = cbn[m];
                                 }
                             }
                         }
                         if (lane < 16) {
-                            atomicMax(prof + c + lane, key_of(myva));
-                            atomicMax(prof_b + c + lane, key_of(myvb));
+                            if constexpr (ROWQ) {
+                                const unsigned long long ka = key_of(myva), kb = key_of_b(myvb);
+                                atomicMax(prof + c + lane, ka > kb ? ka : kb);
+                            } else {
+                                atomicMax(prof + c + lane, key_of(myva));
+                                atomicMax(prof_b + c + lane, key_of(myvb));
+                            }
                         }
                     }
                     for (; c < c1; ++c) {
@@ -1389,15 +1420,18 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
                         const uint32_t y = (uint32_t)H[c * kRows + lane];
                         wa += (int)(x & 0xFFFFu) - (int)(y & 0xFFFFu);
                         wb += (int)(x >> 16) - (int)(y >> 16);
-                        if (kMap && map_a) {
-                            map_a[c] = na;
-                            map_b[c] = nb;
-                        }
+                        if (kMap && map_a) map_a[c] = na;
+                        if (kMap && map_b) map_b[c] = nb;
                         const int va = __reduce_max_sync(kFull, na * 32 + c31);
                         const int vb = __reduce_max_sync(kFull, nb * 32 + c31);
                         if (lane == 0) {
-                            atomicMax(prof + c, key_of(va));
-                            atomicMax(prof_b + c, key_of(vb));
+                            if constexpr (ROWQ) {
+                                const unsigned long long ka = key_of(va), kb = key_of_b(vb);
+                                atomicMax(prof + c, ka > kb ? ka : kb);
+                            } else {
+                                atomicMax(prof + c, key_of(va));
+                                atomicMax(prof_b + c, key_of(vb));
+                            }
                         }
                     }
                 };
@@ -1521,12 +1555,34 @@ transform_kernel(const __grid_constant__ JobTable tbl, int64_t total_items, int3
         };
 
         const std::false_type nos{};
-        if constexpr (PACK) {
+        if constexpr (PACK == 2) {
+            if (rowp) {
+                // a 64-row slab: both halves in one walk where the packed counters
+                // apply, else its two 32-row halves one after the other
+                if (R_slab > kRows && fast && ((job_packed >> jb) & 1u)) {
+                    pass(js, R_slab, std::integral_constant<int, 2>{}, 0, nos);
+                } else {
+                    const int R0 = min(kRows, R_slab), R1 = R_slab - R0;
+                    if (MODE == FH_MODE_START && fast && R0 <= 16)
+                        pass(js, R0, std::false_type{}, 0, std::true_type{});
+                    else
+                        pass(js, R0, std::false_type{}, 0, nos);
+                    if (R1 > 0) {
+                        if (MODE == FH_MODE_START && fast && R1 <= 16)
+                            pass(js + kRows, R1, std::false_type{}, 0, std::true_type{});
+                        else
+                            pass(js + kRows, R1, std::false_type{}, 0, nos);
+                    }
+                }
+            } else {
+                pass(js, R_slab, std::false_type{}, 0, nos);
+            }
+        } else if constexpr (PACK == 1) {
             if (has_b && fast && ((job_packed >> jb) & 1u)) {
                 if (R_slab <= 16)
-                    pass(js, R_slab, std::true_type{}, 0, std::true_type{});
+                    pass(js, R_slab, std::integral_constant<int, 1>{}, 0, std::true_type{});
                 else
-                    pass(js, R_slab, std::true_type{}, 0, nos);
+                    pass(js, R_slab, std::integral_constant<int, 1>{}, 0, nos);
             } else {
                 // a single direction, a pair whose counts need whole words, or one
                 // that takes the clamped walk: each direction on its own
@@ -1863,7 +1919,7 @@ size_t transform_smem_bytes(int32_t tile_cells, int32_t k_over, int32_t mode, in
 // Kernel instantiation for a counting mode and block size: blocks of up to 512
 // threads get up to 128 registers per thread, of up to 640 threads (START
 // mode) 102, of up to 768 threads 80, of 1024 threads 64.
-template <bool WEIGHTED, bool PACK, typename F>
+template <bool WEIGHTED, int PACK, typename F>
 static auto with_transform_kernel_w(int32_t mode, int32_t nwarps, F &&f)
 {
     if constexpr (!PACK) {
@@ -1879,19 +1935,21 @@ static auto with_transform_kernel_w(int32_t mode, int32_t nwarps, F &&f)
 // weighted: instantiation that adds per-FFT weights (adaptive map); plain: +1;
 // pack: direction pairs with two 16-bit counts per word (plain START map only)
 template <typename F>
-static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, bool pack, F &&f)
+static auto with_transform_kernel(int32_t mode, int32_t nwarps, bool weighted, int pack, F &&f)
 {
-    if (pack) return with_transform_kernel_w<false, true>(FH_MODE_START, nwarps, f);
-    return weighted ? with_transform_kernel_w<true, false>(mode, nwarps, f)
-                    : with_transform_kernel_w<false, false>(mode, nwarps, f);
+    if (pack == 1) return with_transform_kernel_w<false, 1>(FH_MODE_START, nwarps, f);
+    if (pack == 2) return with_transform_kernel_w<false, 2>(FH_MODE_START, nwarps, f);
+    return weighted ? with_transform_kernel_w<true, 0>(mode, nwarps, f)
+                    : with_transform_kernel_w<false, 0>(mode, nwarps, f);
 }
 
 cudaError_t transform_prepare(int32_t mode, size_t smem)
 {
     cudaError_t e = cudaSuccess;
     for (int nw : {16, 20, 24, 32})
-        for (int v = 0; v < 3; ++v) {
-            const bool wt = v == 1, pk = v == 2;
+        for (int v = 0; v < 4; ++v) {
+            const bool wt = v == 1;
+            const int pk = v >= 2 ? v - 1 : 0;
             if (pk && mode != FH_MODE_START) continue;
             const cudaError_t r = with_transform_kernel(mode, nw, wt, pk, [&](auto k) {
                 return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1907,7 +1965,7 @@ int transform_blocks_per_sm(int32_t mode, int32_t nwarps, size_t smem)
     int n = 0;
     // (both instantiations are bounded to one block of nwarps warps per SM by
     // their launch bounds; shared memory decides the rest)
-    const cudaError_t e = with_transform_kernel(mode, nwarps, false, false, [&](auto k) {
+    const cudaError_t e = with_transform_kernel(mode, nwarps, false, 0, [&](auto k) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, nwarps * 32, smem);
     });
     return e == cudaSuccess ? n : 0;
@@ -1925,11 +1983,14 @@ cudaError_t launch_transform(int32_t mode, const JobTable &tbl, int64_t total_it
         const int32_t w = (tbl.job[j].tile_cells + tbl.job[j].k_over + 2 * guard) * kRows;
         hist_words = w > hist_words ? w : hist_words;
     }
-    bool weighted = false, pack = mode == FH_MODE_START && tbl.n_jobs > 0;
+    // the launch's packing: every job with direction pairs (1), or with row pairs (2)
+    bool weighted = false, dirs = mode == FH_MODE_START && tbl.n_jobs > 0, rows = dirs;
     for (int j = 0; j < tbl.n_jobs; ++j) {
         weighted = weighted || tbl.job[j].weights != nullptr;
-        pack = pack && tbl.job[j].dir_pairs != 0;
+        dirs = dirs && tbl.job[j].dir_pairs != 0;
+        rows = rows && tbl.job[j].row_pairs != 0;
     }
+    const int pack = dirs ? 1 : rows ? 2 : 0;
     if (weighted && pack) return cudaErrorInvalidValue;  // packed counters hold plain counts only
     with_transform_kernel(mode, nwarps, weighted, pack, [&](auto k) {
         k<<<grid, nwarps * 32, smem, s>>>(tbl, total_items, hist_words, guard, kRows * 4u, sched);

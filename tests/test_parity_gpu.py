@@ -583,3 +583,18 @@ def test_short_last_slab_every_width(fh, oracle_mod, n_fdot):
     o = oracle_mod.search(inp, pp, want_maps=True)
     g = run_gpu(fh, inp, pp, mode=2, tile=320, warps=8)
     compare(g, o, pp, inp.t.shape[0])
+
+
+@pytest.mark.parametrize("n_fdot", [33, 40, 63, 64, 65, 80, 96, 97, 130])
+def test_one_direction_row_pairs(fh, oracle_mod, n_fdot):
+    """One direction of a plain START map walks 64-row slabs with rows j0 + r and
+    j0 + 32 + r in the two 16-bit halves of a counter word (the last slab's
+    halves one after the other where they hold 32 rows or fewer); maps,
+    profiles and candidates equal the oracle's, with the library's default
+    tile and a narrow one (several tiles, a ragged last one)."""
+    inp, pp = synth.random_case(700 + n_fdot, n_fft=30, n_bins=240, k_over=10, n_fdot=n_fdot,
+                                n_dir=1, p=0.3)
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    for tile, warps in ((0, 0), (352, 8)):
+        g = run_gpu(fh, inp, pp, mode=2, tile=tile, warps=warps)
+        compare(g, o, pp, inp.t.shape[0])
