@@ -253,8 +253,9 @@ int fh_sync(fh_plan plan, void *stream);
 /* Time fh_transform over its launch shapes on the current directions (at most
  * 8 of them: the per-item work does not depend on the count) and keep the
  * fastest in the plan; returns its tile width and block warps.  The shapes
- * are: direction pairs (two directions with one 16-bit count each per shared
- * word, where the plain START map allows it) or single directions, block
+ * are: pairs on or off (where the plain START map allows them: two
+ * directions with one 16-bit count each per shared word, or for a single
+ * direction the two 32-row halves of 64-row slabs), block
  * warps (16, 20, 24, 32) and tile widths up to the widest that fits shared
  * memory with the guard cells of that choice; then, for the fastest of them,
  * the item schedule (blocks taking their next item from a device counter, or

@@ -1163,8 +1163,9 @@ int fh_autotune(fh_plan p, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells
             return FH_OK;
         }
     }
-    // candidates: direction pairs (where they apply) or single directions, block
-    // warps, tile widths up to the widest that fits with that choice's guard cells
+    // candidates: pairs (of directions, or of a single direction's row halves;
+    // where they apply) or not, block warps, tile widths up to the widest that
+    // fits with that choice's guard cells
     const int lim = max_optin_smem(p->device);
     std::vector<TuneChoice> cands;
     const int32_t nt = std::min<int32_t>(n_dir, 8);
