@@ -586,6 +586,8 @@ def adaptive_leg(fh, small, flush, torch, steps):
     plan = fh.fh_create_plan(fh.make_desc(pp, n, 1, inp.n_peaks))
     try:
         fh.fh_correct_doppler(plan, *dev)
+        # the launch shape of the weighted map (its own autotuner entry)
+        fh.fh_set_weights(plan, w, 12)
         fh.fh_autotune(plan, 0, 1)
         ts = []
         for k in range(3 + steps):

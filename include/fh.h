@@ -255,15 +255,17 @@ int fh_sync(fh_plan plan, void *stream);
  * fastest in the plan; returns its tile width and block warps.  The shapes
  * are: pairs on or off (where the plain START map allows them: two
  * directions with one 16-bit count each per shared word, or for a single
- * direction the two 32-row halves of 64-row slabs), block
- * warps (16, 20, 24, 32) and tile widths up to the widest that fits shared
- * memory with the guard cells of that choice; then, for the fastest of them,
- * the item schedule (blocks taking their next item from a device counter, or
- * every grid-th item).  Synchronises.  Results are cached per process by grid shape (GPU
- * model, counting mode, weighting, n_f0, n_fdot, K, T_FFT, N_t, n_dir); when
- * the environment variable FH_AUTOTUNE_CACHE names a file, they are also
- * read from and written to it (JSON, one entry per line), so later processes
- * reuse them without timing. */
+ * direction the two 32-row halves of 64-row slabs), block warps (16, 20, 24,
+ * 32) and tile widths up to the widest that fits shared memory with the
+ * guard cells of that choice; then, for the fastest of them, the item
+ * schedule (blocks taking their next item from a device counter, or every
+ * grid-th item).  The shape is chosen for the plan as it stands, weights
+ * included: after fh_set_weights, tune again for the weighted map (which
+ * pairs nothing).  Synchronises.  Results are cached per process by grid
+ * shape (GPU model, counting mode, weighting, n_f0, n_fdot, K, T_FFT, N_t,
+ * n_dir); when the environment variable FH_AUTOTUNE_CACHE names a file, they
+ * are also read from and written to it (JSON, one entry per line), so later
+ * processes reuse them without timing. */
 int fh_autotune(fh_plan plan, int32_t dir_begin, int32_t n_dir, int32_t *tile_cells,
                 int32_t *block_warps, void *stream);
 
