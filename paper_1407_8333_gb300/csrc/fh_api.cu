@@ -250,7 +250,8 @@ struct fh_plan_s {
     size_t win_bytes = 0;
     int32_t guard = 0;                   // guard cells for the transform's fast path (32 rows)
     unsigned long long drift = 0;        // bound of max |D_i| the guards are sized for
-    int32_t pair_pref = 0;               // 0: direction pairs where they apply; 1: never
+    int32_t pair_pref = 0;               // 0: pairs (of directions, or of one direction's row
+                                         // halves) where they apply; 1: never
     int32_t item_counter = 1;            // batched transform: items from the counter (1) or
                                          // every grid-th item per block (0)
     int32_t n_fft = -1;
@@ -830,8 +831,6 @@ int fh_correct_doppler(fh_plan p, const fh_peakmap *pm, const double *v_over_c,
     return FH_OK;
 }
 
-// Direction pairs for n_dir directions of the plan's current peakmap (pref 0:
-// where they apply; 1: never).
 // What an item of n_dir directions of the plan's current peakmap pairs in
 // the shared counter words (pref 0: where it applies; 1: never): 0 nothing,
 // 1 two directions, 2 (one direction) two 32-row halves of a 64-row slab.
