@@ -38,7 +38,8 @@ using Clock = std::chrono::steady_clock;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-constexpr int32_t kServeWarps = 24;  // transform block size of served batches
+constexpr int32_t kServeWarps = 24;      // transform block size of served batches
+constexpr int32_t kServePairWarps = 20;  // the same for batches of paired jobs
 
 struct Job {
     fh_job_id id = 0;
@@ -65,12 +66,19 @@ struct Job {
     int32_t *d_err = nullptr;
     unsigned long long *d_dmax = nullptr;
     int32_t guard = 0;
-    uint32_t *d_win = nullptr;  // peak windows [dir][slab][tile][fft] at the job's tile
+    // what the job's items pair in the counters' 16-bit halves: 0 nothing, 1 two
+    // directions, 2 (one direction) the two 32-row halves of 64-row slabs
+    int32_t pairs = 0;
+    uint32_t *d_win = nullptr;  // peak windows [unit][slab][tile][fft] at the job's tile
+    int32_t *d_udelta = nullptr;  // (pairs == 1) per direction pair, the largest distance
     size_t pin_off = 0;  // offset of its candidates in the batch's pinned buffer
     size_t err_off = 0;
 
     int64_t cand_count() const { return (int64_t)n_dir * n_sb * d.top_k; }
-    int32_t n_slabs() const { return (d.n_fdot + kRows - 1) / kRows; }
+    int32_t slab_rows() const { return pairs == 2 ? 2 * kRows : kRows; }
+    int32_t n_slabs() const { return (d.n_fdot + slab_rows() - 1) / slab_rows(); }
+    int32_t units() const { return pairs == 1 ? (n_dir + 1) / 2 : n_dir; }
+    int32_t warps() const { return pairs ? kServePairWarps : kServeWarps; }
     int32_t n_tiles() const { return tile > 0 ? (d.n_f0 + tile - 1) / tile : 0; }
 
     // layout of the job's single device allocation
@@ -93,10 +101,12 @@ struct Job {
         const size_t a_prof = take(8 * (size_t)n_dir * (size_t)d.n_f0);
         const size_t a_cand = take(sizeof(fh_candidate) * (size_t)cand_count());
         const size_t a_err = take(16);
-        const size_t a_win = take(sizeof(uint32_t) * (size_t)n_dir * (size_t)n_slabs() *
+        const size_t a_win = take(sizeof(uint32_t) * (size_t)units() * (size_t)n_slabs() *
                                   (size_t)n_tiles() * (size_t)std::max(1, n_fft));
         const size_t a_dmax = take(16);
+        const size_t a_ud = take(pairs == 1 ? sizeof(int32_t) * (size_t)units() : 0);
         if (carve) {
+            d_udelta = pairs == 1 ? (int32_t *)(dbuf + a_ud) : nullptr;
             d_dmax = (unsigned long long *)(dbuf + a_dmax);
             d_win = (uint32_t *)(dbuf + a_win);
             d_off = (int64_t *)(dbuf + a_off);
@@ -232,18 +242,22 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
     // keeps the tile its window table was sized for, so jobs (in order of
     // guard) join a group only while every member's tile still fits in shared
     // memory with the group's guard.
-    const int nwarps = kServeWarps;
+    // (a launch's jobs pair alike: grouped by what they pair, then by guard)
     const size_t lim = (size_t)max_optin_smem(device);
     std::vector<Job *> order(batch.begin(), batch.end());
-    std::stable_sort(order.begin(), order.end(),
-                     [](const Job *x, const Job *y) { return x->guard < y->guard; });
-    auto fits = [&](const Job *j, int32_t guard) {
-        return transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps, guard) <= lim;
-    };
+    std::stable_sort(order.begin(), order.end(), [](const Job *x, const Job *y) {
+        return x->pairs != y->pairs ? x->pairs < y->pairs : x->guard < y->guard;
+    });
     for (size_t g = 0; g < order.size();) {
+        const int32_t kind = order[g]->pairs;
+        const int nwarps = order[g]->warps();
+        auto fits = [&](const Job *j, int32_t guard) {
+            return transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps, guard) <= lim;
+        };
         size_t g_end = g + 1;
         int32_t guard = std::max<int32_t>(2, order[g]->guard);
-        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs) {
+        while (g_end < order.size() && g_end - g < (size_t)kMaxBatchJobs &&
+               order[g_end]->pairs == kind) {
             const int32_t gn = std::max(guard, order[g_end]->guard);
             bool ok = true;
             for (size_t k = g; k <= g_end && ok; ++k) ok = fits(order[k], gn);
@@ -279,8 +293,16 @@ int fh_server_s::launch_batch(Slot &slot, std::vector<Job *> &batch)
             t.n_dir = j->n_dir;
             t.windows = j->d_win;
             t.dense = reinterpret_cast<int32_t *>(j->d_dmax + 1);  // beside dmax, cleared with it
+            t.dir_pairs = j->pairs == 1 ? 1 : 0;
+            t.row_pairs = j->pairs == 2 ? 1 : 0;
+            t.unit_delta = j->d_udelta;
+            t.delta_alloc = pair_delta(j->d);
             t.item_begin = items;
-            t.n_items = (int64_t)t.n_slabs * t.n_tiles * j->n_dir;
+            t.n_items = (int64_t)t.n_slabs * t.n_tiles * j->units();
+            if (j->d_udelta) {
+                e = cudaMemsetAsync(j->d_udelta, 0, sizeof(int32_t) * (size_t)j->units(), s);
+                if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(pair distances)");
+            }
             items += t.n_items;
             smem = std::max(smem, transform_smem_bytes(j->tile, j->d.k_over, FH_MODE_START, nwarps,
                                                        guard));
@@ -491,8 +513,18 @@ int copy_job(const fh_job_desc *jd, Job &j, int device)
     // the job runs with the library's default tile for its own guard cells
     const unsigned long long drift =
         std::max(default_drift(j.d), host_drift(j.d, j.kt, j.t.data(), j.n_fft));
-    j.guard = guard_for(drift);
-    j.tile = default_tile(j.d, device, FH_MODE_START, kServeWarps, j.guard);
+    // pairs where they apply: two directions per item, or the row halves of one
+    if (pairs_apply(j.d, device, j.n_fft, j.n_dir, drift)) {
+        j.pairs = 1;
+        j.guard = guard_for(drift) + pair_delta(j.d);
+    } else if (rows_apply(j.d, device, j.n_fft, j.n_dir, drift)) {
+        j.pairs = 2;
+        j.guard = guard_for(drift, 2 * kRows - 1);
+    } else {
+        j.pairs = 0;
+        j.guard = guard_for(drift);
+    }
+    j.tile = default_tile(j.d, device, FH_MODE_START, j.warps(), j.guard);
     j.bytes = j.layout(false);
     return FH_OK;
 }
