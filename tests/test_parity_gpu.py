@@ -598,3 +598,40 @@ def test_one_direction_row_pairs(fh, oracle_mod, n_fdot):
     for tile, warps in ((0, 0), (352, 8)):
         g = run_gpu(fh, inp, pp, mode=2, tile=tile, warps=warps)
         compare(g, o, pp, inp.t.shape[0])
+
+
+def test_row_pairs_dense_and_bad_device_inputs(fh, oracle_mod):
+    """One direction in 64-row slabs when the paired counters do not apply:
+    dense off-grid peaks (two stripes of one FFT can start in one cell, so the
+    16-bit halves could overflow) walk the slab's two 32-row halves one after
+    the other with whole-word counts, equal to the oracle; unsorted device
+    frequencies make the transform take the clamped walk over the 64-row
+    windows, reported at the next synchronising call, and the next valid call
+    is equal to the oracle again."""
+    import torch
+    inp, pp = synth.dense_case(95, dense_ffts=(2, 5), n_dense=40, spacing_bins=0.05,
+                               n_fft=12, n_bins=300, n_fdot=70, n_dir=1, p=0.2)
+    o = oracle_mod.search(inp, pp, want_maps=True)
+    compare(run_gpu(fh, inp, pp, mode=2), o, pp, inp.t.shape[0])
+    clean, cpp = synth.random_case(96, n_fft=12, n_bins=300, n_fdot=70, n_dir=1, p=0.3)
+    plan = fh.fh_create_plan(fh.make_desc(cpp, 12, 1, clean.n_peaks))
+    try:
+        dev = lambda x: torch.from_numpy(x).cuda()
+        f = clean.freq.copy()
+        for i in range(clean.t.shape[0]):
+            a, b = int(clean.offsets[i]), int(clean.offsets[i + 1])
+            f[a:b] = f[a:b][::-1]
+        fh.fh_correct_doppler(plan, dev(clean.t), dev(clean.offsets), dev(f), dev(clean.v),
+                              dev(clean.sky))
+        fh.fh_transform(plan, 0, 1)
+        with pytest.raises(fh.FHError) as ei:
+            fh.fh_sync(plan)
+        assert ei.value.code == fh.FH_ERR_UNSORTED
+        fh.fh_correct_doppler(plan, *[dev(x) for x in (clean.t, clean.offsets, clean.freq,
+                                                      clean.v, clean.sky)])
+        m = torch.full((1, cpp["n_fdot"], cpp["n_f0"]), -7, dtype=torch.int32, device="cuda")
+        fh.fh_transform(plan, 0, 1, m)
+        torch.cuda.synchronize()
+        assert np.array_equal(m.cpu().numpy(), oracle_mod.search(clean, cpp, want_maps=True)["maps"])
+    finally:
+        fh.fh_destroy_plan(plan)
