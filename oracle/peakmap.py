@@ -45,7 +45,10 @@ def select_peaks(s_p, s_ar, theta: float):
     s_p = np.ascontiguousarray(s_p, dtype=np.float32)
     s_ar = np.ascontiguousarray(s_ar, dtype=np.float32)
     n_fft, n_bins = s_p.shape
-    r = s_p / s_ar                                   # binary32, one rounding per bin
+    with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+        # IEEE results for zero, tiny or non-finite spectra (inf, nan) are the
+        # ratios the comparisons below see; no warning is raised for them
+        r = s_p / s_ar                               # binary32, one rounding per bin
     th = np.float32(theta)
     sel = np.zeros((n_fft, n_bins), dtype=bool)
     if n_bins >= 3:
